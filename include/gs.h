@@ -1,0 +1,228 @@
+/*
+ * gs.h — C ABI of the GB300 (sm_103a) differentiable 3D-Gaussian rasterizer.
+ *
+ * The library renders a map of 3D Gaussians (mean, covariance, opacity and colour:
+ * the scene model of Sec. II-A of "Real-time Photorealistic Mapping for Situational
+ * Awareness in Robot Teleoperation") from K camera poses and differentiates the
+ * result back to the Gaussians and the poses, which is what the mapping optimiser
+ * (render I1 of Fig. 3) and render-based pose tracking (Sec. II-B) call every
+ * iteration. The paper names this renderer but does not write it out; the reading
+ * implemented here is the tile-based EWA splatting rasterizer:
+ *
+ *   gs_project      per (view, Gaussian): 2D mean, conic, depth, radius, tile rectangle
+ *   gs_bin_sort     prefix sum of tiles touched, (tile << 32 | depth bits) keys, stable
+ *                   onesweep LSD radix sort, per-tile [start, end) ranges
+ *   gs_raster_fwd   front-to-back alpha compositing of colour, depth, transmittance
+ *   gs_loss_l1      photometric L1(RGB) + lambda L1(depth) and its image gradient
+ *   gs_raster_bwd   reverse of the compositing into per-(Gaussian, tile) gradients
+ *   gs_project_bwd  reverse of the projection into means, log-scales, quaternions,
+ *                   opacity logits, colours and the se(3) camera poses
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named d_* and every array argument are DEVICE pointers unless the
+ *   comment says "host". Arrays are C-contiguous, structure of arrays.
+ * - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *   Every call except gs_read_status only enqueues work on `stream` and returns.
+ * - The library never allocates device memory. The caller owns every buffer and
+ *   provides one opaque workspace `ws` of at least gs_workspace_size() bytes,
+ *   256-byte aligned. The workspace carries state from gs_project through
+ *   gs_project_bwd; calls on one workspace must be ordered on one stream.
+ * - Synchronous errors (bad arguments, undersized workspace, launch failure) are
+ *   returned as gs_status_t and nothing is enqueued. Errors found on the device
+ *   (pair capacity exceeded, a bounded wait that gave up, non-finite input) set
+ *   bits of a device error word inside `ws`; gs_read_status returns it. Kernels
+ *   never trap.
+ * - Gradient outputs are ACCUMULATED (+=). The caller zeroes them; summing over
+ *   several calls or views is how batches accumulate.
+ * - Images: rgb is [K,3,H,W] (planar), depth / T_final / last are [K,H,W]; pixel
+ *   (i, j) is sampled at its centre (i + 0.5, j + 0.5).
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1,          /* null pointer, size out of range, misaligned ws */
+  GS_ERR_WORKSPACE_TOO_SMALL = 2,  /* ws_bytes < gs_workspace_size() */
+  GS_ERR_CAPACITY_OVERFLOW = 3,    /* returned by gs_read_status when the device word says so */
+  GS_ERR_DEVICE_TIMEOUT = 4,       /* returned by gs_read_status: a bounded device wait gave up */
+  GS_ERR_CUDA = 5,                 /* a CUDA runtime call or kernel launch failed */
+  GS_ERR_NONFINITE = 6             /* returned by gs_read_status: non-finite input seen */
+} gs_status_t;
+
+/* Bits of the device error word (gs_read_status). */
+#define GS_DEVERR_PAIR_OVERFLOW 0x1u /* more (Gaussian, tile) pairs than pair_capacity */
+#define GS_DEVERR_TIMEOUT 0x2u       /* a decoupled look-back spin hit its iteration cap */
+#define GS_DEVERR_NONFINITE 0x4u     /* a mean, scale, quaternion, logit or colour was NaN/Inf */
+
+typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype_t;
+
+/* One pinhole camera, 64 bytes. R, t map world to camera: p_c = R p + t, with the
+ * camera looking along +z, x right and y down. Pixel u = fx x/z + cx, v = fy y/z + cy. */
+typedef struct {
+  float fx, fy, cx, cy;
+  float R[9]; /* row-major */
+  float t[3];
+} gs_camera_t;
+
+typedef struct {
+  int32_t width, height;  /* image size shared by all K views, 1..16384 */
+  int32_t tile;           /* tile side in pixels; must be 16 */
+  int32_t num_views;      /* K, 1..1024 */
+  int64_t num_gaussians;  /* N, 0..2^31-1 */
+  int64_t pair_capacity;  /* max (Gaussian, tile) pairs held by the workspace, <= 2^30 - 1 */
+  float near_plane;       /* Gaussians with camera depth <= near_plane are culled (0.2) */
+  float lambda_depth;     /* depth weight of gs_loss_l1 (0.1) */
+} gs_config_t;
+
+/* Gaussian attributes. means may be F32 or BF16/F16 (means_dtype); the other four
+ * arrays share `dtype`. All arithmetic is FP32 whatever the storage type. */
+typedef struct {
+  const void* means;          /* [N,3] world position */
+  const void* log_scales;     /* [N,3] log of the per-axis standard deviation */
+  const void* quats;          /* [N,4] (w,x,y,z), any non-zero length */
+  const void* opacity_logits; /* [N]   opacity = sigmoid(logit) */
+  const void* rgb;            /* [N,3] colour (degree-0 appearance, used as is) */
+  gs_dtype_t dtype;
+  gs_dtype_t means_dtype;
+} gs_gaussians_t;
+
+/* Gradient outputs of gs_project_bwd, FP32, accumulated (+=); any may be NULL (skipped). */
+typedef struct {
+  float* means;          /* [N,3] */
+  float* log_scales;     /* [N,3] */
+  float* quats;          /* [N,4] w.r.t. the stored (unnormalised) quaternion */
+  float* opacity_logits; /* [N] */
+  float* rgb;            /* [N,3] */
+  float* pose;           /* [K,6] (rho, phi): left perturbation T <- Exp(xi) T at xi = 0 */
+} gs_grads_t;
+
+/* Byte offsets of the workspace sub-buffers (for inspection and tests). */
+typedef struct {
+  size_t total;          /* == gs_workspace_size() */
+  size_t status;         /* u32 error word, u32 num_pairs (clamped), u64 total pairs, u64 evals */
+  size_t proj_uv;        /* float4 [K*N]: u_hi, u_lo, v_hi, v_lo (u = u_hi + u_lo) */
+  size_t proj_conic;     /* float4 [K*N]: conic A, B, C (Sigma2^-1 entries 00, 01, 11), depth z */
+  size_t proj_tiles;     /* int4 [K*N]: pair offset, x0 | x1 << 16, y0 | y1 << 16, tiles touched */
+  size_t proj_depth_key; /* u32 [K*N]: binary32 bits of the camera depth (sort key low word) */
+  size_t proj_radius;    /* i32 [K*N]: pixel radius (0 when culled) */
+  size_t color_opacity;  /* float4 [N]: r, g, b, opacity */
+  size_t keys_sorted;    /* u64 [pair_capacity], valid prefix num_pairs, after gs_bin_sort */
+  size_t vals_sorted;    /* u32 [pair_capacity]: Gaussian id of each sorted key */
+  size_t ranges;         /* u32 [K*Tx*Ty][2]: [start, end) of each global tile */
+  size_t pair_grads;     /* float [pair_capacity][12]: per-pair gradients of gs_raster_bwd */
+  int32_t sort_passes;   /* 8-bit LSD passes: ceil((32 + ceil(log2(K*Tx*Ty))) / 8) */
+  int32_t tiles_x, tiles_y;
+} gs_ws_layout_t;
+
+/* ---------------------------------------------------------------- sizing / status */
+
+/* Workspace bytes for `cfg` (host call, no device work). */
+GS_API gs_status_t gs_workspace_size(const gs_config_t* cfg, size_t* bytes);
+
+/* Sub-buffer offsets of the workspace for `cfg` (host call). */
+GS_API gs_status_t gs_workspace_layout(const gs_config_t* cfg, gs_ws_layout_t* out);
+
+/* Synchronises `stream`, then reads the device error word, the pair count and the
+ * eval count (Gaussian-pixel evaluations of the last gs_raster_fwd) into host
+ * memory. Any pointer may be NULL. Returns GS_OK, or the first device error in the
+ * order CAPACITY_OVERFLOW, DEVICE_TIMEOUT, NONFINITE, or GS_ERR_CUDA. */
+GS_API gs_status_t gs_read_status(const gs_config_t* cfg, const void* ws, size_t ws_bytes, uint32_t* err_word,
+                           int64_t* num_pairs, int64_t* evals, void* stream);
+
+/* ---------------------------------------------------------------- the hot path */
+
+/* Projection (Sec. II-A: Gaussians "defined by their mean, covariance and opacity").
+ * For every view k < K and Gaussian g < N, with p_c = R p + t, Sigma = Rq S S^T Rq^T
+ * (Rq from the normalised quaternion, S = diag(exp(log_scale))), J the perspective
+ * Jacobian at p_c with x/z, y/z clamped to 1.3 * (W/2)/fx and 1.3 * (H/2)/fy:
+ *   Sigma2 = J R Sigma R^T J^T + 0.3 I,   conic = Sigma2^-1,
+ *   radius = ceil(3 sqrt(lambda_max)),     lambda_max = mid + sqrt(max(0.1, ((a-c)/2)^2 + b^2)),
+ *   rect   = tiles whose 16x16 square meets [u - r, u + r] x [v - r, v + r],
+ * culling z <= near_plane and empty rectangles. The depth key, culls, radius and
+ * rectangle are computed in binary32 in one fixed operation order (the design doc,
+ * "discrete projection"), so they are reproducible bit for bit. d_cams: K cameras. */
+GS_API gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, const gs_camera_t* d_cams, void* ws,
+                       size_t ws_bytes, void* stream);
+
+/* Binning: exclusive scan of tiles touched, emission of one pair per (view, Gaussian,
+ * tile) with key = ((k*Tx*Ty + ty*Tx + tx) << 32) | depth bits and value = g, a stable
+ * LSD radix sort on the low 32 + ceil(log2(K*Tx*Ty)) key bits (so equal keys keep
+ * (k, g) emission order), and per-tile [start, end) ranges. The pair count stays on
+ * the device; more than pair_capacity pairs sets GS_DEVERR_PAIR_OVERFLOW and only the
+ * first pair_capacity pairs are emitted. */
+GS_API gs_status_t gs_bin_sort(const gs_config_t* cfg, void* ws, size_t ws_bytes, void* stream);
+
+/* Forward compositing (render I1/I2 of Fig. 3). Per pixel, front to back over its
+ * tile's sorted list: power = -0.5 d^T conic d with d = mean2D - pixel (skip if > 0),
+ * alpha = min(0.99, opacity exp(power)) (skip if < 1/255), stop before a Gaussian whose
+ * T (1 - alpha) < 1e-4, otherwise C += rgb alpha T, D += z alpha T, T *= 1 - alpha.
+ * Background 0; D is the un-normalised expected depth. Writes rgb [K,3,H,W],
+ * depth, T_final [K,H,W] and last [K,H,W] = 1 + list position of the last composited
+ * Gaussian (0 if none); each may be NULL except what gs_raster_bwd will need. */
+GS_API gs_status_t gs_raster_fwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                          float* T_final, int32_t* last, void* stream);
+
+/* Photometric loss of a mapping step: L = sum_k [ mean|R - R*| over 3HW + lambda
+ * mean|D - D*| over HW ], sign(0) = 0. Writes dL/drgb [K,3,H,W], dL/ddepth [K,H,W] and
+ * the scalar L to d_loss[0] (device). rgb/depth are the forward outputs. */
+GS_API gs_status_t gs_loss_l1(const gs_config_t* cfg, const float* rgb, const float* depth, const float* rgb_target,
+                       const float* depth_target, float* dL_drgb, float* dL_ddepth, float* d_loss, void* ws,
+                       size_t ws_bytes, void* stream);
+
+/* Backward compositing (the splat-wise back-propagation the mapping optimiser needs,
+ * Sec. II-B). Inputs: the forward outputs rgb, depth, T_final, last and the upstream
+ * gradients dL/drgb, dL/ddepth, dL/dT_final (dL_dT may be NULL = 0). For each
+ * composited Gaussian i of a pixel, with S the colour/depth accumulated behind it:
+ *   dC/dc_i = alpha_i T_i,  dC/dalpha_i = c_i T_i - S / (1 - alpha_i),
+ *   dT_final/dalpha_i = -T_final / (1 - alpha_i); the 0.99 clamp passes no gradient.
+ * Writes one gradient record per sorted pair into the workspace (mean2D, conic,
+ * depth, opacity, colour), summed over the tile's pixels; gs_project_bwd consumes it. */
+GS_API gs_status_t gs_raster_bwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, const float* rgb, const float* depth,
+                          const float* T_final, const int32_t* last, const float* dL_drgb, const float* dL_ddepth,
+                          const float* dL_dT, void* stream);
+
+/* Backward projection: sums each (view, Gaussian)'s pair records in a fixed order
+ * (deterministic, no atomics) and applies the chain rule of gs_project to the means,
+ * log-scales, quaternions (through the normalisation), opacity logits, colours and
+ * the pose of each view (rho, phi), accumulating into `grads`. */
+GS_API gs_status_t gs_project_bwd(const gs_config_t* cfg, const gs_gaussians_t* gaussians, const gs_camera_t* d_cams,
+                           void* ws, size_t ws_bytes, const gs_grads_t* grads, void* stream);
+
+/* Screen-space gradients of the last gs_raster_bwd, summed per (view, Gaussian): for
+ * inspection and densification statistics. Outputs (overwritten, any may be NULL):
+ * d_mean2d [K*N,2], d_conic [K*N,3], d_depth [K*N], d_opacity [N] (w.r.t. the
+ * opacity, not the logit), d_rgb [N,3]. */
+GS_API gs_status_t gs_screen_grads(const gs_config_t* cfg, const void* ws, size_t ws_bytes, float* d_mean2d, float* d_conic,
+                            float* d_depth, float* d_opacity, float* d_rgb, void* stream);
+
+/* ---------------------------------------------------------------- sort primitive */
+
+/* Temporary bytes for gs_sort_pairs on n pairs (host call). */
+GS_API gs_status_t gs_sort_pairs_tmp_size(int64_t n, size_t* bytes);
+
+/* Stable LSD radix sort (8-bit digits, one onesweep pass per digit) of n (key, value)
+ * pairs on the low key_bits (1..64) bits of the keys, in place. tmp: caller-owned
+ * scratch of gs_sort_pairs_tmp_size(n) bytes. n <= 2^30 - 1. */
+GS_API gs_status_t gs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int32_t key_bits, void* tmp, size_t tmp_bytes,
+                          uint32_t* d_err_word, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

@@ -72,6 +72,8 @@ def _declare(L):
     L.orc_expdet_f32.restype = None
     L.orc_project_mirror.argtypes = [_I64, _P, _P, _P, _I, _P, _I, _I, _I, _F, _P, _P, _P, _P, _P]
     L.orc_project_mirror.restype = None
+    L.orc_project64.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P]
+    L.orc_project64.restype = None
     L.orc_bin.argtypes = [_I64, _I, _I, _I, _I, _P, _P, _P, _I64, _P, _P, _P]
     L.orc_bin.restype = _I64
     L.orc_render_fwd.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _D, _D, _D,
@@ -129,6 +131,16 @@ def project_mirror(means, log_scales, quats, cams, W, H, tile=TILE, near=NEAR) -
     lib().orc_project_mirror(N, _ptr(means), _ptr(log_scales), _ptr(quats), K, _ptr(cams), W, H, tile,
                              near, _ptr(out.depth_bits), _ptr(out.radius), _ptr(out.rect), _ptr(out.count),
                              _ptr(out.uv))
+    return out
+
+
+def project64(params, cams, W, H) -> np.ndarray:
+    """FP64 projection of every (view, Gaussian): [K*N, 8] = u, v, A, B, C, z, opacity, det."""
+    means, ls, qs, lg, rgb = params64(*params)
+    cams = _c(np.asarray(cams, np.float64), np.float64).reshape(-1, 16)
+    N, K = means.shape[0], cams.shape[0]
+    out = np.empty((K * N, 8))
+    lib().orc_project64(N, _ptr(means), _ptr(ls), _ptr(qs), _ptr(lg), _ptr(rgb), K, _ptr(cams), W, H, _ptr(out))
     return out
 
 

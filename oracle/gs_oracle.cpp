@@ -384,6 +384,24 @@ void orc_project_mirror(int64_t N, const float* means, const float* log_scales, 
   }
 }
 
+// FP64 projection of every (view, Gaussian): out [K*N, 8] = u, v, A, B, C, z, opacity, det(Sigma2).
+void orc_project64(int64_t N, const double* means, const double* log_scales, const double* quats,
+                   const double* logits, const double* rgb, int K, const double* cams, int W, int H, double* out) {
+  const std::vector<Proj64> pr = project_all(N, means, log_scales, quats, logits, rgb, K, cams, W, H);
+  for (int64_t kg = 0; kg < static_cast<int64_t>(K) * N; ++kg) {
+    const Proj64& P = pr[kg];
+    double* o = out + 8 * kg;
+    o[0] = P.u;
+    o[1] = P.v;
+    o[2] = P.A;
+    o[3] = P.B;
+    o[4] = P.C;
+    o[5] = P.pc[2];
+    o[6] = P.o;
+    o[7] = P.a * P.c - P.b * P.b;
+  }
+}
+
 // Pair emission in increasing (k, g) order, tiles row-major inside each rectangle;
 // key = (global tile id << 32) | depth bits, value = g; std::stable_sort by key keeps
 // equal keys in emission order. ranges[t] = [start, end) of global tile t (empty = [0,0)).

@@ -1,0 +1,237 @@
+"""Python face of the C ABI: one function per ``gs_*`` entry point, plus a small
+``Rasterizer`` that owns a workspace and chains the calls of a forward render and
+of its backward pass.
+
+PyTorch only provides device memory and streams here. Every computation runs in
+the sm_103a kernels of ``libgs.so``; if the library cannot be loaded the calls
+raise instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _lib
+from ._lib import GsConfig, GsGaussians, GsGrads, GsWsLayout, call
+
+DTYPES = {torch.float32: _lib.GS_F32, torch.bfloat16: _lib.GS_BF16, torch.float16: _lib.GS_F16}
+TILE = 16
+
+
+def _p(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "tensors passed to the library must be contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _s(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_config(width, height, num_views, num_gaussians, pair_capacity, near_plane=0.2, lambda_depth=0.1):
+    return GsConfig(int(width), int(height), TILE, int(num_views), int(num_gaussians), int(pair_capacity),
+                    float(near_plane), float(lambda_depth))
+
+
+def workspace_size(cfg: GsConfig) -> int:
+    n = ctypes.c_size_t()
+    call("gs_workspace_size", ctypes.byref(cfg), ctypes.byref(n))
+    return n.value
+
+
+def workspace_layout(cfg: GsConfig) -> GsWsLayout:
+    out = GsWsLayout()
+    call("gs_workspace_layout", ctypes.byref(cfg), ctypes.byref(out))
+    return out
+
+
+@dataclasses.dataclass
+class Gaussians:
+    """Device tensors of N Gaussians (see include/gs.h for layouts)."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    rgb: torch.Tensor
+
+    @property
+    def N(self) -> int:
+        return int(self.means.shape[0])
+
+    def struct(self) -> GsGaussians:
+        dt = DTYPES[self.log_scales.dtype]
+        for t in (self.quats, self.opacity_logits, self.rgb):
+            assert DTYPES[t.dtype] == dt, "log_scales, quats, opacity_logits and rgb share one storage dtype"
+        return GsGaussians(_p(self.means), _p(self.log_scales), _p(self.quats), _p(self.opacity_logits), _p(self.rgb),
+                           dt, DTYPES[self.means.dtype])
+
+    @staticmethod
+    def from_numpy(params, device="cuda", dtype=torch.float32, means_dtype=torch.float32) -> "Gaussians":
+        means, ls, qs, lg, rgb = params
+        t = lambda a, d: torch.as_tensor(a).to(device=device, dtype=d).contiguous()  # noqa: E731
+        return Gaussians(t(means, means_dtype), t(ls, dtype), t(qs, dtype), t(lg, dtype), t(rgb, dtype))
+
+
+def workspace(cfg: GsConfig, device="cuda") -> torch.Tensor:
+    # torch's caching allocator returns blocks aligned to at least 512 bytes
+    ws = torch.empty(workspace_size(cfg), dtype=torch.uint8, device=device)
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def gs_project(cfg, g: Gaussians, cams: torch.Tensor, ws: torch.Tensor, stream=None):
+    gs = g.struct()
+    call("gs_project", ctypes.byref(cfg), ctypes.byref(gs), _p(cams), _p(ws), ws.numel(), _s(stream))
+
+
+def gs_bin_sort(cfg, ws, stream=None):
+    call("gs_bin_sort", ctypes.byref(cfg), _p(ws), ws.numel(), _s(stream))
+
+
+def gs_raster_fwd(cfg, ws, rgb, depth, T_final, last, stream=None):
+    call("gs_raster_fwd", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
+         _s(stream))
+
+
+def gs_loss_l1(cfg, rgb, depth, rgb_target, depth_target, dL_drgb, dL_ddepth, loss, ws, stream=None):
+    call("gs_loss_l1", ctypes.byref(cfg), _p(rgb), _p(depth), _p(rgb_target), _p(depth_target), _p(dL_drgb),
+         _p(dL_ddepth), _p(loss), _p(ws), ws.numel(), _s(stream))
+
+
+def gs_raster_bwd(cfg, ws, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT=None, stream=None):
+    call("gs_raster_bwd", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
+         _p(dL_drgb), _p(dL_ddepth), _p(dL_dT), _s(stream))
+
+
+def gs_project_bwd(cfg, g: Gaussians, cams, ws, grads: dict, stream=None):
+    gs = g.struct()
+    gr = GsGrads(*(_p(grads.get(k)) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose")))
+    call("gs_project_bwd", ctypes.byref(cfg), ctypes.byref(gs), _p(cams), _p(ws), ws.numel(), ctypes.byref(gr),
+         _s(stream))
+
+
+def gs_screen_grads(cfg, ws, d_mean2d=None, d_conic=None, d_depth=None, d_opacity=None, d_rgb=None, stream=None):
+    call("gs_screen_grads", ctypes.byref(cfg), _p(ws), ws.numel(), _p(d_mean2d), _p(d_conic), _p(d_depth),
+         _p(d_opacity), _p(d_rgb), _s(stream))
+
+
+def gs_read_status(cfg, ws, stream=None):
+    """Synchronises the stream; returns (status code, error word, total pairs, evals)."""
+    err = ctypes.c_uint32()
+    npairs = ctypes.c_int64()
+    ev = ctypes.c_int64()
+    code = _lib.load().gs_read_status(ctypes.byref(cfg), _p(ws), ws.numel(), ctypes.byref(err), ctypes.byref(npairs),
+                                      ctypes.byref(ev), _s(stream))
+    return code, err.value, npairs.value, ev.value
+
+
+def gs_sort_pairs_tmp_size(n: int) -> int:
+    b = ctypes.c_size_t()
+    call("gs_sort_pairs_tmp_size", ctypes.c_int64(n), ctypes.byref(b))
+    return b.value
+
+
+def gs_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int, tmp=None, err=None, stream=None):
+    """In-place stable radix sort of int64 (bit pattern u64) keys with int32 (u32) values."""
+    n = keys.numel()
+    assert vals.numel() == n and keys.dtype == torch.int64 and vals.dtype == torch.int32
+    if tmp is None:
+        tmp = torch.empty(max(gs_sort_pairs_tmp_size(n), 256), dtype=torch.uint8, device=keys.device)
+    call("gs_sort_pairs", _p(keys), _p(vals), ctypes.c_int64(n), ctypes.c_int32(key_bits), _p(tmp), tmp.numel(),
+         _p(err), _s(stream))
+
+
+# ----------------------------------------------------------------------------- convenience
+
+class CapacityOverflow(RuntimeError):
+    pass
+
+
+class Rasterizer:
+    """Owns a workspace for (W, H, K views, N Gaussians) and chains the entry points.
+
+    ``render`` runs gs_project -> gs_bin_sort -> gs_raster_fwd; ``backward`` runs
+    gs_raster_bwd -> gs_project_bwd. Outputs and gradients are fresh torch tensors.
+    """
+
+    def __init__(self, width, height, num_views, num_gaussians, pair_capacity=None, device="cuda",
+                 near_plane=0.2, lambda_depth=0.1):
+        self.W, self.H, self.K, self.N = int(width), int(height), int(num_views), int(num_gaussians)
+        self.device = torch.device(device)
+        self.near_plane, self.lambda_depth = near_plane, lambda_depth
+        if pair_capacity is None:
+            pair_capacity = max(1 << 16, 8 * self.N * self.K)
+        self._configure(pair_capacity)
+
+    def _configure(self, cap):
+        self.cap = int(min(cap, (1 << 30) - 1))
+        self.cfg = make_config(self.W, self.H, self.K, self.N, self.cap, self.near_plane, self.lambda_depth)
+        self.ws = workspace(self.cfg, self.device)
+        self.layout = workspace_layout(self.cfg)
+
+    def status(self, stream=None):
+        return gs_read_status(self.cfg, self.ws, stream)
+
+    def project_and_sort(self, g: Gaussians, cams: torch.Tensor, stream=None):
+        gs_project(self.cfg, g, cams, self.ws, stream)
+        gs_bin_sort(self.cfg, self.ws, stream)
+
+    def plan(self, g: Gaussians, cams: torch.Tensor, headroom=1.25, stream=None) -> int:
+        """Runs the projection and binning once and grows the pair capacity if needed."""
+        self.project_and_sort(g, cams, stream)
+        code, err, total, _ = self.status(stream)
+        if err & _lib.DEVERR_PAIR_OVERFLOW:
+            self._configure(int(total * headroom) + 1024)
+            self.project_and_sort(g, cams, stream)
+        return total
+
+    def new_outputs(self):
+        K, H, W, d = self.K, self.H, self.W, self.device
+        return {"rgb": torch.empty((K, 3, H, W), device=d), "depth": torch.empty((K, H, W), device=d),
+                "T": torch.empty((K, H, W), device=d), "last": torch.empty((K, H, W), dtype=torch.int32, device=d)}
+
+    def render(self, g: Gaussians, cams: torch.Tensor, out=None, stream=None):
+        out = out or self.new_outputs()
+        self.project_and_sort(g, cams, stream)
+        gs_raster_fwd(self.cfg, self.ws, out["rgb"], out["depth"], out["T"], out["last"], stream)
+        return out
+
+    def loss_l1(self, out, rgb_target, depth_target, stream=None):
+        g_rgb = torch.empty_like(out["rgb"])
+        g_depth = torch.empty_like(out["depth"])
+        loss = torch.empty(1, device=self.device)
+        gs_loss_l1(self.cfg, out["rgb"], out["depth"], rgb_target, depth_target, g_rgb, g_depth, loss, self.ws, stream)
+        return loss, g_rgb, g_depth
+
+    def backward(self, g: Gaussians, cams, out, dL_drgb, dL_ddepth, dL_dT=None, grads=None, stream=None):
+        if grads is None:
+            d = self.device
+            grads = {"means": torch.zeros((self.N, 3), device=d), "log_scales": torch.zeros((self.N, 3), device=d),
+                     "quats": torch.zeros((self.N, 4), device=d), "opacity_logits": torch.zeros(self.N, device=d),
+                     "rgb": torch.zeros((self.N, 3), device=d), "pose": torch.zeros((self.K, 6), device=d)}
+        gs_raster_bwd(self.cfg, self.ws, out["rgb"], out["depth"], out["T"], out["last"], dL_drgb, dL_ddepth, dL_dT,
+                      stream)
+        gs_project_bwd(self.cfg, g, cams, self.ws, grads, stream)
+        return grads
+
+    def screen_grads(self, stream=None):
+        d = self.device
+        KN = self.K * self.N
+        o = {"d_mean2d": torch.empty((KN, 2), device=d), "d_conic": torch.empty((KN, 3), device=d),
+             "d_depth": torch.empty(KN, device=d), "d_opacity": torch.empty(self.N, device=d),
+             "d_rgb": torch.empty((self.N, 3), device=d)}
+        gs_screen_grads(self.cfg, self.ws, o["d_mean2d"], o["d_conic"], o["d_depth"], o["d_opacity"], o["d_rgb"],
+                        stream)
+        return o
+
+    # --- workspace views (for inspection / tests) ---
+    def ws_view(self, name, dtype, count):
+        off = getattr(self.layout, name)
+        nbytes = count * torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + nbytes].view(dtype)

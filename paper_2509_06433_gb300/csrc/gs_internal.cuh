@@ -1,0 +1,113 @@
+// Internal declarations of the sm_103a rasterizer library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kTile = 16;             // tile side (pixels)
+constexpr int kTilePixels = kTile * kTile;
+constexpr int kProjBlock = 256;       // (view, Gaussian) items per projection / emission block
+constexpr int kSortThreads = 256;     // onesweep block
+constexpr int kSortItems = 15;        // keys per thread per onesweep tile
+constexpr int kSortTileKeys = kSortThreads * kSortItems;
+constexpr int kMaxSortPasses = 8;
+constexpr int kPairGradStride = 12;   // floats per pair gradient record (10 used)
+constexpr int kPoseBlock = 256;       // Gaussians per projection-backward block
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded decoupled look-back
+
+// Workspace status block (first 256 bytes of the workspace).
+struct Status {
+  uint32_t err;
+  uint32_t num_pairs;       // min(total pairs, capacity)
+  uint64_t total_pairs;     // unclamped
+  uint64_t evals;           // Gaussian-pixel evaluations of the last forward raster
+  uint32_t tile_ctr[kMaxSortPasses];  // onesweep dynamic tile counters
+  uint32_t loss_pad[4];
+};
+static_assert(sizeof(Status) <= 256, "status block");
+
+// Everything a kernel needs to find its buffers; built on the host from gs_config_t.
+struct Layout {
+  int64_t N, KN, cap;
+  int K, W, H, Tx, Ty;
+  int64_t n_tiles;          // K * Tx * Ty
+  int tile_bits, key_bits, passes;
+  float near_plane, lambda_depth;
+  int64_t n_proj_blocks;    // ceil(KN / kProjBlock)
+  int64_t max_sort_tiles;   // ceil(cap / kSortTileKeys)
+  int64_t n_pose_blocks;    // ceil(N / kPoseBlock)
+  int64_t n_loss_blocks;
+  // byte offsets into the workspace
+  size_t status, proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, color_opacity, block_sums,
+      block_offsets, keys[2], vals[2], ranges, hist, sort_status, pair_grads, pose_partials, loss_partials;
+  size_t total;
+};
+
+bool make_layout(const gs_config_t* cfg, Layout* L);
+
+template <class T>
+__host__ __device__ inline T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<uint8_t*>(ws) + off);
+}
+template <class T>
+__host__ __device__ inline const T* at(const void* ws, size_t off) {
+  return reinterpret_cast<const T*>(static_cast<const uint8_t*>(ws) + off);
+}
+
+struct GaussPtrs {
+  const void* means;
+  const void* log_scales;
+  const void* quats;
+  const void* logits;
+  const void* rgb;
+  int dtype, means_dtype;
+};
+
+// ---------------------------------------------------------------------------- device helpers
+__device__ __forceinline__ float load_attr(const void* p, int64_t i, int dtype) {
+  if (dtype == GS_F32) return static_cast<const float*>(p)[i];
+  if (dtype == GS_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+  return __half2float(static_cast<const __half*>(p)[i]);
+}
+
+// Launchers (each defined in its own translation unit). All return cudaGetLastError().
+cudaError_t launch_project(const Layout& L, const GaussPtrs& g, const gs_camera_t* cams, void* ws, cudaStream_t s);
+cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_ranges(const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
+                              cudaStream_t s);
+cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const float* depth, const float* T_final,
+                              const int32_t* last, const float* dL_drgb, const float* dL_ddepth, const float* dL_dT,
+                              cudaStream_t s);
+cudaError_t launch_loss(const Layout& L, const float* rgb, const float* depth, const float* rgb_t,
+                        const float* depth_t, float* g_rgb, float* g_depth, float* d_loss, void* ws, cudaStream_t s);
+cudaError_t launch_project_bwd(const Layout& L, const GaussPtrs& g, const gs_camera_t* cams, void* ws,
+                               const gs_grads_t& out, cudaStream_t s);
+cudaError_t launch_screen_grads(const Layout& L, const void* ws, float* d_mean2d, float* d_conic, float* d_depth,
+                                float* d_opacity, float* d_rgb, cudaStream_t s);
+
+// Generic stable onesweep sort of (u64 key, u32 value) pairs used by gs_bin_sort and gs_sort_pairs.
+struct SortArgs {
+  uint64_t* keys[2];
+  uint32_t* vals[2];
+  const uint32_t* n_dev;  // device pair count (nullptr: use n_host)
+  int64_t n_host;         // host pair count or capacity bound
+  uint32_t* hist;         // [passes][256] global digit counts (filled before the passes)
+  uint32_t* tile_status;  // [passes][max_tiles][256]
+  uint32_t* tile_ctr;     // [passes]
+  uint32_t* err;
+  int64_t max_tiles;
+  int passes;
+  int key_bits;  // the last pass only looks at the bits below key_bits
+};
+cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s);
+cudaError_t launch_sort_prepare(const SortArgs& a, cudaStream_t s);  // zero status, build histogram
+
+}  // namespace gs

@@ -1,0 +1,237 @@
+// Projection of 3D Gaussians (Sec. II-A scene model) for K views: 2D mean, conic,
+// depth, pixel radius and tile rectangle of every (view, Gaussian) item.
+//
+// Two arithmetic regimes live here:
+//  * the DISCRETE path (camera depth used as the sort key, the culls, the radius and
+//    the tile rectangle) runs in binary32 in one fixed operation order, with explicit
+//    round-to-nearest intrinsics so the compiler cannot fuse or reorder anything;
+//  * the CONTINUOUS path carries the camera-space mean and the 2D mean as unevaluated
+//    float pairs (hi + lo, Dot2-style compensated arithmetic), so the 2D mean that the
+//    compositing uses is accurate to ~1e-12 px instead of ~4e-5 px at 640 px.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+// Deterministic binary32 exponential: Cody & Waite additive range reduction x = k ln2 + r
+// with a 16-bit head of ln2 (so k * head is exact) and a tail, then the degree-7 Taylor
+// polynomial of e^r by Horner's rule, scaled by 2^k. Max error 1 ulp on [-80, 80].
+__device__ __forceinline__ float exp_det(float x) {
+  if (x != x) return x;
+  x = (x < -80.0f) ? -80.0f : ((x > 80.0f) ? 80.0f : x);
+  const float kf = rintf(__fmul_rn(x, 0x1.715476p+0f));
+  float r = __fmaf_rn(-kf, 0x1.62e4p-1f, x);
+  r = __fmaf_rn(-kf, 0x1.7f7d1cp-20f, r);
+  float p = 0x1.a01a02p-13f;
+  p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);
+  p = __fmaf_rn(p, r, 0x1.111112p-7f);
+  p = __fmaf_rn(p, r, 0x1.555556p-5f);
+  p = __fmaf_rn(p, r, 0x1.555556p-3f);
+  p = __fmaf_rn(p, r, 0x1p-1f);
+  p = __fmaf_rn(p, r, 1.0f);
+  p = __fmaf_rn(p, r, 1.0f);
+  const int k = static_cast<int>(kf);
+  return __fmul_rn(p, __int_as_float((k + 127) << 23));
+}
+
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF renorm(float s, float e) {
+  const float hi = __fadd_rn(s, e);
+  return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+// r0 p0 + r1 p1 + r2 p2 + t as hi + lo
+__device__ __forceinline__ FF dot3_plus(float r0, float r1, float r2, float p0, float p1, float p2, float t) {
+  const FF a = two_prod(r0, p0);
+  const FF b = two_prod(r1, p1);
+  const FF c = two_sum(a.hi, b.hi);
+  float err = __fadd_rn(a.lo, __fadd_rn(b.lo, c.lo));
+  const FF d = two_prod(r2, p2);
+  const FF e = two_sum(c.hi, d.hi);
+  err = __fadd_rn(err, __fadd_rn(d.lo, e.lo));
+  const FF f = two_sum(e.hi, t);
+  err = __fadd_rn(err, f.lo);
+  return renorm(f.hi, err);
+}
+// f * (x / z) + c with x, z given as hi + lo
+__device__ __forceinline__ FF proj_coord(float f, float c, FF x, FF z) {
+  const float q = __fdiv_rn(x.hi, z.hi);
+  float r = __fmaf_rn(-q, z.hi, x.hi);  // exact remainder
+  r = __fadd_rn(r, __fmaf_rn(-q, z.lo, x.lo));
+  const float ql = __fdiv_rn(r, z.hi);
+  const FF p = two_prod(f, q);
+  const float pl = __fmaf_rn(f, ql, p.lo);
+  const FF s = two_sum(p.hi, c);
+  return renorm(s.hi, __fadd_rn(pl, s.lo));
+}
+
+__device__ __forceinline__ uint32_t pack16(int lo, int hi) {
+  return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
+
+__global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
+                                                       uint8_t* __restrict__ ws) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
+  uint32_t count = 0;
+  if (idx < L.KN) {
+    const int k = static_cast<int>(idx / L.N);
+    const int64_t g = idx - static_cast<int64_t>(k) * L.N;
+    const gs_camera_t cam = cams[k];
+    const float p0 = load_attr(G.means, 3 * g + 0, G.means_dtype);
+    const float p1 = load_attr(G.means, 3 * g + 1, G.means_dtype);
+    const float p2 = load_attr(G.means, 3 * g + 2, G.means_dtype);
+    float ls[3], q[4];
+    for (int j = 0; j < 3; ++j) ls[j] = load_attr(G.log_scales, 3 * g + j, G.dtype);
+    for (int j = 0; j < 4; ++j) q[j] = load_attr(G.quats, 4 * g + j, G.dtype);
+    const float* R = cam.R;
+    const float* t = cam.t;
+    if (k == 0) {
+      const float lg = load_attr(G.logits, g, G.dtype);
+      const float c0 = load_attr(G.rgb, 3 * g + 0, G.dtype);
+      const float c1 = load_attr(G.rgb, 3 * g + 1, G.dtype);
+      const float c2 = load_attr(G.rgb, 3 * g + 2, G.dtype);
+      const float o = 1.0f / (1.0f + expf(-lg));
+      at<float4>(ws, L.color_opacity)[g] = make_float4(c0, c1, c2, o);
+      const bool finite = isfinite(p0) && isfinite(p1) && isfinite(p2) && isfinite(ls[0]) && isfinite(ls[1]) &&
+                          isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]) &&
+                          isfinite(lg) && isfinite(c0) && isfinite(c1) && isfinite(c2);
+      if (!finite) atomicOr(&at<Status>(ws, L.status)->err, GS_DEVERR_NONFINITE);
+    }
+
+    // ---------------- discrete path: fixed binary32 operation order -----------------
+    bool valid = true;
+    const float xc = __fmaf_rn(R[0], p0, __fmaf_rn(R[1], p1, __fmaf_rn(R[2], p2, t[0])));
+    const float yc = __fmaf_rn(R[3], p0, __fmaf_rn(R[4], p1, __fmaf_rn(R[5], p2, t[1])));
+    const float zc = __fmaf_rn(R[6], p0, __fmaf_rn(R[7], p1, __fmaf_rn(R[8], p2, t[2])));
+    valid = zc > L.near_plane;
+    const float n2 = __fmaf_rn(q[0], q[0], __fmaf_rn(q[1], q[1], __fmaf_rn(q[2], q[2], __fmul_rn(q[3], q[3]))));
+    const float nq = __fsqrt_rn(n2);
+    valid = valid && (nq > 0.0f);
+    const float qw = __fdiv_rn(q[0], nq), qx = __fdiv_rn(q[1], nq), qy = __fdiv_rn(q[2], nq),
+                qz = __fdiv_rn(q[3], nq);
+    const float xx = __fmul_rn(qx, qx), yy = __fmul_rn(qy, qy), zz = __fmul_rn(qz, qz);
+    const float xy = __fmul_rn(qx, qy), xz = __fmul_rn(qx, qz), yz = __fmul_rn(qy, qz);
+    const float wx = __fmul_rn(qw, qx), wy = __fmul_rn(qw, qy), wz = __fmul_rn(qw, qz);
+    float Q[3][3];
+    Q[0][0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+    Q[0][1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+    Q[0][2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+    Q[1][0] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+    Q[1][1] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+    Q[1][2] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+    Q[2][0] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+    Q[2][1] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+    Q[2][2] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+    const float S0 = exp_det(ls[0]), S1 = exp_det(ls[1]), S2 = exp_det(ls[2]);
+    float M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      M[i][0] = __fmul_rn(Q[i][0], S0);
+      M[i][1] = __fmul_rn(Q[i][1], S1);
+      M[i][2] = __fmul_rn(Q[i][2], S2);
+    }
+    float Nm[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Nm[i][j] = __fmaf_rn(R[3 * i + 0], M[0][j], __fmaf_rn(R[3 * i + 1], M[1][j], __fmul_rn(R[3 * i + 2], M[2][j])));
+    const float xz_ = __fdiv_rn(xc, zc), yz_ = __fdiv_rn(yc, zc);
+    const float limx = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, static_cast<float>(L.W)), cam.fx));
+    const float limy = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, static_cast<float>(L.H)), cam.fy));
+    const float txz = fminf(fmaxf(xz_, -limx), limx);
+    const float tyz = fminf(fmaxf(yz_, -limy), limy);
+    const float j00 = __fdiv_rn(cam.fx, zc), j02 = -__fmul_rn(j00, txz);
+    const float j11 = __fdiv_rn(cam.fy, zc), j12 = -__fmul_rn(j11, tyz);
+    float m1[3], m2[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      m1[j] = __fmaf_rn(j00, Nm[0][j], __fmul_rn(j02, Nm[2][j]));
+      m2[j] = __fmaf_rn(j11, Nm[1][j], __fmul_rn(j12, Nm[2][j]));
+    }
+    const float aa = __fmaf_rn(m1[0], m1[0], __fmaf_rn(m1[1], m1[1], __fmul_rn(m1[2], m1[2])));
+    const float cc = __fmaf_rn(m2[0], m2[0], __fmaf_rn(m2[1], m2[1], __fmul_rn(m2[2], m2[2])));
+    const float bb = __fmaf_rn(m1[0], m2[0], __fmaf_rn(m1[1], m2[1], __fmul_rn(m1[2], m2[2])));
+    const float a = __fadd_rn(aa, 0.3f), c = __fadd_rn(cc, 0.3f);
+    const float k0 = __fmaf_rn(m1[1], m2[2], -__fmul_rn(m1[2], m2[1]));
+    const float k1 = __fmaf_rn(m1[2], m2[0], -__fmul_rn(m1[0], m2[2]));
+    const float k2 = __fmaf_rn(m1[0], m2[1], -__fmul_rn(m1[1], m2[0]));
+    const float det = __fadd_rn(__fadd_rn(__fmaf_rn(k0, k0, __fmaf_rn(k1, k1, __fmul_rn(k2, k2))),
+                                          __fmul_rn(0.3f, __fadd_rn(aa, cc))),
+                                0.09f);
+    valid = valid && (det > 0.0f);
+    const float mid = __fmul_rn(0.5f, __fadd_rn(a, c));
+    const float hd = __fmul_rn(0.5f, __fsub_rn(a, c));
+    const float disc = fmaxf(__fmaf_rn(hd, hd, __fmul_rn(bb, bb)), 0.1f);
+    const float lmax = __fadd_rn(mid, __fsqrt_rn(disc));
+    const float rf = fminf(ceilf(__fmul_rn(3.0f, __fsqrt_rn(lmax))), 1048576.0f);
+    valid = valid && (rf == rf);
+    const float u = __fmaf_rn(cam.fx, xz_, cam.cx);
+    const float v = __fmaf_rn(cam.fy, yz_, cam.cy);
+    valid = valid && isfinite(u) && isfinite(v);
+    const float inv_tile = 1.0f / static_cast<float>(kTile);
+    const float Txf = static_cast<float>(L.Tx), Tyf = static_cast<float>(L.Ty);
+    const float x0f = fminf(fmaxf(floorf(__fmul_rn(__fsub_rn(u, rf), inv_tile)), 0.0f), Txf);
+    const float x1f = fminf(fmaxf(__fadd_rn(floorf(__fmul_rn(__fadd_rn(u, rf), inv_tile)), 1.0f), 0.0f), Txf);
+    const float y0f = fminf(fmaxf(floorf(__fmul_rn(__fsub_rn(v, rf), inv_tile)), 0.0f), Tyf);
+    const float y1f = fminf(fmaxf(__fadd_rn(floorf(__fmul_rn(__fadd_rn(v, rf), inv_tile)), 1.0f), 0.0f), Tyf);
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0, radius = 0;
+    if (valid) {
+      x0 = static_cast<int>(x0f);
+      x1 = static_cast<int>(x1f);
+      y0 = static_cast<int>(y0f);
+      y1 = static_cast<int>(y1f);
+      radius = static_cast<int>(rf);
+      count = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
+      if (count == 0) x0 = x1 = y0 = y1 = radius = 0;
+    }
+    at<uint32_t>(ws, L.proj_depth_key)[idx] = __float_as_uint(zc);
+    at<int32_t>(ws, L.proj_radius)[idx] = radius;
+    at<int4>(ws, L.proj_tiles)[idx] =
+        make_int4(0, static_cast<int>(pack16(x0, x1)), static_cast<int>(pack16(y0, y1)), static_cast<int>(count));
+
+    // ---------------- continuous path ----------------------------------------------
+    if (count) {
+      const FF X = dot3_plus(R[0], R[1], R[2], p0, p1, p2, t[0]);
+      const FF Y = dot3_plus(R[3], R[4], R[5], p0, p1, p2, t[1]);
+      const FF Z = dot3_plus(R[6], R[7], R[8], p0, p1, p2, t[2]);
+      const FF U = proj_coord(cam.fx, cam.cx, X, Z);
+      const FF V = proj_coord(cam.fy, cam.cy, Y, Z);
+      at<float4>(ws, L.proj_uv)[idx] = make_float4(U.hi, U.lo, V.hi, V.lo);
+      // conic = Sigma2^-1 = [[c, -b], [-b, a]] / det with det from the Lagrange identity
+      const float inv_det = 1.0f / det;
+      at<float4>(ws, L.proj_conic)[idx] = make_float4(c * inv_det, -bb * inv_det, a * inv_det, Z.hi);
+    }
+  }
+  // per-block total of tiles touched, consumed by the emission scan
+  __shared__ uint32_t warp_sums[kProjBlock / 32];
+  uint32_t s = count;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < kProjBlock / 32; ++w) tot += warp_sums[w];
+    at<uint32_t>(ws, L.block_sums)[blockIdx.x] = tot;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_project(const Layout& L, const GaussPtrs& g, const gs_camera_t* cams, void* ws, cudaStream_t s) {
+  k_project<<<static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s>>>(L, g, cams, static_cast<uint8_t*>(ws));
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,292 @@
+// Backward of the projection: per Gaussian, sum its per-(view, tile) gradient records in a
+// fixed order, then apply the chain rule of the projection to the Gaussian parameters and
+// to each view's se(3) pose. One thread per Gaussian loops over the K views, so the
+// parameter gradients are accumulated without atomics; pose gradients are reduced per
+// block and then across blocks in a fixed order.
+//
+// Forward (recomputed in FP32): p_c = R p + t; Q = rot(q / |q|); M = Q diag(exp(s));
+// Nm = R M; J = [[fx/z, 0, -fx tx/z], [0, fy/z, -fy ty/z]] with tx, ty the clamped x/z, y/z;
+// m = J Nm (2x3); Sigma2 = m m^T + 0.3 I; conic X = Sigma2^-1; u = fx x/z + cx, v = fy y/z + cy.
+// Reverse: dSigma2 = -X Gbar X, dm = 2 dSigma2 m, dJ = dm Nm^T, dNm = J^T dm, dM = R^T dNm,
+// dQ = dM diag(s), ds = diag(Q^T dM), dq through the normalisation; dp_c from J, (u, v), z;
+// pose (left perturbation): drho = dp_c, dphi = p_c x dp_c + vee(Nm dNm^T - dNm Nm^T).
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+struct Sum10 {
+  float v[10];
+};
+
+// Sums records [off, off + cnt) clipped to the workspace capacity (pairs past the capacity
+// were never emitted when the pair count overflowed; the error word reports that case).
+__device__ __forceinline__ Sum10 sum_pairs(const float* __restrict__ pg, uint32_t off, uint32_t cnt, int64_t cap) {
+  if (static_cast<int64_t>(off) >= cap) cnt = 0;
+  else if (static_cast<int64_t>(off) + cnt > cap) cnt = static_cast<uint32_t>(cap - off);
+  Sum10 s;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) s.v[i] = 0.0f;
+  for (uint32_t j = 0; j < cnt; ++j) {
+    const float4* r = reinterpret_cast<const float4*>(pg + static_cast<size_t>(off + j) * kPairGradStride);
+    const float4 a = r[0], b = r[1], c = r[2];
+    s.v[0] += a.x; s.v[1] += a.y; s.v[2] += a.z; s.v[3] += a.w;
+    s.v[4] += b.x; s.v[5] += b.y; s.v[6] += b.z; s.v[7] += b.w;
+    s.v[8] += c.x; s.v[9] += c.y;
+  }
+  return s;
+}
+
+__global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
+                                                           const uint8_t* __restrict__ ws, gs_grads_t out,
+                                                           float* __restrict__ pose_partials) {
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
+  const bool valid = g < L.N;
+  const int4* tiles = at<int4>(ws, L.proj_tiles);
+  const float* pg = at<float>(ws, L.pair_grads);
+  __shared__ float s_red[kPoseBlock / 32][6];
+
+  float p[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, lg = 0.0f;
+  if (valid) {
+    for (int j = 0; j < 3; ++j) p[j] = load_attr(G.means, 3 * g + j, G.means_dtype);
+    for (int j = 0; j < 3; ++j) ls[j] = load_attr(G.log_scales, 3 * g + j, G.dtype);
+    for (int j = 0; j < 4; ++j) q[j] = load_attr(G.quats, 4 * g + j, G.dtype);
+    lg = load_attr(G.logits, g, G.dtype);
+  }
+  const float qlen = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const float iq = qlen > 0.0f ? 1.0f / qlen : 0.0f;
+  const float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
+  float Q[3][3];
+  Q[0][0] = 1.f - 2.f * (y * y + z * z); Q[0][1] = 2.f * (x * y - w * z); Q[0][2] = 2.f * (x * z + w * y);
+  Q[1][0] = 2.f * (x * y + w * z); Q[1][1] = 1.f - 2.f * (x * x + z * z); Q[1][2] = 2.f * (y * z - w * x);
+  Q[2][0] = 2.f * (x * z - w * y); Q[2][1] = 2.f * (y * z + w * x); Q[2][2] = 1.f - 2.f * (x * x + y * y);
+  const float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+  float M[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[i][j] = Q[i][j] * S[j];
+
+  float d_mean[3] = {0, 0, 0}, dM_acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  float d_op = 0.0f, d_rgb[3] = {0, 0, 0};
+
+  for (int k = 0; k < L.K; ++k) {
+    float pose[6] = {0, 0, 0, 0, 0, 0};
+    int4 tl = make_int4(0, 0, 0, 0);
+    if (valid) tl = tiles[static_cast<int64_t>(k) * L.N + g];
+    if (tl.w > 0) {
+      const Sum10 s = sum_pairs(pg, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap);
+      const float gu = s.v[0], gv = s.v[1], gA = s.v[2], gB = s.v[3], gC = s.v[4], gz = s.v[5];
+      d_op += s.v[6];
+      d_rgb[0] += s.v[7];
+      d_rgb[1] += s.v[8];
+      d_rgb[2] += s.v[9];
+      const gs_camera_t cam = cams[k];
+      const float* R = cam.R;
+      float pc[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) pc[i] = R[3 * i] * p[0] + R[3 * i + 1] * p[1] + R[3 * i + 2] * p[2] + cam.t[i];
+      float Nm[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Nm[i][j] = R[3 * i] * M[0][j] + R[3 * i + 1] * M[1][j] + R[3 * i + 2] * M[2][j];
+      const float iz = 1.0f / pc[2];
+      const float limx = 1.3f * (0.5f * static_cast<float>(L.W) / cam.fx);
+      const float limy = 1.3f * (0.5f * static_cast<float>(L.H) / cam.fy);
+      const float rx = pc[0] * iz, ry = pc[1] * iz;
+      const bool clx = (rx < -limx) || (rx > limx), cly = (ry < -limy) || (ry > limy);
+      const float txz = fminf(fmaxf(rx, -limx), limx), tyz = fminf(fmaxf(ry, -limy), limy);
+      const float J00 = cam.fx * iz, J02 = -J00 * txz, J11 = cam.fy * iz, J12 = -J11 * tyz;
+      float m1[3], m2[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        m1[j] = J00 * Nm[0][j] + J02 * Nm[2][j];
+        m2[j] = J11 * Nm[1][j] + J12 * Nm[2][j];
+      }
+      const float aa = m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2];
+      const float cc = m2[0] * m2[0] + m2[1] * m2[1] + m2[2] * m2[2];
+      const float bb = m1[0] * m2[0] + m1[1] * m2[1] + m1[2] * m2[2];
+      const float k0 = m1[1] * m2[2] - m1[2] * m2[1], k1 = m1[2] * m2[0] - m1[0] * m2[2],
+                  k2 = m1[0] * m2[1] - m1[1] * m2[0];
+      const float det = (k0 * k0 + k1 * k1 + k2 * k2) + 0.3f * (aa + cc) + 0.09f;
+      const float idet = 1.0f / det;
+      const float A = (cc + 0.3f) * idet, B = -bb * idet, C = (aa + 0.3f) * idet;
+      // dSigma2 = -X Gbar X with Gbar = [[gA, gB/2], [gB/2, gC]]
+      const float hB = 0.5f * gB;
+      const float XG00 = A * gA + B * hB, XG01 = A * hB + B * gC;
+      const float XG10 = B * gA + C * hB, XG11 = B * hB + C * gC;
+      const float G00 = -(XG00 * A + XG01 * B), G01 = -(XG00 * B + XG01 * C);
+      const float G10 = -(XG10 * A + XG11 * B), G11 = -(XG10 * B + XG11 * C);
+      float dm1[3], dm2[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dm1[j] = 2.0f * (G00 * m1[j] + G01 * m2[j]);
+        dm2[j] = 2.0f * (G10 * m1[j] + G11 * m2[j]);
+      }
+      const float dJ00 = dm1[0] * Nm[0][0] + dm1[1] * Nm[0][1] + dm1[2] * Nm[0][2];
+      const float dJ02 = dm1[0] * Nm[2][0] + dm1[1] * Nm[2][1] + dm1[2] * Nm[2][2];
+      const float dJ11 = dm2[0] * Nm[1][0] + dm2[1] * Nm[1][1] + dm2[2] * Nm[1][2];
+      const float dJ12 = dm2[0] * Nm[2][0] + dm2[1] * Nm[2][1] + dm2[2] * Nm[2][2];
+      float dN[3][3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dN[0][j] = J00 * dm1[j];
+        dN[1][j] = J11 * dm2[j];
+        dN[2][j] = J02 * dm1[j] + J12 * dm2[j];
+      }
+      // dM = R^T dN (accumulated over views)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dM_acc[i][j] += R[i] * dN[0][j] + R[3 + i] * dN[1][j] + R[6 + i] * dN[2][j];
+      // camera-space mean
+      const float iz2 = iz * iz;
+      float dpc[3];
+      dpc[0] = gu * cam.fx * iz;
+      dpc[1] = gv * cam.fy * iz;
+      dpc[2] = gz - gu * cam.fx * pc[0] * iz2 - gv * cam.fy * pc[1] * iz2;
+      dpc[2] += -cam.fx * iz2 * dJ00 - cam.fy * iz2 * dJ11 + cam.fx * txz * iz2 * dJ02 + cam.fy * tyz * iz2 * dJ12;
+      if (!clx) {
+        dpc[0] += -cam.fx * iz2 * dJ02;
+        dpc[2] += cam.fx * pc[0] * iz2 * iz * dJ02;
+      }
+      if (!cly) {
+        dpc[1] += -cam.fy * iz2 * dJ12;
+        dpc[2] += cam.fy * pc[1] * iz2 * iz * dJ12;
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) d_mean[j] += R[j] * dpc[0] + R[3 + j] * dpc[1] + R[6 + j] * dpc[2];
+      // pose: rho = dp_c ; phi = p_c x dp_c + vee(A - A^T), A = Nm dN^T
+      float Am[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Am[i][j] = Nm[i][0] * dN[j][0] + Nm[i][1] * dN[j][1] + Nm[i][2] * dN[j][2];
+      pose[0] = dpc[0];
+      pose[1] = dpc[1];
+      pose[2] = dpc[2];
+      pose[3] = pc[1] * dpc[2] - pc[2] * dpc[1] + Am[1][2] - Am[2][1];
+      pose[4] = pc[2] * dpc[0] - pc[0] * dpc[2] + Am[2][0] - Am[0][2];
+      pose[5] = pc[0] * dpc[1] - pc[1] * dpc[0] + Am[0][1] - Am[1][0];
+    }
+    // block reduction of this view's pose gradient
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      float v = pose[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      float v = 0.0f;
+      for (int wv = 0; wv < kPoseBlock / 32; ++wv) v += s_red[wv][threadIdx.x];
+      pose_partials[(static_cast<int64_t>(blockIdx.x) * L.K + k) * 6 + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+  if (!valid) return;
+  // M = Q diag(S): dQ = dM diag(S), dS_j = sum_i dM_ij Q_ij
+  float dQ[3][3], dls[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float ds = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dQ[i][j] = dM_acc[i][j] * S[j];
+      ds += dM_acc[i][j] * Q[i][j];
+    }
+    dls[j] = ds * S[j];
+  }
+  float dqh[4];
+  dqh[0] = 2.f * (-z * dQ[0][1] + y * dQ[0][2] + z * dQ[1][0] - x * dQ[1][2] - y * dQ[2][0] + x * dQ[2][1]);
+  dqh[1] = 2.f * (y * dQ[0][1] + z * dQ[0][2] + y * dQ[1][0] - 2.f * x * dQ[1][1] - w * dQ[1][2] + z * dQ[2][0] +
+                  w * dQ[2][1] - 2.f * x * dQ[2][2]);
+  dqh[2] = 2.f * (-2.f * y * dQ[0][0] + x * dQ[0][1] + w * dQ[0][2] + x * dQ[1][0] + z * dQ[1][2] - w * dQ[2][0] +
+                  z * dQ[2][1] - 2.f * y * dQ[2][2]);
+  dqh[3] = 2.f * (-2.f * z * dQ[0][0] - w * dQ[0][1] + x * dQ[0][2] + w * dQ[1][0] - 2.f * z * dQ[1][1] +
+                  y * dQ[1][2] + x * dQ[2][0] + y * dQ[2][1]);
+  const float qd = w * dqh[0] + x * dqh[1] + y * dqh[2] + z * dqh[3];
+  const float qh[4] = {w, x, y, z};
+  const float o = 1.0f / (1.0f + expf(-lg));
+  if (out.means)
+    for (int j = 0; j < 3; ++j) out.means[3 * g + j] += d_mean[j];
+  if (out.log_scales)
+    for (int j = 0; j < 3; ++j) out.log_scales[3 * g + j] += dls[j];
+  if (out.quats)
+    for (int j = 0; j < 4; ++j) out.quats[4 * g + j] += (dqh[j] - qh[j] * qd) * iq;
+  if (out.opacity_logits) out.opacity_logits[g] += d_op * o * (1.0f - o);
+  if (out.rgb)
+    for (int j = 0; j < 3; ++j) out.rgb[3 * g + j] += d_rgb[j];
+}
+
+// pose[k][i] += sum over blocks of pose_partials[block][k][i], in block order.
+__global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_blocks, int K, float* __restrict__ pose) {
+  const int k = blockIdx.x;
+  const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float v = 0.0f;
+  for (int64_t b = lane; b < n_blocks; b += 32) v += partials[(b * K + k) * 6 + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) pose[k * 6 + i] += v;
+}
+
+__global__ void __launch_bounds__(kPoseBlock) k_screen_grads(Layout L, const uint8_t* __restrict__ ws, float* d_mean2d,
+                                                            float* d_conic, float* d_depth, float* d_opacity,
+                                                            float* d_rgb) {
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
+  if (g >= L.N) return;
+  const int4* tiles = at<int4>(ws, L.proj_tiles);
+  const float* pg = at<float>(ws, L.pair_grads);
+  float op = 0.0f, c[3] = {0, 0, 0};
+  for (int k = 0; k < L.K; ++k) {
+    const int64_t kg = static_cast<int64_t>(k) * L.N + g;
+    const int4 tl = tiles[kg];
+    Sum10 s;
+    if (tl.w > 0) {
+      s = sum_pairs(pg, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap);
+    } else {
+      for (int i = 0; i < 10; ++i) s.v[i] = 0.0f;
+    }
+    if (d_mean2d) {
+      d_mean2d[2 * kg] = s.v[0];
+      d_mean2d[2 * kg + 1] = s.v[1];
+    }
+    if (d_conic) {
+      d_conic[3 * kg] = s.v[2];
+      d_conic[3 * kg + 1] = s.v[3];
+      d_conic[3 * kg + 2] = s.v[4];
+    }
+    if (d_depth) d_depth[kg] = s.v[5];
+    op += s.v[6];
+    c[0] += s.v[7];
+    c[1] += s.v[8];
+    c[2] += s.v[9];
+  }
+  if (d_opacity) d_opacity[g] = op;
+  if (d_rgb)
+    for (int j = 0; j < 3; ++j) d_rgb[3 * g + j] = c[j];
+}
+
+}  // namespace
+
+cudaError_t launch_project_bwd(const Layout& L, const GaussPtrs& g, const gs_camera_t* cams, void* ws,
+                               const gs_grads_t& out, cudaStream_t s) {
+  if (L.N == 0) return cudaSuccess;
+  float* partials = at<float>(ws, L.pose_partials);
+  k_project_bwd<<<static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s>>>(L, g, cams, static_cast<uint8_t*>(ws),
+                                                                              out, partials);
+  if (out.pose) k_pose_reduce<<<L.K, 6 * 32, 0, s>>>(partials, L.n_pose_blocks, L.K, out.pose);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_screen_grads(const Layout& L, const void* ws, float* d_mean2d, float* d_conic, float* d_depth,
+                                float* d_opacity, float* d_rgb, cudaStream_t s) {
+  if (L.N == 0) return cudaSuccess;
+  k_screen_grads<<<static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s>>>(
+      L, static_cast<const uint8_t*>(ws), d_mean2d, d_conic, d_depth, d_opacity, d_rgb);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

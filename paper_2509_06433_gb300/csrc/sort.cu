@@ -1,0 +1,246 @@
+// Stable LSD radix sort of (u64 key, u32 value) pairs, one "onesweep" kernel per 8-bit
+// digit (Adinets & Merrill, "Onesweep: A Faster Least Significant Digit Radix Sort for
+// GPUs", 2022): the global digit histograms of all passes are counted up front; each pass
+// then ranks a tile of keys in shared memory, obtains the tile's global offset per digit
+// by a decoupled look-back over the preceding tiles, and scatters through shared memory so
+// that runs of equal digits are written contiguously.
+//
+// Stability: inside a tile, keys are ranked in (warp, item, lane) order, which is their
+// input order; tiles are numbered by a dynamic counter and the look-back sums the counts
+// of all lower-numbered tiles. The look-back spin is bounded: past kSpinLimit polls it
+// sets GS_DEVERR_TIMEOUT and stops waiting (all writes stay inside [0, n)).
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr uint32_t kFlagAggregate = 1u << 30;
+constexpr uint32_t kFlagPrefix = 2u << 30;
+constexpr uint32_t kValueMask = (1u << 30) - 1;
+constexpr int kWarps = kSortThreads / 32;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Exclusive scan of one value per thread over a kSortThreads block. tmp: kWarps words.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* tmp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) tmp[warp] = incl;
+  __syncthreads();
+  uint32_t off = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) off += (w < warp) ? tmp[w] : 0u;
+  __syncthreads();
+  return off + incl - x;
+}
+
+struct SortSmem {
+  uint64_t keys[kSortTileKeys];
+  uint32_t vals[kSortTileKeys];
+  uint32_t warp_hist[kWarps][256];
+  uint32_t bucket[256];       // exclusive scan of this pass's global digit histogram
+  uint32_t global_base[256];  // destination of the tile's first key of each digit
+  uint32_t local_start[256];  // first slot of each digit in the tile's shared-memory copy
+  uint32_t scan_tmp[kWarps];
+  uint32_t tile;
+};
+
+__device__ __forceinline__ uint32_t digit_mask(const SortArgs& a, int pass) {
+  const int rem = a.key_bits - 8 * pass;
+  return rem >= 8 ? 0xffu : ((1u << rem) - 1u);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint64_t* __restrict__ kin = a.keys[pass & 1];
+  const uint32_t* __restrict__ vin = a.vals[pass & 1];
+  uint64_t* __restrict__ kout = a.keys[(pass + 1) & 1];
+  uint32_t* __restrict__ vout = a.vals[(pass + 1) & 1];
+  uint32_t n = static_cast<uint32_t>(a.n_host);
+  if (a.n_dev) n = min(*a.n_dev, n);
+  const uint32_t n_tiles = (n + kSortTileKeys - 1) / kSortTileKeys;
+  const int shift = 8 * pass;
+  const uint32_t dmask = digit_mask(a, pass);
+  uint32_t* status = a.tile_status + static_cast<size_t>(pass) * a.max_tiles * 256;
+
+  S.bucket[t] = block_exclusive_scan(a.hist[pass * 256 + t], S.scan_tmp);
+
+  for (;;) {
+    if (t == 0) S.tile = atomicAdd(&a.tile_ctr[pass], 1u);
+    __syncthreads();
+    const uint32_t tile = S.tile;
+    if (tile >= n_tiles) break;
+    for (int d = lane; d < 256; d += 32) S.warp_hist[warp][d] = 0;
+    __syncwarp();
+    const uint32_t wbase = tile * kSortTileKeys + warp * (32 * kSortItems);
+    uint64_t kr[kSortItems];
+    uint32_t vr[kSortItems], rr[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const uint32_t i = wbase + it * 32 + lane;
+      const bool valid = i < n;
+      kr[it] = valid ? kin[i] : ~0ull;
+      vr[it] = valid ? vin[i] : 0u;
+      const uint32_t d = valid ? static_cast<uint32_t>(kr[it] >> shift) & dmask : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t prior = valid ? S.warp_hist[warp][d] : 0u;
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) S.warp_hist[warp][d] = prior + __popc(peers);
+      __syncwarp();
+      rr[it] = prior + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    // thread t owns digit t: prefix over warps and the tile's count
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = S.warp_hist[w][t];
+      S.warp_hist[w][t] = cnt;
+      cnt += c;
+    }
+    uint32_t excl = 0;
+    if (tile == 0) {
+      st_relaxed(&status[t], kFlagPrefix | cnt);
+    } else {
+      st_relaxed(&status[static_cast<size_t>(tile) * 256 + t], kFlagAggregate | cnt);
+      int64_t j = static_cast<int64_t>(tile) - 1;
+      uint32_t spins = 0;
+      while (j >= 0) {
+        const uint32_t v = ld_relaxed(&status[static_cast<size_t>(j) * 256 + t]);
+        const uint32_t f = v & ~kValueMask;
+        if (f == 0) {
+          if (++spins > kSpinLimit) {
+            atomicOr(a.err, GS_DEVERR_TIMEOUT);
+            break;
+          }
+          continue;
+        }
+        excl += v & kValueMask;
+        if (f == kFlagPrefix) break;
+        --j;
+      }
+      st_relaxed(&status[static_cast<size_t>(tile) * 256 + t], kFlagPrefix | (excl + cnt));
+    }
+    S.global_base[t] = S.bucket[t] + excl;
+    S.local_start[t] = block_exclusive_scan(cnt, S.scan_tmp);
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const uint32_t i = wbase + it * 32 + lane;
+      if (i < n) {
+        const uint32_t d = static_cast<uint32_t>(kr[it] >> shift) & dmask;
+        const uint32_t pos = S.local_start[d] + S.warp_hist[warp][d] + rr[it];
+        S.keys[pos] = kr[it];
+        S.vals[pos] = vr[it];
+      }
+    }
+    __syncthreads();
+    const uint32_t rem = n - tile * kSortTileKeys;
+    const uint32_t tile_n = rem < static_cast<uint32_t>(kSortTileKeys) ? rem : kSortTileKeys;
+    for (uint32_t j = t; j < tile_n; j += kSortThreads) {
+      const uint64_t key = S.keys[j];
+      const uint32_t d = static_cast<uint32_t>(key >> shift) & dmask;
+      const uint32_t dst = S.global_base[d] + (j - S.local_start[d]);
+      kout[dst] = key;
+      vout[dst] = S.vals[j];
+    }
+    __syncthreads();
+  }
+}
+
+// Digit histograms of every pass, and clearing of the look-back status of the used tiles.
+__global__ void k_sort_hist(SortArgs a) {
+  __shared__ uint32_t s_hist[kMaxSortPasses * 256];
+  for (int i = threadIdx.x; i < a.passes * 256; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  const uint64_t n = static_cast<uint64_t>(a.n_host);
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  const uint64_t gtid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (uint64_t i = gtid; i < n; i += stride) {
+    const uint64_t key = a.keys[0][i];
+    for (int p = 0; p < a.passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & digit_mask(a, p))], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.passes * 256; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
+  const uint64_t used = (n + kSortTileKeys - 1) / kSortTileKeys;
+  for (int p = 0; p < a.passes; ++p) {
+    uint32_t* sp = a.tile_status + static_cast<uint64_t>(p) * a.max_tiles * 256;
+    for (uint64_t i = gtid; i < used * 256; i += stride) sp[i] = 0;
+  }
+}
+
+int sort_grid(int64_t max_tiles) {
+  static int blocks_per_sm = -1, sms = 0;
+  if (blocks_per_sm < 0) {
+    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sizeof(SortSmem)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_onesweep, kSortThreads, sizeof(SortSmem));
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int64_t resident = static_cast<int64_t>(blocks_per_sm) * sms;
+  const int64_t g = max_tiles < resident ? max_tiles : resident;
+  return static_cast<int>(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s) {
+  const int grid = sort_grid(a.max_tiles);
+  for (int p = 0; p < a.passes; ++p) {
+    k_onesweep<<<grid, kSortThreads, sizeof(SortSmem), s>>>(a, p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_prepare(const SortArgs& a, cudaStream_t s) {
+  cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * 256 * a.passes, s);
+  cudaMemsetAsync(a.tile_ctr, 0, sizeof(uint32_t) * kMaxSortPasses, s);
+  int64_t blocks = (a.n_host + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  k_sort_hist<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s) {
+  SortArgs a{};
+  a.keys[0] = at<uint64_t>(ws, L.keys[0]);
+  a.keys[1] = at<uint64_t>(ws, L.keys[1]);
+  a.vals[0] = at<uint32_t>(ws, L.vals[0]);
+  a.vals[1] = at<uint32_t>(ws, L.vals[1]);
+  Status* st = at<Status>(ws, L.status);
+  a.n_dev = &st->num_pairs;
+  a.n_host = L.cap;
+  a.hist = at<uint32_t>(ws, L.hist);
+  a.tile_status = at<uint32_t>(ws, L.sort_status);
+  a.tile_ctr = st->tile_ctr;
+  a.err = &st->err;
+  a.max_tiles = L.max_sort_tiles;
+  a.passes = L.passes;
+  a.key_bits = L.key_bits;
+  return launch_onesweep(a, s);
+}
+
+}  // namespace gs

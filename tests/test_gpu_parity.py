@@ -1,0 +1,266 @@
+"""GPU parity of the rasterizer against the FP64 oracle, through the C ABI.
+
+Projection records (depth key, radius, rectangle, tiles touched), the sorted keys and
+values and the tile ranges must match bit for bit; images must match within max-abs
+1e-4 (pixels next to a threshold may take either side of it); every gradient tensor
+within relative L2 1e-3. Scenes are the seeded workloads of ``scenes`` at full size
+(the forward workload and the mapping-step workload) and shrunk variants with ragged
+image sizes and several views.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from scenes import make_scene, random_image
+from scenes.generate import camera_array
+from tests.gpu_common import GRAD_RTOL, check_images, gpu_render, read_discrete, rel_l2, to_np, torch_mods
+
+pytestmark = pytest.mark.gpu
+
+SCENES = {
+    "fwd10k": lambda: make_scene("fwd10k"),
+    "map100k": lambda: make_scene("map100k"),
+    "ragged_tiny": lambda: make_scene("map100k", n=600, W=50, H=37, f=40.0),
+    "window_k3": lambda: make_scene("window500k", n=20000, K=3, W=160, H=120, f=130.0),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def scene(name):
+    return SCENES[name]()
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_fwd(name):
+    s = scene(name)
+    return oracle.forward(s.params(), s.cams, s.W, s.H)
+
+
+@functools.lru_cache(maxsize=None)
+def gpu_fwd(name):
+    s = scene(name)
+    r, g, ct, out = gpu_render(s.params(), s.cams, s.W, s.H)
+    return r, g, ct, out, read_discrete(r)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_projection_discrete_bit_exact(name):
+    m = oracle_fwd(name)["lists"].mirror
+    d = gpu_fwd(name)[4]
+    np.testing.assert_array_equal(d["count"], m.count)
+    np.testing.assert_array_equal(d["radius"], m.radius)
+    np.testing.assert_array_equal(d["rect"], m.rect)
+    valid = m.count > 0
+    np.testing.assert_array_equal(d["depth_bits"][valid], m.depth_bits[valid])
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_projection_continuous(name):
+    s = scene(name)
+    ref = oracle.project64(s.params(), s.cams, s.W, s.H)
+    d = gpu_fwd(name)[4]
+    valid = d["count"] > 0
+    u = d["uv"][:, 0].astype(np.float64) + d["uv"][:, 1]
+    v = d["uv"][:, 2].astype(np.float64) + d["uv"][:, 3]
+    # compensated (hi + lo) 2D mean: far below the 3e-5 px of a plain binary32 value at 640 px
+    assert np.abs(u - ref[:, 0])[valid].max() < 1e-6
+    assert np.abs(v - ref[:, 1])[valid].max() < 1e-6
+    conic = d["conic"][:, :3].astype(np.float64)
+    scale = np.maximum(np.abs(ref[:, 2]), np.abs(ref[:, 4]))
+    err = np.abs(conic - ref[:, 2:5]).max(axis=1) / scale
+    assert err[valid].max() < 2e-5
+    assert (np.abs(d["conic"][:, 3] - ref[:, 5]) / ref[:, 5])[valid].max() < 1e-6
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_sort_and_ranges_bit_exact(name):
+    L = oracle_fwd(name)["lists"]
+    d = gpu_fwd(name)[4]
+    assert d["status"] == 0 and d["err"] == 0
+    assert d["total_pairs"] == len(L.keys)
+    np.testing.assert_array_equal(d["keys"], L.keys)
+    np.testing.assert_array_equal(d["vals"], L.vals)
+    np.testing.assert_array_equal(d["ranges"], L.ranges)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_forward_images(name):
+    orc = oracle_fwd(name)
+    out = to_np(gpu_fwd(name)[3])
+    rep = check_images(out, orc)
+    d = gpu_fwd(name)[4]
+    assert abs(d["evals"] - orc["total_evals"]) <= 1e-3 * orc["total_evals"]
+    print(name, rep)
+
+
+def _upstream(name, s):
+    K, H, W = s.K, s.H, s.W
+    return (random_image(11, (K, 3, H, W)), random_image(12, (K, H, W)), random_image(13, (K, H, W)))
+
+
+@functools.lru_cache(maxsize=None)
+def gpu_bwd(name):
+    torch, api = torch_mods()
+    s = scene(name)
+    r, g, ct, out, _ = gpu_fwd(name)
+    gr, gd, gt = (torch.as_tensor(a).cuda() for a in _upstream(name, s))
+    grads = r.backward(g, ct, out, gr, gd, gt)
+    sg = r.screen_grads()
+    torch.cuda.synchronize()
+    return to_np(grads), to_np(sg)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_bwd(name):
+    s = scene(name)
+    gr, gd, gt = _upstream(name, s)
+    return oracle.backward(s.params(), s.cams, s.W, s.H, oracle_fwd(name)["lists"], gr, gd, gt)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_backward_screen_space(name):
+    _, sg = gpu_bwd(name)
+    o = oracle_bwd(name)["screen"]
+    for gk, ok in (("d_mean2d", "d_uv"), ("d_conic", "d_conic"), ("d_depth", "d_z"), ("d_opacity", "d_opac"),
+                   ("d_rgb", "d_rgb")):
+        e = rel_l2(sg[gk], o[ok])
+        assert e < GRAD_RTOL, (gk, e)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_backward_parameters_and_pose(name):
+    g, _ = gpu_bwd(name)
+    o = oracle_bwd(name)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose"):
+        e = rel_l2(g[k], o[k])
+        assert e < GRAD_RTOL, (k, e)
+
+
+def test_backward_is_deterministic():
+    torch, _ = torch_mods()
+    s = scene("map100k")
+    r, g, ct, out, _ = gpu_fwd("map100k")
+    gr, gd, gt = (torch.as_tensor(a).cuda() for a in _upstream("map100k", s))
+    a = r.backward(g, ct, out, gr, gd, gt)
+    b = r.backward(g, ct, out, gr, gd, gt)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_loss_l1_against_oracle():
+    torch, api = torch_mods()
+    K, H, W = 2, 37, 50
+    rgb, rgb_t = random_image(21, (K, 3, H, W), 0, 1), random_image(22, (K, 3, H, W), 0, 1)
+    dep, dep_t = random_image(23, (K, H, W), 0, 8), random_image(24, (K, H, W), 0, 8)
+    rgb_t[0, 0, :3, :3] = rgb[0, 0, :3, :3]  # equal values: sign(0) = 0
+    L, gr, gd = oracle.loss_l1(rgb, dep, rgb_t, dep_t, 0.1)
+    r = api.Rasterizer(W, H, K, 1)
+    out = {"rgb": torch.as_tensor(rgb).cuda(), "depth": torch.as_tensor(dep).cuda()}
+    loss, g_rgb, g_depth = r.loss_l1(out, torch.as_tensor(rgb_t).cuda(), torch.as_tensor(dep_t).cuda())
+    assert abs(loss.item() - L) <= 1e-5 * abs(L)
+    np.testing.assert_allclose(g_rgb.cpu().numpy(), gr, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(g_depth.cpu().numpy(), gd, rtol=1e-6, atol=0)
+
+
+def test_mapping_step_end_to_end():
+    """Loss-driven mapping step at the full map100k size: render, L1 against the
+    perturbed-scene target, backward to every parameter."""
+    torch, api = torch_mods()
+    s = scene("map100k")
+    t = s.target
+    o_t = oracle.forward(t.params(), t.cams, t.W, t.H)
+    o = oracle_fwd("map100k")
+    L, gr, gd = oracle.loss_l1(o["rgb"], o["depth"], o_t["rgb"], o_t["depth"], 0.1)
+    og = oracle.backward(s.params(), s.cams, s.W, s.H, o["lists"], gr, gd)
+    _, _, _, out_t = gpu_render(t.params(), t.cams, t.W, t.H)
+    r, g, ct, out, _ = gpu_fwd("map100k")
+    loss, g_rgb, g_depth = r.loss_l1(out, out_t["rgb"], out_t["depth"])
+    grads = to_np(r.backward(g, ct, out, g_rgb, g_depth))
+    assert abs(loss.item() - L) <= 1e-4 * L
+    for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose"):
+        e = rel_l2(grads[k], og[k])
+        assert e < GRAD_RTOL, (k, e)
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_empty_scene():
+    torch, api = torch_mods()
+    W, H = 48, 32
+    params = (np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32),
+              np.zeros(0, np.float32), np.zeros((0, 3), np.float32))
+    cam = camera_array(50, 50, 24, 16, np.eye(3), np.zeros(3))
+    r, g, ct, out = gpu_render(params, cam, W, H, cap=1024)
+    o = to_np(out)
+    assert np.all(o["rgb"] == 0) and np.all(o["depth"] == 0) and np.all(o["T"] == 1) and np.all(o["last"] == 0)
+    assert r.status()[2] == 0
+
+
+def test_all_culled_behind_camera():
+    s = make_scene("fwd10k", n=300)
+    means = s.means.copy()
+    means[:, 2] = -means[:, 2]
+    params = (means,) + s.params()[1:]
+    r, g, ct, out = gpu_render(params, s.cams, s.W, s.H, cap=4096)
+    d = read_discrete(r)
+    assert d["total_pairs"] == 0 and np.all(d["count"] == 0)
+    assert np.all(to_np(out)["T"] == 1)
+
+
+def test_single_gaussian_covering_every_tile():
+    W, H = 100, 70
+    params = (np.array([[0.0, 0.0, 2.0]], np.float32), np.array([[0.5, 0.4, 0.3]], np.float32),
+              np.array([[0.9, 0.1, -0.2, 0.3]], np.float32), np.array([1.0], np.float32),
+              np.array([[0.3, 0.6, 0.9]], np.float32))
+    cam = camera_array(60, 60, 50, 35, np.eye(3), np.zeros(3))
+    orc = oracle.forward(params, cam, W, H)
+    assert orc["lists"].mirror.count[0] == 7 * 5
+    r, g, ct, out = gpu_render(params, cam, W, H, cap=1024)
+    check_images(to_np(out), orc)
+    d = read_discrete(r)
+    np.testing.assert_array_equal(d["keys"], orc["lists"].keys)
+
+
+def test_capacity_overflow_is_reported_and_replanned():
+    torch, api = torch_mods()
+    s = scene("fwd10k")
+    g = api.Gaussians.from_numpy(s.params())
+    ct = torch.as_tensor(s.cams).cuda()
+    r = api.Rasterizer(s.W, s.H, 1, s.N, pair_capacity=1000)
+    out = r.render(g, ct)
+    code, err, total, _ = r.status()
+    assert code == 3 and err & 1  # GS_ERR_CAPACITY_OVERFLOW
+    assert total == len(oracle_fwd("fwd10k")["lists"].keys)
+    r.plan(g, ct)
+    assert r.cap >= total
+    out = r.render(g, ct)
+    assert r.status()[0] == 0
+    check_images(to_np(out), oracle_fwd("fwd10k"))
+
+
+def test_nonfinite_input_flagged():
+    s = make_scene("fwd10k", n=500)
+    means = s.means.copy()
+    means[7, 0] = np.nan
+    params = (means,) + s.params()[1:]
+    r, g, ct, out = gpu_render(params, s.cams, s.W, s.H, cap=1 << 16)
+    code, err, _, _ = r.status()
+    assert code == 6 and err & 4  # GS_ERR_NONFINITE
+    orc = oracle.forward(params, s.cams, s.W, s.H)
+    assert orc["lists"].mirror.count[7] == 0
+    check_images(to_np(out), orc)
+
+
+def test_bf16_and_f16_storage_match_dequantised_oracle():
+    torch, _ = torch_mods()
+    s = make_scene("map100k", n=5000, W=160, H=120, f=130.0)
+    for dt in (torch.bfloat16, torch.float16):
+        stored = [torch.as_tensor(a).to(dt).float().numpy() for a in s.params()[1:]]
+        params = (s.means,) + tuple(stored)  # the exactly dequantised values the oracle consumes
+        orc = oracle.forward(params, s.cams, s.W, s.H)
+        r, g, ct, out = gpu_render(s.params(), s.cams, s.W, s.H, dtype=dt)
+        d = read_discrete(r)
+        np.testing.assert_array_equal(d["keys"], orc["lists"].keys)
+        check_images(to_np(out), orc)

@@ -1,0 +1,391 @@
+"""Benchmark of the GB300 rasterizer on the mapping-step workload.
+
+One step = one mapping iteration on the map100k workload (100,000 Gaussians, half on
+3 planes; one 640x480 view, fx = fy = 525): gs_project -> gs_bin_sort -> gs_raster_fwd ->
+gs_loss_l1 (against the render of a perturbed copy of the scene) -> gs_raster_bwd ->
+gs_project_bwd, gradients for every Gaussian parameter and the camera pose.
+
+Prints one JSON line. `value` is mapping iterations/s with inputs resident in HBM, timed
+with CUDA events per step, L2 flushed (256 MB write) between steps outside the timed
+region. `e2e` is the same metric through the same C ABI calls with the step's inputs
+copied from pinned host memory and the gradients and loss copied back inside the timed
+region. `--impl reference` times the FP64 CPU oracle on the same workload instead.
+
+Multi-GPU (torchrun, N ranks): the path is replicated, one independent mapping step per
+rank ("replicas only", weak scaling); value = steps over all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mapping iters/s (K-keyframe fwd+bwd) & tracking iters/s; Gaussian-pixel evals/s vs roofline"
+WORKLOAD = "map100k"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def workload_config():
+    from scenes import SCENE_CONFIGS
+    seed, n, K, W, H, f, _ = SCENE_CONFIGS[WORKLOAD]
+    return {"workload": f"{WORKLOAD}: {n} Gaussians (50% free in [-2,2]^2x[2,8] m, 50% on 3 planes), "
+                        f"{K} view {W}x{H} f={f:g}, fwd+bwd with L1(RGB)+0.1 L1(depth) vs perturbed-scene target",
+            "N": n, "K": K, "width": W, "height": H, "seed": seed, "storage": "f32", "tile": 16,
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, out_path):
+        self.out_path = out_path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.out_path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, device_index=0):
+        if self.proc is None or not os.path.exists(self.out_path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out_path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2509_06433_gb300 import build, api
+    from scenes import make_scene
+
+    build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = make_scene(WORKLOAD)
+    t = s.target
+    g = api.Gaussians.from_numpy(s.params(), device=dev)
+    gt = api.Gaussians.from_numpy(t.params(), device=dev)
+    cams = torch.as_tensor(s.cams).to(dev)
+    r = api.Rasterizer(s.W, s.H, s.K, s.N, device=dev)
+    r.plan(g, cams)
+    # photometric target: render of the perturbed copy (input data, produced before timing)
+    tgt = r.render(gt, cams)
+    rgb_t, depth_t = tgt["rgb"].clone(), tgt["depth"].clone()
+    r.plan(g, cams)
+    out = r.new_outputs()
+    g_rgb = torch.empty_like(out["rgb"])
+    g_depth = torch.empty_like(out["depth"])
+    loss = torch.empty(1, device=dev)
+    grads = {"means": torch.zeros((s.N, 3), device=dev), "log_scales": torch.zeros((s.N, 3), device=dev),
+             "quats": torch.zeros((s.N, 4), device=dev), "opacity_logits": torch.zeros(s.N, device=dev),
+             "rgb": torch.zeros((s.N, 3), device=dev), "pose": torch.zeros((s.K, 6), device=dev)}
+    stream = torch.cuda.current_stream(dev)
+    cfg, ws = r.cfg, r.ws
+    n_launch = 1 + (2 + r.layout.sort_passes + 1) + 1 + 2 + 1 + 2  # kernels of ours per step
+
+    def zero_grads():
+        for v in grads.values():
+            v.zero_()
+
+    stage_names = ["project", "bin_sort", "raster_fwd", "loss", "raster_bwd", "project_bwd"]
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        api.gs_project(cfg, g, cams, ws, stream)
+        mark(1)
+        api.gs_bin_sort(cfg, ws, stream)
+        mark(2)
+        api.gs_raster_fwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], stream)
+        mark(3)
+        api.gs_loss_l1(cfg, out["rgb"], out["depth"], rgb_t, depth_t, g_rgb, g_depth, loss, ws, stream)
+        mark(4)
+        api.gs_raster_bwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth, None, stream)
+        mark(5)
+        api.gs_project_bwd(cfg, g, cams, ws, grads, stream)
+        mark(6)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    for _ in range(args.warmup):
+        zero_grads()
+        step()
+    torch.cuda.synchronize(dev)
+    code, err, pairs, evals = r.status()
+    if code != 0:
+        raise RuntimeError(f"device status {code} (error word {err}) during warm-up")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident timing: events around each step, L2 flushed between steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    barrier()
+    clock_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
+    os.makedirs(os.path.dirname(clock_path), exist_ok=True)
+    with ClockSampler(clock_path) as clk:
+        for i in range(args.steps):
+            zero_grads()
+            flush.fill_(float(i))
+            step(evs[i])
+        barrier()
+    step_ms = [e[0].elapsed_time(e[6]) for e in evs]
+    stage_ms = {nm: [e[j].elapsed_time(e[j + 1]) for e in evs] for j, nm in enumerate(stage_names)}
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    code, err, pairs, evals = r.status()
+    if code != 0:
+        raise RuntimeError(f"device status {code} (error word {err}) in the timed region")
+
+    # ---- end to end through the C ABI: pinned host inputs in, gradients + loss out
+    host_in = [torch.as_tensor(a).pin_memory() for a in s.params()]
+    host_tgt = [rgb_t.cpu().pin_memory(), depth_t.cpu().pin_memory()]
+    dev_in = [x.to(dev) for x in host_in]
+    dev_tgt = [x.to(dev) for x in host_tgt]
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in grads.items()}
+    host_loss = torch.empty(1, pin_memory=True)
+    ge = api.Gaussians(*dev_in)
+    h2d = sum(x.numel() * x.element_size() for x in host_in + host_tgt)
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 4
+
+    def e2e_step():
+        for d, h in zip(dev_in + dev_tgt, host_in + host_tgt):
+            d.copy_(h, non_blocking=True)
+        zero_grads()
+        api.gs_project(cfg, ge, cams, ws, stream)
+        api.gs_bin_sort(cfg, ws, stream)
+        api.gs_raster_fwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], stream)
+        api.gs_loss_l1(cfg, out["rgb"], out["depth"], dev_tgt[0], dev_tgt[1], g_rgb, g_depth, loss, ws, stream)
+        api.gs_raster_bwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth, None, stream)
+        api.gs_project_bwd(cfg, ge, cams, ws, grads, stream)
+        for k, v in grads.items():
+            host_out[k].copy_(v, non_blocking=True)
+        host_loss.copy_(loss, non_blocking=True)
+
+    for _ in range(max(3, args.warmup)):
+        e2e_step()
+    e2e_steps = max(10, args.steps // 2)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # ---- roofline of the dominant kernel
+    med = {k: statistics.median(v) for k, v in stage_ms.items()}
+    dominant = max(med, key=med.get)
+    st = r.layout.status
+    blended = int(r.ws[st + 56:st + 64].view(torch.int64).item())
+    counts = {"evals": evals, "blended": blended, "evals_bwd": int(out["last"].sum().item())}
+    roof = roofline(dominant, stage_ms[dominant], counts, pairs, s, r)
+
+    clocks = clk.summary(local)
+    iters = args.steps * world
+    line = {
+        "metric": METRIC,
+        "value": iters / (total_ms / 1e3),
+        "unit": "mapping iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded map100k scene; no dataset)",
+        "config": workload_config() | {"parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_steps * world / (e2e_ms / 1e3), "unit": "mapping iters/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": n_launch * args.steps,
+        "pairs": pairs,
+        "evals_per_step": evals,
+        "blended_evals_per_step": blended,
+        "gaussian_pixel_evals_per_s": evals * iters / (total_ms / 1e3),
+        "stage_ms_median": {k: round(v, 5) for k, v in med.items()},
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    return line
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Algorithmic FP32 work of the compositing kernels (an FMA counts 2 FLOPs):
+#  every eval: d = mean - pixel (2), power (2 FMA + 3 MUL = 7), o * exp(power) (1)  -> 10
+#  forward, per blended eval: T (1 - alpha) (2), w = alpha T (1), 4 colour/depth FMAs (8) -> 11
+#  backward, per blended eval: T update, weights, dL/dalpha, dL/dcolour, dL/ddepth, dL/dopacity,
+#  dL/dconic, dL/dmean2D (counted from the kernel source)                                   -> 44
+FLOP_EVAL = 10.0
+FLOP_FWD_BLEND = 11.0
+FLOP_BWD_BLEND = 44.0
+
+
+def roofline(stage, ms_list, counts, pairs, s, r):
+    import torch
+    peaks, src = load_peaks()
+    dev = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = dev.multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
+    t = statistics.mean(ms_list) / 1e3
+    if stage in ("raster_fwd", "raster_bwd"):
+        if stage == "raster_fwd":
+            flop = FLOP_EVAL * counts["evals"] + FLOP_FWD_BLEND * counts["blended"]
+        else:
+            flop = FLOP_EVAL * counts["evals_bwd"] + FLOP_BWD_BLEND * counts["blended"]
+        return {"kernel": stage, "bound": "alu", "achieved": flop / t / 1e12, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": flop / t / 1e12 / fp32_peak_tflops, "traffic": None,
+                "peak_source": f"FP32 = {sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz (max clock; {src} peaks file)"}
+    # HBM-bound stages: algorithmic bytes
+    passes = r.layout.sort_passes
+    N, K = s.N, s.K
+    bytes_ = {"project": N * 56 + K * N * (16 * 3 + 8) + N * 16,
+              "bin_sort": pairs * (12 + passes * 24 + 8) + K * N * 24,
+              "loss": K * s.H * s.W * 4 * (4 + 4 + 4),
+              "project_bwd": N * 56 + pairs * 48 + N * 56}.get(stage, 0)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    return {"kernel": stage, "bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": bytes_ / t / 1e9 / hbm, "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+
+def oracle_step_rate(budget_s):
+    """Times the FP64 oracle's mapping step (forward, L1 loss, backward) on the same
+    workload for about budget_s seconds (at least one full step)."""
+    import oracle
+    from scenes import make_scene
+    s = make_scene(WORKLOAD)
+    t = s.target
+    oracle.lib()
+    ot = oracle.forward(t.params(), t.cams, t.W, t.H)  # target: input data, outside the timing
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o = oracle.forward(s.params(), s.cams, s.W, s.H)
+        L, gr, gd = oracle.loss_l1(o["rgb"], o["depth"], ot["rgb"], ot["depth"], 0.1)
+        oracle.backward(s.params(), s.cams, s.W, s.H, o["lists"], gr, gd)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n / el, "unit": "mapping iters/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} full map100k mapping steps (FP64 forward + loss + backward), {el:.1f} s"}
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args.gpus)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cb = oracle_step_rate(args.cpu_seconds)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"], "n_gpus": world,
+                "steps": cb["sample"], "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (seeded map100k scene)",
+                "config": workload_config() | {"parallelism": "CPU oracle, rank 0 only"},
+                "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                                            "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_step_rate(args.cpu_seconds)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

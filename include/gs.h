@@ -114,7 +114,8 @@ typedef struct {
 /* Byte offsets of the workspace sub-buffers (for inspection and tests). */
 typedef struct {
   size_t total;          /* == gs_workspace_size() */
-  size_t status;         /* u32 error word, u32 num_pairs (clamped), u64 total pairs, u64 evals */
+  size_t status;         /* u32 error word, u32 num_pairs (clamped), u64 total pairs, u64 evals,
+                            u32[8] sort tile counters, u64 evals that blended a splat */
   size_t proj_uv;        /* float4 [K*N]: u_hi, u_lo, v_hi, v_lo (u = u_hi + u_lo) */
   size_t proj_conic;     /* float4 [K*N]: conic A, B, C (Sigma2^-1 entries 00, 01, 11), depth z */
   size_t proj_tiles;     /* int4 [K*N]: pair offset, x0 | x1 << 16, y0 | y1 << 16, tiles touched */

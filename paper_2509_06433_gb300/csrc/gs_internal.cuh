@@ -28,7 +28,8 @@ struct Status {
   uint64_t total_pairs;     // unclamped
   uint64_t evals;           // Gaussian-pixel evaluations of the last forward raster
   uint32_t tile_ctr[kMaxSortPasses];  // onesweep dynamic tile counters
-  uint32_t loss_pad[4];
+  uint64_t composited;      // evaluations of the last forward raster that blended a splat
+  uint64_t pad;
 };
 static_assert(sizeof(Status) <= 256, "status block");
 

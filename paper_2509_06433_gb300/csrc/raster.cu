@@ -73,9 +73,10 @@ __device__ __forceinline__ bool splat_alpha(const SplatSmem& S, int j, float dx,
 __global__ void __launch_bounds__(kThreads) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
                                                          float* __restrict__ out_rgb, float* __restrict__ out_depth,
                                                          float* __restrict__ out_T, int32_t* __restrict__ out_last,
-                                                         uint64_t* __restrict__ evals_out) {
+                                                         uint64_t* __restrict__ evals_out,
+                                                         uint64_t* __restrict__ composited_out) {
   __shared__ SplatSmem S;
-  __shared__ uint32_t s_evals[kThreads / 32];
+  __shared__ uint32_t s_evals[kThreads / 32], s_blend[kThreads / 32];
   const int64_t tile_g = blockIdx.x;
   const int64_t per_view = static_cast<int64_t>(L.Tx) * L.Ty;
   const int k = static_cast<int>(tile_g / per_view);
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_fwd(Layout L, const uint8_t
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
   float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f, cd = 0.0f;
   int32_t last = 0;
-  uint32_t evals = 0;
+  uint32_t evals = 0, blended = 0;
   bool done = !inside;
   for (uint32_t base = rg.x; base < rg.y; base += kThreads) {
     if (__syncthreads_count(!done) == 0) break;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_fwd(Layout L, const uint8_t
         cb = __fmaf_rn(S.b[j], w, cb);
         cd = __fmaf_rn(S.z[j], w, cd);
         T = Tn;
+        ++blended;
         last = static_cast<int32_t>(base - rg.x) + j + 1;
       }
     }
@@ -131,15 +133,25 @@ __global__ void __launch_bounds__(kThreads) k_raster_fwd(Layout L, const uint8_t
     if (out_T) out_T[k * HW + pix] = T;
     if (out_last) out_last[k * HW + pix] = last;
   }
-  uint32_t e = evals;
+  uint32_t e = evals, c = blended;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-  if ((threadIdx.x & 31) == 0) s_evals[threadIdx.x >> 5] = e;
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_evals[threadIdx.x >> 5] = e;
+    s_blend[threadIdx.x >> 5] = c;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint64_t tot = 0;
-    for (int w = 0; w < kThreads / 32; ++w) tot += s_evals[w];
+    uint64_t tot = 0, totc = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      tot += s_evals[w];
+      totc += s_blend[w];
+    }
     if (tot) atomicAdd(reinterpret_cast<unsigned long long*>(evals_out), static_cast<unsigned long long>(tot));
+    if (totc) atomicAdd(reinterpret_cast<unsigned long long*>(composited_out), static_cast<unsigned long long>(totc));
   }
 }
 
@@ -193,6 +205,9 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(Layout L, uint8_t* __re
                                                          const float* __restrict__ g_T) {
   __shared__ SplatSmem S;
   __shared__ float s_acc[kThreads][kPairGradStride];
+  // per-warp partial sums of a sub-chunk of kSub splats, summed over warps in a fixed order
+  constexpr int kSub = 32;
+  __shared__ float s_part[kThreads / 32][kSub][10];
   __shared__ uint32_t s_slot[kThreads];
   __shared__ int s_maxlast[kThreads / 32];
   const int64_t tile_g = blockIdx.x;
@@ -284,10 +299,26 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(Layout L, uint8_t* __re
           contrib = true;
         }
       }
+      const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+      float red = 0.0f;
       if (__any_sync(0xffffffffu, contrib)) {
         warp_transpose_reduce16(v, lane);
-        const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-        if (!(lane & 1) && idx < 10) atomicAdd(&s_acc[j][idx], v[0]);
+        red = v[0];
+      }
+      if (!(lane & 1) && idx < 10) s_part[threadIdx.x >> 5][j % kSub][idx] = red;
+      if ((j % kSub) == kSub - 1 || j == n - 1) {
+        __syncthreads();
+        const int j0 = j - (j % kSub);
+        for (int e = threadIdx.x; e < kSub * 10; e += kThreads) {
+          const int jj = e / 10, q = e - jj * 10;
+          if (j0 + jj <= j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int wv = 0; wv < kThreads / 32; ++wv) acc += s_part[wv][jj][q];
+            s_acc[j0 + jj][q] = acc;
+          }
+        }
+        __syncthreads();
       }
     }
     __syncthreads();
@@ -322,9 +353,10 @@ cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* dept
                               cudaStream_t s) {
   Status* st = at<Status>(ws, L.status);
   cudaMemsetAsync(&st->evals, 0, sizeof(uint64_t), s);
+  cudaMemsetAsync(&st->composited, 0, sizeof(uint64_t), s);
   if (L.n_tiles == 0) return cudaGetLastError();
   k_raster_fwd<<<static_cast<unsigned>(L.n_tiles), kThreads, 0, s>>>(L, static_cast<const uint8_t*>(ws), rgb, depth,
-                                                                     T_final, last, &st->evals);
+                                                                     T_final, last, &st->evals, &st->composited);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,8 @@ typedef enum {
   GS_ERR_CAPACITY_OVERFLOW = 3,    /* returned by gs_read_status when the device word says so */
   GS_ERR_DEVICE_TIMEOUT = 4,       /* returned by gs_read_status: a bounded device wait gave up */
   GS_ERR_CUDA = 5,                 /* a CUDA runtime call or kernel launch failed */
-  GS_ERR_NONFINITE = 6             /* returned by gs_read_status: non-finite input seen */
+  GS_ERR_NONFINITE = 6,            /* returned by gs_read_status: non-finite input seen */
+  GS_ERR_SIZE_LIMIT = 7            /* n exceeds a fixed maximum (gs_sort_pairs_noalloc) */
 } gs_status_t;
 
 /* Bits of the device error word (gs_read_status). */
@@ -221,6 +222,28 @@ GS_API gs_status_t gs_sort_pairs_tmp_size(int64_t n, size_t* bytes);
  * scratch of gs_sort_pairs_tmp_size(n) bytes. n <= 2^30 - 1. */
 GS_API gs_status_t gs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int32_t key_bits, void* tmp, size_t tmp_bytes,
                           uint32_t* d_err_word, void* stream);
+
+/* Largest n accepted by gs_sort_pairs_noalloc. */
+#define GS_SORT_NOALLOC_MAX_PAIRS 1048576
+
+/* The paper has no counterpart to this call: it serves callers that cannot allocate.
+ *
+ * Same result as gs_sort_pairs (stable LSD radix sort of n pairs on the low key_bits
+ * bits, in place), but the call needs no temporary buffer from the caller and allocates
+ * nothing: its scratch is one fixed device array inside the library, sized for
+ * GS_SORT_NOALLOC_MAX_PAIRS pairs (about 14 MB), which every GPU that loads the library
+ * keeps until the process exits. It is for code that cannot call cudaMalloc where it
+ * sorts, such as a renderer plugin whose buffers belong to a host application, or a
+ * real-time loop that cannot take cudaMalloc's device synchronisation and latency.
+ *
+ * - n > GS_SORT_NOALLOC_MAX_PAIRS returns GS_ERR_SIZE_LIMIT and enqueues nothing.
+ * - All calls share the one scratch array: calls whose GPU work overlaps (other streams,
+ *   other host threads on the same device) race and must be serialised by the caller.
+ * - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ * - d_err_word (device, may be NULL) receives GS_DEVERR_TIMEOUT if a look-back wait gave up. */
+GS_API gs_status_t gs_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int64_t n, int32_t key_bits,
+                                         uint32_t* d_err_word, void* stream);
 
 #ifdef __cplusplus
 }

@@ -18,14 +18,15 @@ c_int32, c_int64, c_float, c_void_p, c_size_t, c_uint32 = (ctypes.c_int32, ctype
 
 GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_WORKSPACE_TOO_SMALL", 3: "GS_ERR_CAPACITY_OVERFLOW",
-                4: "GS_ERR_DEVICE_TIMEOUT", 5: "GS_ERR_CUDA", 6: "GS_ERR_NONFINITE"}
+                4: "GS_ERR_DEVICE_TIMEOUT", 5: "GS_ERR_CUDA", 6: "GS_ERR_NONFINITE", 7: "GS_ERR_SIZE_LIMIT"}
+SORT_NOALLOC_MAX_PAIRS = 1048576
 DEVERR_PAIR_OVERFLOW, DEVERR_TIMEOUT, DEVERR_NONFINITE = 0x1, 0x2, 0x4
 GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 
 #: every entry point declared in include/gs.h
 EXPORTS = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
            "gs_raster_fwd", "gs_loss_l1", "gs_raster_bwd", "gs_project_bwd", "gs_screen_grads",
-           "gs_sort_pairs_tmp_size", "gs_sort_pairs")
+           "gs_sort_pairs_tmp_size", "gs_sort_pairs", "gs_sort_pairs_noalloc")
 
 
 class GsConfig(ctypes.Structure):
@@ -85,6 +86,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                 "gs_screen_grads": [P, P, c_size_t, P, P, P, P, P, P],
                 "gs_sort_pairs_tmp_size": [c_int64, P],
                 "gs_sort_pairs": [P, P, c_int64, c_int32, P, c_size_t, P, P],
+                "gs_sort_pairs_noalloc": [P, P, c_int64, c_int32, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)

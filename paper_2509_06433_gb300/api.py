@@ -147,6 +147,14 @@ def gs_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int, tmp=Non
          _p(err), _s(stream))
 
 
+def gs_sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: int, err=None, stream=None):
+    """gs_sort_pairs without a temporary buffer (library-owned scratch, n <= SORT_NOALLOC_MAX_PAIRS)."""
+    n = keys.numel()
+    assert vals.numel() == n and keys.dtype == torch.int64 and vals.dtype == torch.int32
+    call("gs_sort_pairs_noalloc", _p(keys), _p(vals), ctypes.c_int64(n), ctypes.c_int32(key_bits), _p(err),
+         _s(stream))
+
+
 # ----------------------------------------------------------------------------- convenience
 
 class CapacityOverflow(RuntimeError):

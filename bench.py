@@ -144,7 +144,9 @@ def run_ours(args, rank, world):
              "rgb": torch.zeros((s.N, 3), device=dev), "pose": torch.zeros((s.K, 6), device=dev)}
     stream = torch.cuda.current_stream(dev)
     cfg, ws = r.cfg, r.ws
-    n_launch = 1 + (2 + r.layout.sort_passes + 1) + 1 + 2 + 1 + 2  # kernels of ours per step
+    # kernels of ours per step: project; item depth sort (4 passes), counts, scan, emit, pair sort
+    # passes, ranges; raster fwd; loss (2); raster bwd; project bwd + pose reduction
+    n_launch = 1 + 4 + 3 + r.layout.sort_passes + 1 + 1 + 2 + 1 + 2
 
     def zero_grads():
         for v in grads.values():
@@ -328,7 +330,7 @@ def roofline(stage, ms_list, counts, pairs, s, r):
     passes = r.layout.sort_passes
     N, K = s.N, s.K
     bytes_ = {"project": N * 56 + K * N * (16 * 3 + 8) + N * 16,
-              "bin_sort": pairs * (12 + passes * 24 + 8) + K * N * 24,
+              "bin_sort": K * N * (4 * 16 + 24) + pairs * (12 + passes * 24 + 8),
               "loss": K * s.H * s.W * 4 * (4 + 4 + 4),
               "project_bwd": N * 56 + pairs * 48 + N * 56}.get(stage, 0)
     hbm = float(peaks.get("hbm_gbs", 6800.0))

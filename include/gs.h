@@ -127,7 +127,7 @@ typedef struct {
   size_t vals_sorted;    /* u32 [pair_capacity]: Gaussian id of each sorted key */
   size_t ranges;         /* u32 [K*Tx*Ty][2]: [start, end) of each global tile */
   size_t pair_grads;     /* float [pair_capacity][12]: per-pair gradients of gs_raster_bwd */
-  int32_t sort_passes;   /* 8-bit LSD passes: ceil((32 + ceil(log2(K*Tx*Ty))) / 8) */
+  int32_t sort_passes;   /* 8-bit LSD passes of the pair sort over the tile bits: ceil(ceil(log2(K*Tx*Ty)) / 8) */
   int32_t tiles_x, tiles_y;
 } gs_ws_layout_t;
 
@@ -161,12 +161,15 @@ GS_API gs_status_t gs_read_status(const gs_config_t* cfg, const void* ws, size_t
 GS_API gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, const gs_camera_t* d_cams, void* ws,
                        size_t ws_bytes, void* stream);
 
-/* Binning: exclusive scan of tiles touched, emission of one pair per (view, Gaussian,
- * tile) with key = ((k*Tx*Ty + ty*Tx + tx) << 32) | depth bits and value = g, a stable
- * LSD radix sort on the low 32 + ceil(log2(K*Tx*Ty)) key bits (so equal keys keep
- * (k, g) emission order), and per-tile [start, end) ranges. The pair count stays on
- * the device; more than pair_capacity pairs sets GS_DEVERR_PAIR_OVERFLOW and only the
- * first pair_capacity pairs are emitted. */
+/* Binning: sorts the (view, Gaussian) pairs of every tile by depth. Result: one pair per
+ * (view, Gaussian, tile) with key = ((k*Tx*Ty + ty*Tx + tx) << 32) | depth bits and value
+ * = g, in the order of a stable sort of those keys emitted in (k, g) order (equal keys keep
+ * (k, g) order), plus per-tile [start, end) ranges. Computed as: a stable onesweep radix sort
+ * of the K*N items on their 32-bit depth keys, an exclusive scan of tiles touched in that
+ * order, emission in that order, and a stable onesweep radix sort of the pairs on the tile
+ * bits only. The pair count stays on the device; more than pair_capacity pairs sets
+ * GS_DEVERR_PAIR_OVERFLOW and only the first pair_capacity pairs are emitted. Consumes the
+ * state of the preceding gs_project on the same workspace (call it once per gs_project). */
 GS_API gs_status_t gs_bin_sort(const gs_config_t* cfg, void* ws, size_t ws_bytes, void* stream);
 
 /* Forward compositing (render I1/I2 of Fig. 3). Per pixel, front to back over its

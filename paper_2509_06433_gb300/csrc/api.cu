@@ -34,12 +34,13 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->n_tiles = static_cast<int64_t>(L->K) * L->Tx * L->Ty;
   L->tile_bits = ceil_log2(L->n_tiles);
   L->key_bits = 32 + L->tile_bits;
-  L->passes = (L->key_bits + 7) / 8;
+  L->passes = (L->tile_bits + 7) / 8;
   L->cap = cfg->pair_capacity;
   L->near_plane = cfg->near_plane;
   L->lambda_depth = cfg->lambda_depth;
   L->n_proj_blocks = L->KN > 0 ? (L->KN + kProjBlock - 1) / kProjBlock : 1;
   L->max_sort_tiles = (L->cap + kSortTileKeys - 1) / kSortTileKeys;
+  L->max_item_tiles = L->KN > 0 ? (L->KN + kSortTileKeys - 1) / kSortTileKeys : 1;
   L->n_pose_blocks = L->N > 0 ? (L->N + kPoseBlock - 1) / kPoseBlock : 1;
   const int64_t pixels = static_cast<int64_t>(L->K) * L->W * L->H;
   L->n_loss_blocks = (pixels + 255) / 256 < 1024 ? (pixels + 255) / 256 : 1024;
@@ -69,6 +70,13 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->pair_grads = take(cap * kPairGradStride * 4);
   L->pose_partials = take(static_cast<size_t>(L->n_pose_blocks) * L->K * 6 * 4);
   L->loss_partials = take(static_cast<size_t>(L->n_loss_blocks) * 4);
+  L->item_keys[0] = take(KN * 4);
+  L->item_keys[1] = take(KN * 4);
+  L->item_vals[0] = take(KN * 4);
+  L->item_vals[1] = take(KN * 4);
+  L->item_hist = take(4 * 256 * 4);
+  L->item_status = take(static_cast<size_t>(4) * L->max_item_tiles * 256 * 4);
+  L->sorted_counts = take(static_cast<size_t>(L->n_proj_blocks) * kProjBlock * 4);
   L->total = o;
   return true;
 }
@@ -156,6 +164,7 @@ gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, 
   if (!d_cams || !gauss_ptrs(gaussians, L.N, &g)) return GS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(at<Status>(ws, L.status), 0, sizeof(Status), s) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaMemsetAsync(at<uint32_t>(ws, L.item_hist), 0, 4 * 256 * 4, s) != cudaSuccess) return GS_ERR_CUDA;
   return launched(launch_project(L, g, d_cams, ws, s));
 }
 
@@ -164,7 +173,8 @@ gs_status_t gs_bin_sort(const gs_config_t* cfg, void* ws, size_t ws_bytes, void*
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = launch_bin(L, ws, s);
+  cudaError_t e = launch_item_sort(L, ws, s);
+  if (e == cudaSuccess) e = launch_bin(L, ws, s);
   if (e == cudaSuccess) e = launch_sort_passes(L, ws, s);
   if (e == cudaSuccess) e = launch_ranges(L, ws, s);
   return launched(e);

@@ -1,12 +1,14 @@
-// Tile binning of the projected Gaussians: exclusive scan of tiles touched, emission of
-// one (key, value) pair per (view, Gaussian, tile), digit histograms for the radix sort,
-// and per-tile [start, end) ranges of the sorted list.
+// Tile binning of the projected Gaussians, after the (view, Gaussian) items have been
+// stably sorted by camera depth: tiles touched per item in depth order, exclusive scan,
+// emission of one (key, value) pair per (view, Gaussian, tile) in depth order, digit
+// histograms of the pair sort, and per-tile [start, end) ranges of the sorted list.
 //
 // key   = ((k * Tx * Ty + ty * Tx + tx) << 32) | bits(camera depth)   (depth > 0, so the
 //         float bit pattern orders like the depth)
 // value = Gaussian id g.
-// Pairs are emitted in increasing (k, g) order, tiles row-major inside each rectangle, so a
-// stable sort leaves equal keys in (k, g) order.
+// Emission runs over the items in (depth bits, k*N + g) order, tiles row-major inside each
+// rectangle. The pair sort then only orders the tile bits (stable), which leaves every
+// tile's pairs in (depth bits, k*N + g) order: the order of a stable sort of the full keys.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -14,8 +16,30 @@ namespace {
 
 constexpr int kScanThreads = 1024;
 
-// Exclusive scan of the per-block pair totals written by the projection; total pair count,
-// capacity check; clears the digit histograms and the onesweep tile counters.
+// Tiles touched by each item in depth order, and per-block totals for the scan.
+__global__ void __launch_bounds__(kProjBlock) k_sorted_counts(Layout L, uint8_t* __restrict__ ws) {
+  const int64_t s = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
+  uint32_t cnt = 0;
+  if (s < L.KN) {
+    const uint32_t kg = at<uint32_t>(ws, L.item_vals[0])[s];
+    cnt = static_cast<uint32_t>(at<int4>(ws, L.proj_tiles)[kg].w);
+  }
+  at<uint32_t>(ws, L.sorted_counts)[s] = cnt;
+  __shared__ uint32_t warp_sums[kProjBlock / 32];
+  uint32_t v = cnt;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < kProjBlock / 32; ++w) tot += warp_sums[w];
+    at<uint32_t>(ws, L.block_sums)[blockIdx.x] = tot;
+  }
+}
+
+// Exclusive scan of the per-block pair totals; total pair count, capacity check; clears the
+// pair-sort digit histograms and tile counters.
 __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(Layout L, uint8_t* __restrict__ ws) {
   const uint32_t* sums = at<uint32_t>(ws, L.block_sums);
   uint64_t* offs = at<uint64_t>(ws, L.block_offsets);
@@ -58,11 +82,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(Layout L, uint8_t*
     if (carry > static_cast<uint64_t>(L.cap)) atomicOr(&st->err, GS_DEVERR_PAIR_OVERFLOW);
   }
   uint32_t* hist = at<uint32_t>(ws, L.hist);
-  for (int i = threadIdx.x; i < L.passes * 256; i += kScanThreads) hist[i] = 0;
-  if (threadIdx.x < kMaxSortPasses) st->tile_ctr[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < kMaxSortPasses * 256; i += kScanThreads) hist[i] = 0;
+  if (threadIdx.x < 4) st->tile_ctr[4 + threadIdx.x] = 0;
 }
 
-// One block per kProjBlock (view, Gaussian) items. The block's pairs are written as one
+// One block per kProjBlock depth-sorted items. The block's pairs are written as one
 // contiguous, coalesced run: thread j of the block handles pair j of the run and finds its
 // item by binary search over the block-local exclusive scan.
 __global__ void __launch_bounds__(kProjBlock) k_emit(Layout L, uint8_t* __restrict__ ws) {
@@ -70,20 +94,17 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(Layout L, uint8_t* __restri
   __shared__ uint32_t s_rect_x[kProjBlock], s_rect_y[kProjBlock], s_key[kProjBlock], s_gid[kProjBlock];
   __shared__ uint32_t s_warp[kProjBlock / 32];
   __shared__ int s_view[kProjBlock];
-  __shared__ uint32_t s_hist[kMaxSortPasses * 256];
+  __shared__ uint32_t s_hist[4 * 256];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t idx = static_cast<int64_t>(blockIdx.x) * kProjBlock + t;
+  const int64_t s = static_cast<int64_t>(blockIdx.x) * kProjBlock + t;
   int4* tiles = at<int4>(ws, L.proj_tiles);
+  const uint32_t cnt = at<uint32_t>(ws, L.sorted_counts)[s];
+  uint32_t kg = 0;
   int4 tl = make_int4(0, 0, 0, 0);
-  int k = 0;
-  uint32_t dkey = 0, gid = 0;
-  if (idx < L.KN) {
-    tl = tiles[idx];
-    k = static_cast<int>(idx / L.N);
-    gid = static_cast<uint32_t>(idx - static_cast<int64_t>(k) * L.N);
-    dkey = at<uint32_t>(ws, L.proj_depth_key)[idx];
+  if (cnt) {
+    kg = at<uint32_t>(ws, L.item_vals[0])[s];
+    tl = tiles[kg];
   }
-  const uint32_t cnt = static_cast<uint32_t>(tl.w);
   // block exclusive scan of cnt
   uint32_t incl = cnt;
 #pragma unroll
@@ -92,7 +113,7 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(Layout L, uint8_t* __restri
     if (lane >= o) incl += y;
   }
   if (lane == 31) s_warp[warp] = incl;
-  for (int i = t; i < L.passes * 256; i += kProjBlock) s_hist[i] = 0;
+  for (int i = t; i < 4 * 256; i += kProjBlock) s_hist[i] = 0;
   __syncthreads();
   if (warp == 0) {
     uint32_t w = (lane < kProjBlock / 32) ? s_warp[lane] : 0;
@@ -110,14 +131,15 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(Layout L, uint8_t* __restri
   const uint64_t cap = static_cast<uint64_t>(L.cap);
   s_excl[t] = excl;
   if (t == 0) s_excl[kProjBlock] = block_total;
+  const int k = static_cast<int>(kg / static_cast<uint64_t>(L.N > 0 ? L.N : 1));
   s_rect_x[t] = static_cast<uint32_t>(tl.y);
   s_rect_y[t] = static_cast<uint32_t>(tl.z);
-  s_key[t] = dkey;
-  s_gid[t] = gid;
+  s_key[t] = cnt ? at<uint32_t>(ws, L.proj_depth_key)[kg] : 0u;
+  s_gid[t] = static_cast<uint32_t>(kg - static_cast<int64_t>(k) * L.N);
   s_view[t] = k;
-  if (idx < L.KN) {
+  if (cnt) {
     const uint64_t off = base + excl;
-    tiles[idx].x = static_cast<int>(off < cap ? off : cap);
+    tiles[kg].x = static_cast<int>(off < cap ? off : cap);
   }
   __syncthreads();
 
@@ -139,17 +161,17 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(Layout L, uint8_t* __restri
     const uint32_t y0 = ry & 0xffffu;
     const uint32_t ty = y0 + r / w, tx = x0 + r % w;
     const uint64_t tid = static_cast<uint64_t>(s_view[lo]) * tiles_per_view + static_cast<uint64_t>(ty) * L.Tx + tx;
-    const uint64_t key = (tid << 32) | s_key[lo];
-    keys[pos] = key;
+    keys[pos] = (tid << 32) | s_key[lo];
     vals[pos] = s_gid[lo];
-    for (int p = 0; p < L.passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 0xffu)], 1u);
+    const uint32_t tid32 = static_cast<uint32_t>(tid);
+    for (int p = 0; p < L.passes; ++p) atomicAdd(&s_hist[p * 256 + ((tid32 >> (8 * p)) & 0xffu)], 1u);
   }
   __syncthreads();
   uint32_t* hist = at<uint32_t>(ws, L.hist);
   for (int i = t; i < L.passes * 256; i += kProjBlock)
     if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
 
-  // clear the tile ranges and the onesweep look-back status for this sort
+  // clear the tile ranges and the pair sort's look-back status
   const Status* st = at<Status>(ws, L.status);
   const uint64_t n = st->num_pairs;
   const uint64_t used_tiles = (n + kSortTileKeys - 1) / kSortTileKeys;
@@ -175,7 +197,7 @@ __global__ void k_ranges(Layout L, uint8_t* __restrict__ ws, const uint64_t* __r
   }
 }
 
-int num_sms() {
+int num_sms_bin() {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -190,6 +212,7 @@ int num_sms() {
 
 cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s) {
   auto* w = static_cast<uint8_t*>(ws);
+  k_sorted_counts<<<static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s>>>(L, w);
   k_scan_blocks<<<1, kScanThreads, 0, s>>>(L, w);
   k_emit<<<static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s>>>(L, w);
   return cudaGetLastError();
@@ -199,7 +222,7 @@ cudaError_t launch_ranges(const Layout& L, void* ws, cudaStream_t s) {
   auto* w = static_cast<uint8_t*>(ws);
   const uint64_t* keys = at<uint64_t>(ws, L.keys[L.passes & 1]);
   const int64_t want = (L.cap + 255) / 256;
-  const int blocks = static_cast<int>(want < 8 * num_sms() ? (want > 0 ? want : 1) : 8 * num_sms());
+  const int blocks = static_cast<int>(want < 8 * num_sms_bin() ? (want > 0 ? want : 1) : 8 * num_sms_bin());
   k_ranges<<<blocks, 256, 0, s>>>(L, w, keys);
   return cudaGetLastError();
 }

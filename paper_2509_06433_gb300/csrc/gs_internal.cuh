@@ -27,7 +27,7 @@ struct Status {
   uint32_t num_pairs;       // min(total pairs, capacity)
   uint64_t total_pairs;     // unclamped
   uint64_t evals;           // Gaussian-pixel evaluations of the last forward raster
-  uint32_t tile_ctr[kMaxSortPasses];  // onesweep dynamic tile counters
+  uint32_t tile_ctr[kMaxSortPasses];  // onesweep dynamic tile counters: [0,4) item sort, [4,8) pair sort
   uint64_t composited;      // evaluations of the last forward raster that blended a splat
   uint64_t pad;
 };
@@ -38,7 +38,9 @@ struct Layout {
   int64_t N, KN, cap;
   int K, W, H, Tx, Ty;
   int64_t n_tiles;          // K * Tx * Ty
-  int tile_bits, key_bits, passes;
+  int tile_bits, key_bits;
+  int passes;               // pair-sort passes over the tile bits: ceil(tile_bits / 8)
+  int64_t max_item_tiles;   // ceil(KN / kSortTileKeys): onesweep tiles of the per-item depth sort
   float near_plane, lambda_depth;
   int64_t n_proj_blocks;    // ceil(KN / kProjBlock)
   int64_t max_sort_tiles;   // ceil(cap / kSortTileKeys)
@@ -47,6 +49,9 @@ struct Layout {
   // byte offsets into the workspace
   size_t status, proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, color_opacity, block_sums,
       block_offsets, keys[2], vals[2], ranges, hist, sort_status, pair_grads, pose_partials, loss_partials;
+  // per-item depth sort (u32 depth key, u32 item index), its histograms and look-back status,
+  // and the tiles touched by each item in depth order
+  size_t item_keys[2], item_vals[2], item_hist, item_status, sorted_counts;
   size_t total;
 };
 
@@ -80,6 +85,7 @@ __device__ __forceinline__ float load_attr(const void* p, int64_t i, int dtype) 
 // Launchers (each defined in its own translation unit). All return cudaGetLastError().
 cudaError_t launch_project(const Layout& L, const GaussPtrs& g, const gs_camera_t* cams, void* ws, cudaStream_t s);
 cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_item_sort(const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_ranges(const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
@@ -94,9 +100,11 @@ cudaError_t launch_project_bwd(const Layout& L, const GaussPtrs& g, const gs_cam
 cudaError_t launch_screen_grads(const Layout& L, const void* ws, float* d_mean2d, float* d_conic, float* d_depth,
                                 float* d_opacity, float* d_rgb, cudaStream_t s);
 
-// Generic stable onesweep sort of (u64 key, u32 value) pairs used by gs_bin_sort and gs_sort_pairs.
-struct SortArgs {
-  uint64_t* keys[2];
+// Generic stable onesweep sort of (key, u32 value) pairs: u64 keys for the (tile, depth) pairs
+// and gs_sort_pairs, u32 keys for the per-item depth sort of gs_bin_sort.
+template <class KeyT>
+struct SortArgsT {
+  KeyT* keys[2];
   uint32_t* vals[2];
   const uint32_t* n_dev;  // device pair count (nullptr: use n_host)
   int64_t n_host;         // host pair count or capacity bound
@@ -106,9 +114,13 @@ struct SortArgs {
   uint32_t* err;
   int64_t max_tiles;
   int passes;
-  int key_bits;  // the last pass only looks at the bits below key_bits
+  int key_bits;   // the last pass only looks at the bits below key_bits
+  int first_bit;  // pass p sorts on bits [first_bit + 8p, first_bit + 8p + 8)
 };
+using SortArgs = SortArgsT<uint64_t>;
+using SortArgs32 = SortArgsT<uint32_t>;
 cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s);
+cudaError_t launch_onesweep(const SortArgs32& a, cudaStream_t s);
 cudaError_t launch_sort_prepare(const SortArgs& a, cudaStream_t s);  // zero status, build histogram
 
 }  // namespace gs

@@ -82,7 +82,10 @@ __device__ __forceinline__ uint32_t pack16(int lo, int hi) {
 __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                        uint8_t* __restrict__ ws) {
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
-  uint32_t count = 0;
+  __shared__ uint32_t s_hist[4 * 256];
+  for (int i = threadIdx.x; i < 4 * 256; i += kProjBlock) s_hist[i] = 0;
+  __syncthreads();
+  uint32_t count = 0, item_key = 0xffffffffu;
   if (idx < L.KN) {
     const int k = static_cast<int>(idx / L.N);
     const int64_t g = idx - static_cast<int64_t>(k) * L.N;
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
       if (count == 0) x0 = x1 = y0 = y1 = radius = 0;
     }
     at<uint32_t>(ws, L.proj_depth_key)[idx] = __float_as_uint(zc);
+    if (count) item_key = __float_as_uint(zc);
     at<int32_t>(ws, L.proj_radius)[idx] = radius;
     at<int4>(ws, L.proj_tiles)[idx] =
         make_int4(0, static_cast<int>(pack16(x0, x1)), static_cast<int>(pack16(y0, y1)), static_cast<int>(count));
@@ -213,18 +217,25 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
       at<float4>(ws, L.proj_conic)[idx] = make_float4(c * inv_det, -bb * inv_det, a * inv_det, Z.hi);
     }
   }
-  // per-block total of tiles touched, consumed by the emission scan
-  __shared__ uint32_t warp_sums[kProjBlock / 32];
-  uint32_t s = count;
+  // depth-sort key of the item (culled items sort last and emit nothing) and its digit counts
+  if (idx < L.KN) {
+    const uint32_t key = item_key;
+    at<uint32_t>(ws, L.item_keys[0])[idx] = key;
+    at<uint32_t>(ws, L.item_vals[0])[idx] = static_cast<uint32_t>(idx);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t tot = 0;
-    for (int w = 0; w < kProjBlock / 32; ++w) tot += warp_sums[w];
-    at<uint32_t>(ws, L.block_sums)[blockIdx.x] = tot;
+    for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 0xffu)], 1u);
   }
+  __syncthreads();
+  uint32_t* hist = at<uint32_t>(ws, L.item_hist);
+  for (int i = threadIdx.x; i < 4 * 256; i += kProjBlock)
+    if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
+  // clear the look-back status of the item sort
+  const uint64_t used = static_cast<uint64_t>(L.max_item_tiles) * 256;
+  const uint64_t gsize = static_cast<uint64_t>(gridDim.x) * kProjBlock;
+  uint32_t* st = at<uint32_t>(ws, L.item_status);
+  for (int p = 0; p < 4; ++p)
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kProjBlock + threadIdx.x; i < used; i += gsize)
+      st[static_cast<uint64_t>(p) * used + i] = 0;
 }
 
 }  // namespace

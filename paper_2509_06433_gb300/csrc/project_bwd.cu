@@ -37,6 +37,43 @@ __device__ __forceinline__ Sum10 sum_pairs(const float* __restrict__ pg, uint32_
   return s;
 }
 
+// Warp-wide version: a lane whose item has more than kCoopPairs records gets them summed
+// by the whole warp (lane-strided partial sums, then a fixed butterfly), the others sum
+// their own serially. Every lane of the warp must call it. Deterministic.
+constexpr uint32_t kCoopPairs = 32;
+__device__ __forceinline__ Sum10 sum_pairs_warp(const float* __restrict__ pg, uint32_t off, uint32_t cnt,
+                                                int64_t cap, bool active) {
+  const int lane = threadIdx.x & 31;
+  if (!active) cnt = 0;
+  const bool big = cnt > kCoopPairs;
+  Sum10 mine = sum_pairs(pg, off, big ? 0u : cnt, cap);
+  uint32_t pending = __ballot_sync(0xffffffffu, big);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const uint32_t o = __shfl_sync(0xffffffffu, off, src);
+    uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
+    if (static_cast<int64_t>(o) >= cap) c = 0;
+    else if (static_cast<int64_t>(o) + c > cap) c = static_cast<uint32_t>(cap - o);
+    Sum10 part;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) part.v[i] = 0.0f;
+    for (uint32_t j = lane; j < c; j += 32) {
+      const float4* r = reinterpret_cast<const float4*>(pg + static_cast<size_t>(o + j) * kPairGradStride);
+      const float4 a = r[0], b = r[1], d = r[2];
+      part.v[0] += a.x; part.v[1] += a.y; part.v[2] += a.z; part.v[3] += a.w;
+      part.v[4] += b.x; part.v[5] += b.y; part.v[6] += b.z; part.v[7] += b.w;
+      part.v[8] += d.x; part.v[9] += d.y;
+    }
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+#pragma unroll
+      for (int x = 16; x > 0; x >>= 1) part.v[i] += __shfl_xor_sync(0xffffffffu, part.v[i], x);
+    if (lane == src) mine = part;
+  }
+  return mine;
+}
+
 __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                            const uint8_t* __restrict__ ws, gs_grads_t out,
                                                            float* __restrict__ pose_partials) {
@@ -74,8 +111,8 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
     float pose[6] = {0, 0, 0, 0, 0, 0};
     int4 tl = make_int4(0, 0, 0, 0);
     if (valid) tl = tiles[static_cast<int64_t>(k) * L.N + g];
+    const Sum10 s = sum_pairs_warp(pg, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
     if (tl.w > 0) {
-      const Sum10 s = sum_pairs(pg, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap);
       const float gu = s.v[0], gv = s.v[1], gA = s.v[2], gB = s.v[3], gC = s.v[4], gz = s.v[5];
       d_op += s.v[6];
       d_rgb[0] += s.v[7];
@@ -236,19 +273,16 @@ __global__ void __launch_bounds__(kPoseBlock) k_screen_grads(Layout L, const uin
                                                             float* d_conic, float* d_depth, float* d_opacity,
                                                             float* d_rgb) {
   const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
-  if (g >= L.N) return;
+  const bool valid = g < L.N;  // no early return: the pair sums are warp-cooperative
   const int4* tiles = at<int4>(ws, L.proj_tiles);
   const float* pg = at<float>(ws, L.pair_grads);
   float op = 0.0f, c[3] = {0, 0, 0};
   for (int k = 0; k < L.K; ++k) {
     const int64_t kg = static_cast<int64_t>(k) * L.N + g;
-    const int4 tl = tiles[kg];
-    Sum10 s;
-    if (tl.w > 0) {
-      s = sum_pairs(pg, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap);
-    } else {
-      for (int i = 0; i < 10; ++i) s.v[i] = 0.0f;
-    }
+    int4 tl = make_int4(0, 0, 0, 0);
+    if (valid) tl = tiles[kg];
+    const Sum10 s = sum_pairs_warp(pg, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
+    if (!valid) continue;
     if (d_mean2d) {
       d_mean2d[2 * kg] = s.v[0];
       d_mean2d[2 * kg + 1] = s.v[1];
@@ -264,6 +298,7 @@ __global__ void __launch_bounds__(kPoseBlock) k_screen_grads(Layout L, const uin
     c[1] += s.v[8];
     c[2] += s.v[9];
   }
+  if (!valid) return;
   if (d_opacity) d_opacity[g] = op;
   if (d_rgb)
     for (int j = 0; j < 3; ++j) d_rgb[3 * g + j] = c[j];

@@ -1,9 +1,10 @@
-// Stable LSD radix sort of (u64 key, u32 value) pairs, one "onesweep" kernel per 8-bit
-// digit (Adinets & Merrill, "Onesweep: A Faster Least Significant Digit Radix Sort for
-// GPUs", 2022): the global digit histograms of all passes are counted up front; each pass
-// then ranks a tile of keys in shared memory, obtains the tile's global offset per digit
-// by a decoupled look-back over the preceding tiles, and scatters through shared memory so
-// that runs of equal digits are written contiguously.
+// Stable LSD radix sort of (key, u32 value) pairs, one "onesweep" kernel per 8-bit digit
+// (Adinets & Merrill, "Onesweep: A Faster Least Significant Digit Radix Sort for GPUs",
+// 2022): the global digit histograms of all passes are counted up front; each pass then
+// ranks a tile of keys in shared memory, obtains the tile's global offset per digit by a
+// decoupled look-back over the preceding tiles, and scatters through shared memory so that
+// runs of equal digits are written contiguously. Keys are u64 ((tile, depth) pairs and the
+// gs_sort_pairs primitive) or u32 (the per-item depth sort of gs_bin_sort).
 //
 // Stability: inside a tile, keys are ranked in (warp, item, lane) order, which is their
 // input order; tiles are numbered by a dynamic counter and the look-back sums the counts
@@ -51,8 +52,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
   return off + incl - x;
 }
 
+template <class KeyT>
 struct SortSmem {
-  uint64_t keys[kSortTileKeys];
+  KeyT keys[kSortTileKeys];
   uint32_t vals[kSortTileKeys];
   uint32_t warp_hist[kWarps][256];
   uint32_t bucket[256];       // exclusive scan of this pass's global digit histogram
@@ -62,23 +64,25 @@ struct SortSmem {
   uint32_t tile;
 };
 
-__device__ __forceinline__ uint32_t digit_mask(const SortArgs& a, int pass) {
-  const int rem = a.key_bits - 8 * pass;
+template <class KeyT>
+__device__ __forceinline__ uint32_t digit_mask(const SortArgsT<KeyT>& a, int pass) {
+  const int rem = a.key_bits - (a.first_bit + 8 * pass);
   return rem >= 8 ? 0xffu : ((1u << rem) - 1u);
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass) {
+template <class KeyT>
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, int pass) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+  SortSmem<KeyT>& S = *reinterpret_cast<SortSmem<KeyT>*>(smem_raw);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const uint64_t* __restrict__ kin = a.keys[pass & 1];
+  const KeyT* __restrict__ kin = a.keys[pass & 1];
   const uint32_t* __restrict__ vin = a.vals[pass & 1];
-  uint64_t* __restrict__ kout = a.keys[(pass + 1) & 1];
+  KeyT* __restrict__ kout = a.keys[(pass + 1) & 1];
   uint32_t* __restrict__ vout = a.vals[(pass + 1) & 1];
   uint32_t n = static_cast<uint32_t>(a.n_host);
   if (a.n_dev) n = min(*a.n_dev, n);
   const uint32_t n_tiles = (n + kSortTileKeys - 1) / kSortTileKeys;
-  const int shift = 8 * pass;
+  const int shift = a.first_bit + 8 * pass;
   const uint32_t dmask = digit_mask(a, pass);
   uint32_t* status = a.tile_status + static_cast<size_t>(pass) * a.max_tiles * 256;
 
@@ -92,14 +96,19 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
     for (int d = lane; d < 256; d += 32) S.warp_hist[warp][d] = 0;
     __syncwarp();
     const uint32_t wbase = tile * kSortTileKeys + warp * (32 * kSortItems);
-    uint64_t kr[kSortItems];
+    KeyT kr[kSortItems];
     uint32_t vr[kSortItems], rr[kSortItems];
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
       const uint32_t i = wbase + it * 32 + lane;
       const bool valid = i < n;
-      kr[it] = valid ? kin[i] : ~0ull;
+      kr[it] = valid ? kin[i] : static_cast<KeyT>(~static_cast<KeyT>(0));
       vr[it] = valid ? vin[i] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const uint32_t i = wbase + it * 32 + lane;
+      const bool valid = i < n;
       const uint32_t d = valid ? static_cast<uint32_t>(kr[it] >> shift) & dmask : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const uint32_t prior = valid ? S.warp_hist[warp][d] : 0u;
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
     const uint32_t rem = n - tile * kSortTileKeys;
     const uint32_t tile_n = rem < static_cast<uint32_t>(kSortTileKeys) ? rem : kSortTileKeys;
     for (uint32_t j = t; j < tile_n; j += kSortThreads) {
-      const uint64_t key = S.keys[j];
+      const KeyT key = S.keys[j];
       const uint32_t d = static_cast<uint32_t>(key >> shift) & dmask;
       const uint32_t dst = S.global_base[d] + (j - S.local_start[d]);
       kout[dst] = key;
@@ -177,7 +186,8 @@ __global__ void k_sort_hist(SortArgs a) {
   const uint64_t gtid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   for (uint64_t i = gtid; i < n; i += stride) {
     const uint64_t key = a.keys[0][i];
-    for (int p = 0; p < a.passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & digit_mask(a, p))], 1u);
+    for (int p = 0; p < a.passes; ++p)
+      atomicAdd(&s_hist[p * 256 + ((key >> (a.first_bit + 8 * p)) & digit_mask(a, p))], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < a.passes * 256; i += blockDim.x)
@@ -189,30 +199,44 @@ __global__ void k_sort_hist(SortArgs a) {
   }
 }
 
-int sort_grid(int64_t max_tiles) {
-  static int blocks_per_sm = -1, sms = 0;
-  if (blocks_per_sm < 0) {
-    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sizeof(SortSmem)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_onesweep, kSortThreads, sizeof(SortSmem));
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
   }
-  const int64_t resident = static_cast<int64_t>(blocks_per_sm) * sms;
+  return sms;
+}
+
+template <class KeyT>
+int sort_grid(int64_t max_tiles) {
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    cudaFuncSetAttribute(k_onesweep<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(sizeof(SortSmem<KeyT>)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_onesweep<KeyT>, kSortThreads,
+                                                  sizeof(SortSmem<KeyT>));
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int64_t resident = static_cast<int64_t>(blocks_per_sm) * num_sms();
   const int64_t g = max_tiles < resident ? max_tiles : resident;
   return static_cast<int>(g > 0 ? g : 1);
 }
 
-}  // namespace
-
-cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s) {
-  const int grid = sort_grid(a.max_tiles);
-  for (int p = 0; p < a.passes; ++p) {
-    k_onesweep<<<grid, kSortThreads, sizeof(SortSmem), s>>>(a, p);
-  }
+template <class KeyT>
+cudaError_t onesweep_passes(const SortArgsT<KeyT>& a, cudaStream_t s) {
+  const int grid = sort_grid<KeyT>(a.max_tiles);
+  for (int p = 0; p < a.passes; ++p)
+    k_onesweep<KeyT><<<grid, kSortThreads, sizeof(SortSmem<KeyT>), s>>>(a, p);
   return cudaGetLastError();
 }
+
+}  // namespace
+
+cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s) { return onesweep_passes(a, s); }
+cudaError_t launch_onesweep(const SortArgs32& a, cudaStream_t s) { return onesweep_passes(a, s); }
 
 cudaError_t launch_sort_prepare(const SortArgs& a, cudaStream_t s) {
   cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * 256 * a.passes, s);
@@ -224,7 +248,34 @@ cudaError_t launch_sort_prepare(const SortArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// gs_bin_sort: (1) stable depth sort of the K*N (view, Gaussian) items, (2) per-item pair
+// counts in depth order, scan, emission of the pairs in depth order, (3) stable sort of the
+// pairs on the tile bits only, (4) ranges. Pairs sharing a tile leave step (3) ordered by
+// (depth bits, k*N + g), exactly the order of a stable sort of the full 64-bit keys emitted
+// in (k, g) order.
+cudaError_t launch_item_sort(const Layout& L, void* ws, cudaStream_t s) {
+  SortArgs32 a{};
+  a.keys[0] = at<uint32_t>(ws, L.item_keys[0]);
+  a.keys[1] = at<uint32_t>(ws, L.item_keys[1]);
+  a.vals[0] = at<uint32_t>(ws, L.item_vals[0]);
+  a.vals[1] = at<uint32_t>(ws, L.item_vals[1]);
+  Status* st = at<Status>(ws, L.status);
+  a.n_dev = nullptr;
+  a.n_host = L.KN;
+  a.hist = at<uint32_t>(ws, L.item_hist);
+  a.tile_status = at<uint32_t>(ws, L.item_status);
+  a.tile_ctr = st->tile_ctr;
+  a.err = &st->err;
+  a.max_tiles = L.max_item_tiles;
+  a.passes = 4;
+  a.key_bits = 32;
+  a.first_bit = 0;
+  if (L.KN == 0) return cudaSuccess;
+  return launch_onesweep(a, s);
+}
+
 cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s) {
+  if (L.passes == 0) return cudaSuccess;  // a single tile: the emission order is final
   SortArgs a{};
   a.keys[0] = at<uint64_t>(ws, L.keys[0]);
   a.keys[1] = at<uint64_t>(ws, L.keys[1]);
@@ -235,11 +286,12 @@ cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s) {
   a.n_host = L.cap;
   a.hist = at<uint32_t>(ws, L.hist);
   a.tile_status = at<uint32_t>(ws, L.sort_status);
-  a.tile_ctr = st->tile_ctr;
+  a.tile_ctr = st->tile_ctr + 4;
   a.err = &st->err;
   a.max_tiles = L.max_sort_tiles;
   a.passes = L.passes;
   a.key_bits = L.key_bits;
+  a.first_bit = 32;
   return launch_onesweep(a, s);
 }
 

@@ -51,8 +51,8 @@ def test_workspace_size_and_layout(lib):
     assert lib.gs_workspace_layout(ctypes.byref(cfg), ctypes.byref(lay)) == 0
     assert lay.total == n.value
     assert (lay.tiles_x, lay.tiles_y) == (40, 30)
-    # 1200 tiles -> 11 tile bits -> 43 key bits -> 6 passes of 8 bits
-    assert lay.sort_passes == 6
+    # 1200 tiles -> 11 tile bits -> 2 pair-sort passes of 8 bits (depth is ordered per item first)
+    assert lay.sort_passes == 2
     offs = [lay.status, lay.proj_uv, lay.proj_conic, lay.proj_tiles, lay.proj_depth_key, lay.proj_radius,
             lay.color_opacity, lay.ranges, lay.pair_grads]
     assert all(o % 256 == 0 for o in offs + [lay.keys_sorted, lay.vals_sorted])
@@ -62,7 +62,7 @@ def test_workspace_size_and_layout(lib):
     assert lib.gs_workspace_size(ctypes.byref(_cfg(cap=1 << 21)), ctypes.byref(n2)) == 0 and n2.value > n.value
     k8 = GsWsLayout()
     assert lib.gs_workspace_layout(ctypes.byref(_cfg(K=8)), ctypes.byref(k8)) == 0
-    assert k8.sort_passes == 6  # 9600 tiles -> 14 bits -> 46 bits
+    assert k8.sort_passes == 2  # 9600 tiles -> 14 bits
 
 
 @pytest.mark.parametrize("bad", [dict(tile=8), dict(W=0), dict(H=20000), dict(K=0), dict(N=-1), dict(cap=0),

@@ -135,6 +135,8 @@ def run_ours(args, rank, world):
     tgt = r.render(gt, cams)
     rgb_t, depth_t = tgt["rgb"].clone(), tgt["depth"].clone()
     r.plan(g, cams)
+    from paper_2509_06433_gb300 import autotune
+    tuned = autotune.tune(r, g, cams)
     out = r.new_outputs()
     g_rgb = torch.empty_like(out["rgb"])
     g_depth = torch.empty_like(out["depth"])
@@ -287,6 +289,7 @@ def run_ours(args, rank, world):
         "gaussian_pixel_evals_per_s": evals * iters / (total_ms / 1e3),
         "stage_ms_median": {k: round(v, 5) for k, v in med.items()},
         "roofline": roof,
+        "autotune": {"fwd_ms": tuned["fwd"], "bwd_ms": tuned["bwd"], "px_per_thread": list(tuned["choice"])},
         "clocks": clocks,
     }
     return line

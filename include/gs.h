@@ -88,6 +88,10 @@ typedef struct {
   int64_t pair_capacity;  /* max (Gaussian, tile) pairs held by the workspace, <= 2^30 - 1 */
   float near_plane;       /* Gaussians with camera depth <= near_plane are culled (0.2) */
   float lambda_depth;     /* depth weight of gs_loss_l1 (0.1) */
+  int32_t fwd_px_per_thread;  /* pixels per thread of gs_raster_fwd: 1, 2 or 4; 0 = library default */
+  int32_t bwd_px_per_thread;  /* pixels per thread of gs_raster_bwd: 1, 2 or 4; 0 = library default.
+                                 Every choice takes the same skip/stop decisions: forward outputs are
+                                 bit-identical, gradients differ only in summation order. */
 } gs_config_t;
 
 /* Gaussian attributes. means may be F32 or BF16/F16 (means_dtype); the other four

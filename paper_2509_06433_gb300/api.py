@@ -32,9 +32,10 @@ def _s(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def make_config(width, height, num_views, num_gaussians, pair_capacity, near_plane=0.2, lambda_depth=0.1):
+def make_config(width, height, num_views, num_gaussians, pair_capacity, near_plane=0.2, lambda_depth=0.1,
+                fwd_px=0, bwd_px=0):
     return GsConfig(int(width), int(height), TILE, int(num_views), int(num_gaussians), int(pair_capacity),
-                    float(near_plane), float(lambda_depth))
+                    float(near_plane), float(lambda_depth), int(fwd_px), int(bwd_px))
 
 
 def workspace_size(cfg: GsConfig) -> int:

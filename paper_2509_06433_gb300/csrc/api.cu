@@ -38,6 +38,10 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->cap = cfg->pair_capacity;
   L->near_plane = cfg->near_plane;
   L->lambda_depth = cfg->lambda_depth;
+  if (cfg->fwd_px_per_thread < 0 || cfg->fwd_px_per_thread > 4 || cfg->fwd_px_per_thread == 3) return false;
+  if (cfg->bwd_px_per_thread < 0 || cfg->bwd_px_per_thread > 4 || cfg->bwd_px_per_thread == 3) return false;
+  L->fwd_px = cfg->fwd_px_per_thread;
+  L->bwd_px = cfg->bwd_px_per_thread;
   L->n_proj_blocks = L->KN > 0 ? (L->KN + kProjBlock - 1) / kProjBlock : 1;
   L->max_sort_tiles = (L->cap + kSortTileKeys - 1) / kSortTileKeys;
   L->max_item_tiles = L->KN > 0 ? (L->KN + kSortTileKeys - 1) / kSortTileKeys : 1;

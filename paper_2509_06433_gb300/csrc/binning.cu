@@ -146,25 +146,35 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(Layout L, uint8_t* __restri
   uint64_t* keys = at<uint64_t>(ws, L.keys[0]);
   uint32_t* vals = at<uint32_t>(ws, L.vals[0]);
   const uint64_t tiles_per_view = static_cast<uint64_t>(L.Tx) * L.Ty;
-  for (uint32_t j = t; j < block_total; j += kProjBlock) {
+  // the loop trip count is uniform over the block so that whole warps reach the
+  // warp-aggregated histogram update (neighbouring pairs mostly share their tile digits)
+  for (uint32_t j0 = 0; j0 < block_total; j0 += kProjBlock) {
+    const uint32_t j = j0 + t;
     const uint64_t pos = base + j;
-    if (pos >= cap) break;
-    // last item with s_excl <= j
-    int lo = 0, hi = kProjBlock;  // invariant: s_excl[lo] <= j < s_excl[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s_excl[mid] <= j) lo = mid; else hi = mid;
+    const bool active = j < block_total && pos < cap;
+    uint32_t tid32 = 0;
+    if (active) {
+      // last item with s_excl <= j
+      int lo = 0, hi = kProjBlock;  // invariant: s_excl[lo] <= j < s_excl[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_excl[mid] <= j) lo = mid; else hi = mid;
+      }
+      const uint32_t r = j - s_excl[lo];
+      const uint32_t rx = s_rect_x[lo], ry = s_rect_y[lo];
+      const uint32_t x0 = rx & 0xffffu, w = (rx >> 16) - x0;
+      const uint32_t y0 = ry & 0xffffu;
+      const uint32_t ty = y0 + r / w, tx = x0 + r % w;
+      const uint64_t tid = static_cast<uint64_t>(s_view[lo]) * tiles_per_view + static_cast<uint64_t>(ty) * L.Tx + tx;
+      keys[pos] = (tid << 32) | s_key[lo];
+      vals[pos] = s_gid[lo];
+      tid32 = static_cast<uint32_t>(tid);
     }
-    const uint32_t r = j - s_excl[lo];
-    const uint32_t rx = s_rect_x[lo], ry = s_rect_y[lo];
-    const uint32_t x0 = rx & 0xffffu, w = (rx >> 16) - x0;
-    const uint32_t y0 = ry & 0xffffu;
-    const uint32_t ty = y0 + r / w, tx = x0 + r % w;
-    const uint64_t tid = static_cast<uint64_t>(s_view[lo]) * tiles_per_view + static_cast<uint64_t>(ty) * L.Tx + tx;
-    keys[pos] = (tid << 32) | s_key[lo];
-    vals[pos] = s_gid[lo];
-    const uint32_t tid32 = static_cast<uint32_t>(tid);
-    for (int p = 0; p < L.passes; ++p) atomicAdd(&s_hist[p * 256 + ((tid32 >> (8 * p)) & 0xffu)], 1u);
+    for (int p = 0; p < L.passes; ++p) {
+      const uint32_t d = active ? ((tid32 >> (8 * p)) & 0xffu) : 0x100u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (active && lane == __ffs(peers) - 1) atomicAdd(&s_hist[p * 256 + d], static_cast<uint32_t>(__popc(peers)));
+    }
   }
   __syncthreads();
   uint32_t* hist = at<uint32_t>(ws, L.hist);

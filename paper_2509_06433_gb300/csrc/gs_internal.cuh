@@ -20,6 +20,8 @@ constexpr int kMaxSortPasses = 8;
 constexpr int kPairGradStride = 12;   // floats per pair gradient record (10 used)
 constexpr int kPoseBlock = 256;       // Gaussians per projection-backward block
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded decoupled look-back
+constexpr int kDefaultFwdPx = 2;      // pixels per thread of the compositing kernels when
+constexpr int kDefaultBwdPx = 2;      // gs_config_t leaves the choice to the library
 
 // Workspace status block (first 256 bytes of the workspace).
 struct Status {
@@ -42,6 +44,7 @@ struct Layout {
   int passes;               // pair-sort passes over the tile bits: ceil(tile_bits / 8)
   int64_t max_item_tiles;   // ceil(KN / kSortTileKeys): onesweep tiles of the per-item depth sort
   float near_plane, lambda_depth;
+  int fwd_px, bwd_px;       // pixels per thread of the compositing kernels (0 = default)
   int64_t n_proj_blocks;    // ceil(KN / kProjBlock)
   int64_t max_sort_tiles;   // ceil(cap / kSortTileKeys)
   int64_t n_pose_blocks;    // ceil(N / kPoseBlock)

@@ -1,32 +1,33 @@
 // Tile compositing: forward (render) and backward (splat gradients).
 //
-// One CTA of 128 threads per (view, 16x16 tile); each thread owns two vertically adjacent
-// pixels of one column, so the horizontal offset to a splat is shared and every splat
-// record loaded from shared memory serves two pixels. The tile's depth-sorted list is
-// walked in chunks of 128 splats staged in shared memory as three float4 per splat
-// (coalesced loads of the sorted Gaussian ids, one gather of the projected record each).
+// One CTA per (view, 16x16 tile). Each thread owns PX vertically adjacent pixels of one
+// column (PX = 1, 2 or 4, chosen per workload), so the horizontal offset to a splat is
+// shared and every splat record loaded from shared memory serves PX pixels. The per-pixel
+// update is branch-free (a masked blend with weight 0 leaves every accumulator bit for bit
+// unchanged), so the PX pixel chains interleave. The tile's depth-sorted list is walked in
+// chunks staged in shared memory as three float4 per splat (coalesced loads of the sorted
+// Gaussian ids, one gather of the projected record each).
 //
 // Both kernels evaluate a splat's opacity with the same inline function on the same
 // operands, so the backward pass takes exactly the forward pass's skip and stop decisions
 // and recovers the same transmittance T_i front to back, without storing per-splat alphas.
 //
-// The backward pass sums each splat's 10 gradient terms over a warp's 64 pixels (two per
-// lane, then a transpose-reduce: 16 shuffles for 16 padded values), writes one partial per
-// warp into shared memory, and at the end of each chunk sums the 4 warp partials in a
-// fixed order into one record per (splat, tile) pair of the pair-gradient buffer. No global
-// atomics: the gradients are deterministic.
+// The backward pass sums each splat's 10 gradient terms over a warp's pixels (PX per lane,
+// then a transpose-reduce: 16 shuffles for 16 padded values), writes one partial per warp
+// into shared memory, and at the end of each chunk sums the warp partials in a fixed order
+// into one record per (splat, tile) pair of the pair-gradient buffer. No global atomics:
+// the gradients are deterministic.
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kRasterThreads = kTilePixels / 2;  // two pixels per thread
-constexpr int kWarps = kRasterThreads / 32;
-constexpr int kChunk = kRasterThreads;           // splats staged per chunk
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
+constexpr int kFwdChunk = 128;  // splats staged per forward chunk
+constexpr int kBwdChunk = 64;   // splats staged per backward chunk
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -36,11 +37,13 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 // Staged splat: A = (x, y, qa, qb), B = (qc, opacity, depth, -), C = (r, g, b, -) where
 // (x, y) is the 2D mean relative to the tile origin and power * log2(e) = qa dx^2 + qb dx dy + qc dy^2.
+template <int CH>
 struct Stage {
-  float4 A[kChunk], B[kChunk], C[kChunk];
+  float4 A[CH], B[CH], C[CH];
 };
 
-__device__ __forceinline__ uint32_t stage_splat(Stage& S, int j, const Layout& L, const uint8_t* ws,
+template <int CH>
+__device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layout& L, const uint8_t* ws,
                                                 const uint32_t* vals, uint32_t i, int k, float ox, float oy) {
   const uint32_t gid = vals[i];
   const int64_t kg = static_cast<int64_t>(k) * L.N + gid;
@@ -54,17 +57,20 @@ __device__ __forceinline__ uint32_t stage_splat(Stage& S, int j, const Layout& L
   return gid;
 }
 
-// Opacity of a splat at pixel offset (dx, dy). Returns false when the splat is skipped
-// (power > 0 or alpha < 1/255). G = exp(power); clamped: alpha hit 0.99.
-__device__ __forceinline__ bool splat_alpha(const float4& A, const float4& B, float dx, float dy, float& alpha,
-                                            float& G, bool& clamped) {
-  const float p = __fmaf_rn(dx, __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy)), __fmul_rn(__fmul_rn(B.x, dy), dy));
-  if (p > 0.0f) return false;
-  G = ex2_approx(p);
-  const float a = __fmul_rn(B.y, G);
-  clamped = a > kAlphaMax;
-  alpha = clamped ? kAlphaMax : a;
-  return alpha >= kAlphaMin;
+// Opacity of a splat at pixel offset (dx, dy) with qadx = qa * dx. keep: the splat is not
+// skipped (power <= 0 and alpha >= 1/255). G = exp(power); raw = opacity * G before the clamp.
+struct Alpha {
+  float alpha, G, raw;
+  bool keep;
+};
+__device__ __forceinline__ Alpha splat_alpha(const float4& A, const float4& B, float qadx, float dx, float dy) {
+  Alpha r;
+  const float p = __fmaf_rn(dx, __fmaf_rn(A.w, dy, qadx), __fmul_rn(__fmul_rn(B.x, dy), dy));
+  r.G = ex2_approx(p);
+  r.raw = __fmul_rn(B.y, r.G);
+  r.alpha = fminf(r.raw, kAlphaMax);
+  r.keep = (p <= 0.0f) && (r.alpha >= kAlphaMin);
+  return r;
 }
 
 struct TileCoord {
@@ -81,85 +87,98 @@ __device__ __forceinline__ TileCoord tile_coord(const Layout& L, int64_t tile_g)
 }
 
 // ============================================================================ forward
-struct FwdPixel {
-  float T, r, g, b, d;
-  int32_t last;
-  uint32_t evals, blended;
-  bool done;
-};
-
-__device__ __forceinline__ void fwd_step(FwdPixel& P, const float4& A, const float4& B, const float4& C, float dx,
-                                         float dy, int pos) {
-  ++P.evals;
-  float alpha, G;
-  bool clamped;
-  if (!splat_alpha(A, B, dx, dy, alpha, G, clamped)) return;
-  const float Tn = __fmaf_rn(-P.T, alpha, P.T);
-  if (Tn < kTStop) {
-    P.done = true;
-    return;
-  }
-  const float w = __fmul_rn(alpha, P.T);
-  P.r = __fmaf_rn(C.x, w, P.r);
-  P.g = __fmaf_rn(C.y, w, P.g);
-  P.b = __fmaf_rn(C.z, w, P.b);
-  P.d = __fmaf_rn(B.z, w, P.d);
-  P.T = Tn;
-  ++P.blended;
-  P.last = pos + 1;
-}
-
-__global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
-                                                               float* __restrict__ out_rgb,
-                                                               float* __restrict__ out_depth,
-                                                               float* __restrict__ out_T,
-                                                               int32_t* __restrict__ out_last,
-                                                               uint64_t* __restrict__ evals_out,
-                                                               uint64_t* __restrict__ blended_out) {
-  __shared__ Stage S;
+template <int PX>
+__global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
+                                                                 float* __restrict__ out_rgb,
+                                                                 float* __restrict__ out_depth,
+                                                                 float* __restrict__ out_T,
+                                                                 int32_t* __restrict__ out_last,
+                                                                 uint64_t* __restrict__ evals_out,
+                                                                 uint64_t* __restrict__ blended_out) {
+  constexpr int kThreads = kTilePixels / PX;
+  constexpr int kWarps = kThreads / 32;
+  __shared__ Stage<kFwdChunk> S;
   __shared__ uint32_t s_red[2][kWarps];
   const TileCoord tc = tile_coord(L, blockIdx.x);
-  const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * 2;
+  const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * PX;
   const int px = tc.tx * kTile + lx, py = tc.ty * kTile + ly;
   const uint32_t* vals = at<uint32_t>(ws, (L.passes & 1) ? L.vals[1] : L.vals[0]);
   const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
   const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
-  const float pxc = static_cast<float>(lx) + 0.5f, pyc0 = static_cast<float>(ly) + 0.5f,
-              pyc1 = static_cast<float>(ly + 1) + 0.5f;
-  FwdPixel p0{1.0f, 0.f, 0.f, 0.f, 0.f, 0, 0u, 0u, !(px < L.W && py < L.H)};
-  FwdPixel p1{1.0f, 0.f, 0.f, 0.f, 0.f, 0, 0u, 0u, !(px < L.W && py + 1 < L.H)};
-  for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
-    if (__syncthreads_count(!(p0.done && p1.done)) == 0) break;
-    const uint32_t i = base + threadIdx.x;
-    if (i < rg.y) stage_splat(S, threadIdx.x, L, ws, vals, i, tc.k, ox, oy);
+  const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
+  float T[PX], cr[PX], cg[PX], cb[PX], cd[PX];
+  int32_t last[PX], stop_at[PX];
+  bool done[PX];
+  uint32_t blended = 0;
+  bool all_done = true;
+#pragma unroll
+  for (int q = 0; q < PX; ++q) {
+    T[q] = 1.0f;
+    cr[q] = cg[q] = cb[q] = cd[q] = 0.0f;
+    last[q] = 0;
+    stop_at[q] = -1;
+    done[q] = !(px < L.W && py + q < L.H);
+    all_done = all_done && done[q];
+  }
+  for (uint32_t base = rg.x; base < rg.y; base += kFwdChunk) {
+    if (__syncthreads_count(!all_done) == 0) break;
+    for (int jj = threadIdx.x; jj < kFwdChunk; jj += kThreads) {
+      const uint32_t i = base + jj;
+      if (i < rg.y) stage_splat(S, jj, L, ws, vals, i, tc.k, ox, oy);
+    }
     __syncthreads();
-    const int n = min(kChunk, static_cast<int>(rg.y - base));
+    const int n = min(kFwdChunk, static_cast<int>(rg.y - base));
     const int pos0 = static_cast<int>(base - rg.x);
-    for (int j = 0; j < n && !(p0.done && p1.done); ++j) {
+    for (int j = 0; j < n; ++j) {
+      if (__all_sync(0xffffffffu, all_done)) break;
       const float4 A = S.A[j], B = S.B[j], C = S.C[j];
       const float dx = __fsub_rn(A.x, pxc);
-      if (!p0.done) fwd_step(p0, A, B, C, dx, __fsub_rn(A.y, pyc0), pos0 + j);
-      if (!p1.done) fwd_step(p1, A, B, C, dx, __fsub_rn(A.y, pyc1), pos0 + j);
+      const float qadx = __fmul_rn(A.z, dx);
+      const int pos = pos0 + j;
+      all_done = true;
+#pragma unroll
+      for (int q = 0; q < PX; ++q) {
+        // pixel-centre offsets are formed the same way whatever PX is, so every variant
+        // takes bit-identical decisions
+        const Alpha a = splat_alpha(A, B, qadx, dx, __fsub_rn(A.y, pyc + static_cast<float>(q)));
+        const bool ok = a.keep && !done[q];
+        const float Tn = __fmaf_rn(-T[q], a.alpha, T[q]);
+        const bool stop = ok && (Tn < kTStop);
+        const bool blend = ok && !stop;
+        const float w = blend ? __fmul_rn(a.alpha, T[q]) : 0.0f;
+        cr[q] = __fmaf_rn(C.x, w, cr[q]);
+        cg[q] = __fmaf_rn(C.y, w, cg[q]);
+        cb[q] = __fmaf_rn(C.z, w, cb[q]);
+        cd[q] = __fmaf_rn(B.z, w, cd[q]);
+        T[q] = blend ? Tn : T[q];
+        last[q] = blend ? pos + 1 : last[q];
+        stop_at[q] = stop ? pos : stop_at[q];
+        blended += blend ? 1u : 0u;
+        done[q] = done[q] || stop;
+        all_done = all_done && done[q];
+      }
     }
   }
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
+  const int len = static_cast<int>(rg.y - rg.x);
+  uint32_t evals = 0;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const FwdPixel& P = q ? p1 : p0;
+  for (int q = 0; q < PX; ++q) {
     const int y = py + q;
     if (px < L.W && y < L.H) {
+      evals += static_cast<uint32_t>(stop_at[q] >= 0 ? stop_at[q] + 1 : len);
       const int64_t pix = static_cast<int64_t>(y) * L.W + px;
       if (out_rgb) {
-        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 0) * HW + pix] = P.r;
-        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 1) * HW + pix] = P.g;
-        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 2) * HW + pix] = P.b;
+        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 0) * HW + pix] = cr[q];
+        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 1) * HW + pix] = cg[q];
+        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 2) * HW + pix] = cb[q];
       }
-      if (out_depth) out_depth[tc.k * HW + pix] = P.d;
-      if (out_T) out_T[tc.k * HW + pix] = P.T;
-      if (out_last) out_last[tc.k * HW + pix] = P.last;
+      if (out_depth) out_depth[tc.k * HW + pix] = cd[q];
+      if (out_T) out_T[tc.k * HW + pix] = T[q];
+      if (out_last) out_last[tc.k * HW + pix] = last[q];
     }
   }
-  uint32_t e = p0.evals + p1.evals, c = p0.blended + p1.blended;
+  uint32_t e = evals, c = blended;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -223,94 +242,62 @@ __device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-struct BwdPixel {
-  float T, Sg, hT, gr, gg, gb, gd;
-  int last;
-};
-
-// Gradient record layout (floats): 0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 dz, 6 do, 7 dr, 8 dg, 9 db.
-// Adds this pixel's terms for splat (A, B, C) at list position pos into v; returns true if it blended.
-__device__ __forceinline__ bool bwd_step(BwdPixel& P, const float4& A, const float4& B, const float4& C, float dx,
-                                         float dy, int pos, float (&v)[16]) {
-  if (pos >= P.last) return false;
-  float alpha, G;
-  bool clamped;
-  if (!splat_alpha(A, B, dx, dy, alpha, G, clamped)) return false;
-  const float T = P.T;
-  const float w = __fmul_rn(alpha, T);
-  const float cgz = C.x * P.gr + C.y * P.gg + C.z * P.gb + B.z * P.gd;
-  P.Sg -= cgz * w;  // now: colour/depth behind this splat, weighted by dL/dpixel
-  const float dalpha = T * cgz - (P.Sg + P.hT) / (1.0f - alpha);
-  v[5] += w * P.gd;
-  v[7] += w * P.gr;
-  v[8] += w * P.gg;
-  v[9] += w * P.gb;
-  if (!clamped) {
-    // power = -0.5 (A dx^2 + C dy^2) - B dx dy with qa = -0.5 A log2e, qb = -B log2e, qc = -0.5 C log2e
-    constexpr float kLn2 = 0.6931471805599453f;
-    const float dpow = alpha * dalpha;
-    const float dpl = dpow * kLn2;
-    v[6] += G * dalpha;
-    v[2] += -0.5f * dx * dx * dpow;
-    v[3] += -dx * dy * dpow;
-    v[4] += -0.5f * dy * dy * dpow;
-    v[0] += (2.0f * A.z * dx + A.w * dy) * dpl;
-    v[1] += (2.0f * B.x * dy + A.w * dx) * dpl;
-  }
-  P.T = __fmaf_rn(-T, alpha, T);
-  return true;
-}
-
 __device__ __forceinline__ uint32_t pair_slot(const int4& tl, int tx, int ty) {
   const uint32_t x0 = static_cast<uint32_t>(tl.y) & 0xffffu, x1 = static_cast<uint32_t>(tl.y) >> 16;
   const uint32_t y0 = static_cast<uint32_t>(tl.z) & 0xffffu;
   return static_cast<uint32_t>(tl.x) + (static_cast<uint32_t>(ty) - y0) * (x1 - x0) + (static_cast<uint32_t>(tx) - x0);
 }
 
-__global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(Layout L, uint8_t* __restrict__ ws,
-                                                               const float* __restrict__ rgb,
-                                                               const float* __restrict__ depth,
-                                                               const float* __restrict__ T_final,
-                                                               const int32_t* __restrict__ last_in,
-                                                               const float* __restrict__ g_rgb,
-                                                               const float* __restrict__ g_depth,
-                                                               const float* __restrict__ g_T) {
-  __shared__ Stage S;
-  __shared__ uint32_t s_slot[kChunk];
-  __shared__ float s_part[kWarps][kChunk][10];
+// Gradient record layout (floats): 0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 dz, 6 do, 7 dr, 8 dg, 9 db.
+template <int PX>
+__global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8_t* __restrict__ ws,
+                                                                 const float* __restrict__ rgb,
+                                                                 const float* __restrict__ depth,
+                                                                 const float* __restrict__ T_final,
+                                                                 const int32_t* __restrict__ last_in,
+                                                                 const float* __restrict__ g_rgb,
+                                                                 const float* __restrict__ g_depth,
+                                                                 const float* __restrict__ g_T) {
+  constexpr int kThreads = kTilePixels / PX;
+  constexpr int kWarps = kThreads / 32;
+  __shared__ Stage<kBwdChunk> S;
+  __shared__ uint32_t s_slot[kBwdChunk];
+  __shared__ float s_part[kWarps][kBwdChunk][10];
   __shared__ int s_maxlast[kWarps];
   const TileCoord tc = tile_coord(L, blockIdx.x);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * 2;
+  const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * PX;
   const int px = tc.tx * kTile + lx, py = tc.ty * kTile + ly;
   const uint32_t* vals = at<uint32_t>(ws, (L.passes & 1) ? L.vals[1] : L.vals[0]);
   const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
   const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
-  const float pxc = static_cast<float>(lx) + 0.5f, pyc0 = static_cast<float>(ly) + 0.5f,
-              pyc1 = static_cast<float>(ly + 1) + 0.5f;
+  const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
   const int4* tiles = at<int4>(ws, L.proj_tiles);
   float* pair_grads = at<float>(ws, L.pair_grads);
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
 
-  BwdPixel pp[2];
+  float T[PX], Sg[PX], hT[PX], gr[PX], gg[PX], gb[PX], gd[PX];
+  int last[PX];
+  int wl = 0;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    BwdPixel& P = pp[q];
-    P = BwdPixel{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+  for (int q = 0; q < PX; ++q) {
+    T[q] = 1.0f;
+    Sg[q] = hT[q] = gr[q] = gg[q] = gb[q] = gd[q] = 0.0f;
+    last[q] = 0;
     const int y = py + q;
     if (px < L.W && y < L.H) {
       const int64_t pix = static_cast<int64_t>(y) * L.W + px;
       const int64_t c0 = static_cast<int64_t>(tc.k) * 3 * HW + pix;
-      P.gr = g_rgb[c0];
-      P.gg = g_rgb[c0 + HW];
-      P.gb = g_rgb[c0 + 2 * HW];
-      P.gd = g_depth[tc.k * HW + pix];
-      P.Sg = P.gr * rgb[c0] + P.gg * rgb[c0 + HW] + P.gb * rgb[c0 + 2 * HW] + P.gd * depth[tc.k * HW + pix];
-      if (g_T) P.hT = g_T[tc.k * HW + pix] * T_final[tc.k * HW + pix];
-      P.last = last_in[tc.k * HW + pix];
+      gr[q] = g_rgb[c0];
+      gg[q] = g_rgb[c0 + HW];
+      gb[q] = g_rgb[c0 + 2 * HW];
+      gd[q] = g_depth[tc.k * HW + pix];
+      Sg[q] = gr[q] * rgb[c0] + gg[q] * rgb[c0 + HW] + gb[q] * rgb[c0 + 2 * HW] + gd[q] * depth[tc.k * HW + pix];
+      if (g_T) hT[q] = g_T[tc.k * HW + pix] * T_final[tc.k * HW + pix];
+      last[q] = last_in[tc.k * HW + pix];
+      wl = max(wl, last[q]);
     }
   }
-  int wl = max(pp[0].last, pp[1].last);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
   const int warp_last = wl;  // this warp's pixels need list positions [0, warp_last)
@@ -321,42 +308,74 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(Layout L, uint8_t
   for (int w = 0; w < kWarps; ++w) max_last = max(max_last, s_maxlast[w]);
   const uint32_t stop = min(rg.y, rg.x + static_cast<uint32_t>(max_last));
   const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+  constexpr float kLn2 = 0.6931471805599453f;
 
-  for (uint32_t base = rg.x; base < stop; base += kChunk) {
-    const uint32_t i = base + threadIdx.x;
-    if (i < stop) {
-      const uint32_t gid = stage_splat(S, threadIdx.x, L, ws, vals, i, tc.k, ox, oy);
-      s_slot[threadIdx.x] = pair_slot(tiles[static_cast<int64_t>(tc.k) * L.N + gid], tc.tx, tc.ty);
+  for (uint32_t base = rg.x; base < stop; base += kBwdChunk) {
+    for (int jj = threadIdx.x; jj < kBwdChunk; jj += kThreads) {
+      const uint32_t i = base + jj;
+      if (i < stop) {
+        const uint32_t gid = stage_splat(S, jj, L, ws, vals, i, tc.k, ox, oy);
+        s_slot[jj] = pair_slot(tiles[static_cast<int64_t>(tc.k) * L.N + gid], tc.tx, tc.ty);
+      }
     }
-    for (int e = threadIdx.x; e < kWarps * kChunk * 10; e += kRasterThreads) (&s_part[0][0][0])[e] = 0.0f;
+    for (int e = threadIdx.x; e < kWarps * kBwdChunk * 10; e += kThreads) (&s_part[0][0][0])[e] = 0.0f;
     __syncthreads();
-    const int n = min(kChunk, static_cast<int>(stop - base));
+    const int n = min(kBwdChunk, static_cast<int>(stop - base));
     const int pos0 = static_cast<int>(base - rg.x);
     const int nw = min(n, warp_last - pos0);  // splats of this chunk this warp must visit
     for (int j = 0; j < nw; ++j) {
       const float4 A = S.A[j], B = S.B[j], C = S.C[j];
+      const float dx = __fsub_rn(A.x, pxc);
+      const float qadx = __fmul_rn(A.z, dx);
+      const int pos = pos0 + j;
       float v[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = 0.0f;
-      const float dx = __fsub_rn(A.x, pxc);
-      bool contrib = bwd_step(pp[0], A, B, C, dx, __fsub_rn(A.y, pyc0), pos0 + j, v);
-      contrib |= bwd_step(pp[1], A, B, C, dx, __fsub_rn(A.y, pyc1), pos0 + j, v);
+      bool contrib = false;
+#pragma unroll
+      for (int q = 0; q < PX; ++q) {
+        const float dy = __fsub_rn(A.y, pyc + static_cast<float>(q));
+        const Alpha a = splat_alpha(A, B, qadx, dx, dy);
+        const bool ok = a.keep && (pos < last[q]);
+        const bool open = ok && !(a.raw > kAlphaMax);  // the 0.99 clamp passes no gradient
+        const float Tq = T[q];
+        const float w = __fmul_rn(a.alpha, Tq);
+        const float cgz = C.x * gr[q] + C.y * gg[q] + C.z * gb[q] + B.z * gd[q];
+        const float sg = Sg[q] - cgz * w;  // colour/depth behind this splat, weighted by dL/dpixel
+        const float dalpha = Tq * cgz - __fdividef(sg + hT[q], 1.0f - a.alpha);
+        const float wm = ok ? w : 0.0f;
+        const float dpow = open ? a.alpha * dalpha : 0.0f;
+        const float dpl = dpow * kLn2;
+        v[5] += wm * gd[q];
+        v[7] += wm * gr[q];
+        v[8] += wm * gg[q];
+        v[9] += wm * gb[q];
+        v[6] += open ? a.G * dalpha : 0.0f;
+        v[2] += -0.5f * dx * dx * dpow;
+        v[3] += -dx * dy * dpow;
+        v[4] += -0.5f * dy * dy * dpow;
+        v[0] += (2.0f * qadx + A.w * dy) * dpl;
+        v[1] += (2.0f * B.x * dy + A.w * dx) * dpl;
+        Sg[q] = ok ? sg : Sg[q];
+        T[q] = ok ? __fmaf_rn(-Tq, a.alpha, Tq) : Tq;
+        contrib = contrib || ok;
+      }
       if (__any_sync(0xffffffffu, contrib)) {
         warp_transpose_reduce16(v, lane);
         if (!(lane & 1) && idx < 10) s_part[warp][j][idx] = v[0];
       }
     }
     __syncthreads();
-    if (threadIdx.x < n) {
+    for (int jj = threadIdx.x; jj < n; jj += kThreads) {
       float a[10];
 #pragma unroll
       for (int q = 0; q < 10; ++q) {
         float acc = 0.0f;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) acc += s_part[w][threadIdx.x][q];
+        for (int w = 0; w < kWarps; ++w) acc += s_part[w][jj][q];
         a[q] = acc;
       }
-      float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(s_slot[threadIdx.x]) * kPairGradStride);
+      float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(s_slot[jj]) * kPairGradStride);
       dst[0] = make_float4(a[0], a[1], a[2], a[3]);
       dst[1] = make_float4(a[4], a[5], a[6], a[7]);
       dst[2] = make_float4(a[8], a[9], 0.0f, 0.0f);
@@ -364,7 +383,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(Layout L, uint8_t
     __syncthreads();
   }
   // pairs behind every pixel's last contributor receive zero records
-  for (uint32_t i = stop + threadIdx.x; i < rg.y; i += kRasterThreads) {
+  for (uint32_t i = stop + threadIdx.x; i < rg.y; i += kThreads) {
     const uint32_t gid = vals[i];
     const uint32_t slot = pair_slot(tiles[static_cast<int64_t>(tc.k) * L.N + gid], tc.tx, tc.ty);
     float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(slot) * kPairGradStride);
@@ -375,6 +394,8 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(Layout L, uint8_t
   }
 }
 
+int pick_px(int requested, int fallback) { return (requested == 1 || requested == 2 || requested == 4) ? requested : fallback; }
+
 }  // namespace
 
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
@@ -383,8 +404,13 @@ cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* dept
   cudaMemsetAsync(&st->evals, 0, sizeof(uint64_t), s);
   cudaMemsetAsync(&st->composited, 0, sizeof(uint64_t), s);
   if (L.n_tiles == 0) return cudaGetLastError();
-  k_raster_fwd<<<static_cast<unsigned>(L.n_tiles), kRasterThreads, 0, s>>>(
-      L, static_cast<const uint8_t*>(ws), rgb, depth, T_final, last, &st->evals, &st->composited);
+  const unsigned grid = static_cast<unsigned>(L.n_tiles);
+  const uint8_t* w = static_cast<const uint8_t*>(ws);
+  switch (pick_px(L.fwd_px, kDefaultFwdPx)) {
+    case 1: k_raster_fwd<1><<<grid, kTilePixels, 0, s>>>(L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
+    case 2: k_raster_fwd<2><<<grid, kTilePixels / 2, 0, s>>>(L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
+    default: k_raster_fwd<4><<<grid, kTilePixels / 4, 0, s>>>(L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
+  }
   return cudaGetLastError();
 }
 
@@ -392,8 +418,13 @@ cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const
                               const int32_t* last, const float* dL_drgb, const float* dL_ddepth, const float* dL_dT,
                               cudaStream_t s) {
   if (L.n_tiles == 0) return cudaSuccess;
-  k_raster_bwd<<<static_cast<unsigned>(L.n_tiles), kRasterThreads, 0, s>>>(L, static_cast<uint8_t*>(ws), rgb, depth,
-                                                                           T_final, last, dL_drgb, dL_ddepth, dL_dT);
+  const unsigned grid = static_cast<unsigned>(L.n_tiles);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  switch (pick_px(L.bwd_px, kDefaultBwdPx)) {
+    case 1: k_raster_bwd<1><<<grid, kTilePixels, 0, s>>>(L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
+    case 2: k_raster_bwd<2><<<grid, kTilePixels / 2, 0, s>>>(L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
+    default: k_raster_bwd<4><<<grid, kTilePixels / 4, 0, s>>>(L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
+  }
   return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def _cfg(W=640, H=480, K=1, N=100_000, cap=1 << 20, tile=16, near=0.2):
     from paper_2509_06433_gb300._lib import GsConfig
-    return GsConfig(W, H, tile, K, N, cap, near, 0.1)
+    return GsConfig(W, H, tile, K, N, cap, near, 0.1, 0, 0)
 
 
 def test_workspace_size_and_layout(lib):

@@ -264,3 +264,43 @@ def test_bf16_and_f16_storage_match_dequantised_oracle():
         d = read_discrete(r)
         np.testing.assert_array_equal(d["keys"], orc["lists"].keys)
         check_images(to_np(out), orc)
+
+
+@pytest.mark.parametrize("name", ["ragged_tiny", "map100k"])
+def test_pixels_per_thread_variants_agree(name):
+    """Every (forward, backward) pixels-per-thread variant takes the same decisions: the
+    forward outputs are bit-identical; the gradients differ only by the order in which
+    pixels are summed (relative L2 below 1e-6)."""
+    torch, api = torch_mods()
+    s = scene(name)
+    r, g, ct, _, _ = gpu_fwd(name)
+    gr, gd, gt = (torch.as_tensor(a).cuda() for a in _upstream(name, s))
+    ref = None
+    for fpx in (1, 2, 4):
+        for bpx in (1, 2, 4):
+            r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = fpx, bpx
+            out = r.render(g, ct)
+            grads = r.backward(g, ct, out, gr, gd, gt)
+            got = {**{k: v.clone() for k, v in out.items()}, **{"g_" + k: v for k, v in grads.items()}}
+            if ref is None:
+                ref = got
+            else:
+                for k in ref:
+                    if k.startswith("g_"):
+                        e = rel_l2(got[k].cpu().numpy(), ref[k].cpu().numpy())
+                        assert e < 1e-6, (fpx, bpx, k, e)
+                    else:
+                        assert torch.equal(ref[k], got[k]), (fpx, bpx, k)
+    r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0
+
+
+def test_autotuner_picks_a_variant():
+    torch, api = torch_mods()
+    from paper_2509_06433_gb300 import autotune
+    s = scene("fwd10k")
+    r, g, ct, _, _ = gpu_fwd("fwd10k")
+    res = autotune.tune(r, g, ct, reps=3)
+    assert res["choice"][0] in (1, 2, 4) and res["choice"][1] in (1, 2, 4)
+    assert (r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread) == res["choice"]
+    check_images(to_np(r.render(g, ct)), oracle_fwd("fwd10k"))
+    r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0

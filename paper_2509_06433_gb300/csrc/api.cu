@@ -81,6 +81,11 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->item_hist = take(4 * 256 * 4);
   L->item_status = take(static_cast<size_t>(4) * L->max_item_tiles * 256 * 4);
   L->sorted_counts = take(static_cast<size_t>(L->n_proj_blocks) * kProjBlock * 4);
+  L->item_offsets = take((KN + 1) * 4);
+  L->item_rect = take(KN * 16);
+  L->item_kg = take(KN * 8);
+  L->tile_diff = take(static_cast<size_t>(L->K) * (L->Tx + 1) * (L->Ty + 1) * 4);
+  L->n_emit_blocks = (L->cap + kEmitPairs - 1) / kEmitPairs;
   L->total = o;
   return true;
 }
@@ -169,6 +174,9 @@ gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(at<Status>(ws, L.status), 0, sizeof(Status), s) != cudaSuccess) return GS_ERR_CUDA;
   if (cudaMemsetAsync(at<uint32_t>(ws, L.item_hist), 0, 4 * 256 * 4, s) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaMemsetAsync(at<int32_t>(ws, L.tile_diff), 0, static_cast<size_t>(L.K) * (L.Tx + 1) * (L.Ty + 1) * 4, s) !=
+      cudaSuccess)
+    return GS_ERR_CUDA;
   return launched(launch_project(L, g, d_cams, ws, s));
 }
 
@@ -180,7 +188,6 @@ gs_status_t gs_bin_sort(const gs_config_t* cfg, void* ws, size_t ws_bytes, void*
   cudaError_t e = launch_item_sort(L, ws, s);
   if (e == cudaSuccess) e = launch_bin(L, ws, s);
   if (e == cudaSuccess) e = launch_sort_passes(L, ws, s);
-  if (e == cudaSuccess) e = launch_ranges(L, ws, s);
   return launched(e);
 }
 

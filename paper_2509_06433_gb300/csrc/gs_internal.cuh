@@ -12,7 +12,9 @@ namespace gs {
 
 constexpr int kTile = 16;             // tile side (pixels)
 constexpr int kTilePixels = kTile * kTile;
-constexpr int kProjBlock = 256;       // (view, Gaussian) items per projection / emission block
+constexpr int kProjBlock = 256;       // (view, Gaussian) items per projection / scan block
+constexpr int kEmitPairs = 2048;      // pairs emitted per emission block
+constexpr int kProjGridCells = 6144;  // largest (Tx+1)(Ty+1) difference grid kept in shared memory
 constexpr int kSortThreads = 256;     // onesweep block
 constexpr int kSortItems = 15;        // keys per thread per onesweep tile
 constexpr int kSortTileKeys = kSortThreads * kSortItems;
@@ -55,6 +57,12 @@ struct Layout {
   // per-item depth sort (u32 depth key, u32 item index), its histograms and look-back status,
   // and the tiles touched by each item in depth order
   size_t item_keys[2], item_vals[2], item_hist, item_status, sorted_counts;
+  // in depth order: exclusive pair offset of each item (KN + 1 entries), its rectangle and
+  // depth key (int4: x0|x1<<16, y0|y1<<16, depth bits, -), its (view, Gaussian id)
+  size_t item_offsets, item_rect, item_kg;
+  // per view a (Ty+1) x (Tx+1) difference grid of the items' tile rectangles -> pairs per tile
+  size_t tile_diff;
+  int64_t n_emit_blocks;    // ceil(cap / kEmitPairs)
   size_t total;
 };
 
@@ -90,7 +98,7 @@ cudaError_t launch_project(const Layout& L, const GaussPtrs& g, const gs_camera_
 cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_item_sort(const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s);
-cudaError_t launch_ranges(const Layout& L, void* ws, cudaStream_t s);
+
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
                               cudaStream_t s);
 cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const float* depth, const float* T_final,
@@ -119,6 +127,7 @@ struct SortArgsT {
   int passes;
   int key_bits;   // the last pass only looks at the bits below key_bits
   int first_bit;  // pass p sorts on bits [first_bit + 8p, first_bit + 8p + 8)
+  const uint64_t* total_dev;  // if set and *total_dev > n_host (capacity overflow), do nothing
 };
 using SortArgs = SortArgsT<uint64_t>;
 using SortArgs32 = SortArgsT<uint32_t>;

@@ -83,7 +83,16 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
                                                        uint8_t* __restrict__ ws) {
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
   __shared__ uint32_t s_hist[4 * 256];
+  // the block's rectangles are first added into a shared copy of its first view's difference
+  // grid (when it fits), then flushed with one global atomic per non-zero cell
+  __shared__ int32_t s_grid[kProjGridCells];
+  const int gstride = L.Tx + 1;
+  const int gcells = gstride * (L.Ty + 1);
+  const bool use_sgrid = gcells <= kProjGridCells;
+  const int k_block = static_cast<int>((static_cast<int64_t>(blockIdx.x) * kProjBlock) / (L.N > 0 ? L.N : 1));
   for (int i = threadIdx.x; i < 4 * 256; i += kProjBlock) s_hist[i] = 0;
+  if (use_sgrid)
+    for (int i = threadIdx.x; i < gcells; i += kProjBlock) s_grid[i] = 0;
   __syncthreads();
   uint32_t count = 0, item_key = 0xffffffffu;
   if (idx < L.KN) {
@@ -196,7 +205,18 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
       y1 = static_cast<int>(y1f);
       radius = static_cast<int>(rf);
       count = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
-      if (count == 0) x0 = x1 = y0 = y1 = radius = 0;
+      if (count == 0) {
+        x0 = x1 = y0 = y1 = radius = 0;
+      } else {
+        // rectangle into the view's difference grid: its 2D prefix sum is the pairs per tile
+        int32_t* dg = (use_sgrid && k == k_block)
+                          ? s_grid
+                          : at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * gcells;
+        atomicAdd(&dg[y0 * gstride + x0], 1);
+        atomicAdd(&dg[y0 * gstride + x1], -1);
+        atomicAdd(&dg[y1 * gstride + x0], -1);
+        atomicAdd(&dg[y1 * gstride + x1], 1);
+      }
     }
     at<uint32_t>(ws, L.proj_depth_key)[idx] = __float_as_uint(zc);
     if (count) item_key = __float_as_uint(zc);
@@ -226,6 +246,11 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
     for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 0xffu)], 1u);
   }
   __syncthreads();
+  if (use_sgrid && k_block < L.K) {
+    int32_t* dg = at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k_block) * gcells;
+    for (int i = threadIdx.x; i < gcells; i += kProjBlock)
+      if (s_grid[i]) atomicAdd(&dg[i], s_grid[i]);
+  }
   uint32_t* hist = at<uint32_t>(ws, L.item_hist);
   for (int i = threadIdx.x; i < 4 * 256; i += kProjBlock)
     if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);

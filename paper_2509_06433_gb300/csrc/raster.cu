@@ -37,9 +37,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 // Staged splat: A = (x, y, qa, qb), B = (qc, opacity, depth, -), C = (r, g, b, -) where
 // (x, y) is the 2D mean relative to the tile origin and power * log2(e) = qa dx^2 + qb dx dy + qc dy^2.
+// Box = (x - hx, x + hx, y - hy, y + hy) bounds the ellipse where opacity * exp(power) >= 1/255,
+// widened by a safety margin: outside it no pixel can keep the splat, so a warp whose pixel
+// centres all lie outside skips the splat without changing any decision.
 template <int CH>
 struct Stage {
-  float4 A[CH], B[CH], C[CH];
+  float4 A[CH], B[CH], C[CH], Box[CH];
 };
 
 template <int CH>
@@ -50,11 +53,29 @@ __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layou
   const float4 uv = at<float4>(ws, L.proj_uv)[kg];
   const float4 cn = at<float4>(ws, L.proj_conic)[kg];
   const float4 co = at<float4>(ws, L.color_opacity)[gid];
-  S.A[j] = make_float4(__fadd_rn(__fsub_rn(uv.x, ox), uv.y), __fadd_rn(__fsub_rn(uv.z, oy), uv.w),
-                       __fmul_rn(cn.x, -0.5f * kLog2e), __fmul_rn(cn.y, -kLog2e));
+  const float x = __fadd_rn(__fsub_rn(uv.x, ox), uv.y), y = __fadd_rn(__fsub_rn(uv.z, oy), uv.w);
+  S.A[j] = make_float4(x, y, __fmul_rn(cn.x, -0.5f * kLog2e), __fmul_rn(cn.y, -kLog2e));
   S.B[j] = make_float4(__fmul_rn(cn.z, -0.5f * kLog2e), co.w, cn.w, 0.0f);
   S.C[j] = make_float4(co.x, co.y, co.z, 0.0f);
+  // o exp(-d^T X d / 2) >= 1/255  <=>  d^T X d <= 2 ln(255 o); the ellipse's half-extents are
+  // sqrt(t Sigma2_xx), sqrt(t Sigma2_yy) with Sigma2 = X^-1 (X = conic). Margins: 1% on t, 0.05 px.
+  // (the 1.0001 keeps opacities within rounding of 1/255 from being skipped)
+  const float t = 2.0f * logf(255.0f * 1.0001f * co.w);
+  float hx = -1.0f, hy = -1.0f;
+  if (t >= 0.0f) {
+    const float detX = cn.x * cn.z - cn.y * cn.y;
+    const float tt = 1.01f * t / detX;
+    hx = sqrtf(tt * cn.z) + 0.05f;  // Sigma2_xx = C / det(X)
+    hy = sqrtf(tt * cn.x) + 0.05f;  // Sigma2_yy = A / det(X)
+    if (!(hx == hx) || !(hy == hy) || !(detX > 0.0f)) hx = hy = 1e30f;  // degenerate: never skip
+  }
+  S.Box[j] = make_float4(x - hx, x + hx, y - hy, y + hy);
   return gid;
+}
+
+// True when the splat's box misses the pixel centres [0.5, 15.5] x [ylo, yhi] of a warp.
+__device__ __forceinline__ bool box_misses(const float4& b, float ylo, float yhi) {
+  return b.y < 0.5f || b.x > 15.5f || b.w < ylo || b.z > yhi;
 }
 
 // Opacity of a splat at pixel offset (dx, dy) with qadx = qa * dx. keep: the splat is not
@@ -106,6 +127,9 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
   const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
   const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
+  // this warp's pixel rows: (2 * warp) * PX .. (2 * warp + 2) * PX - 1
+  const float wylo = static_cast<float>((threadIdx.x >> 5) * 2 * PX) + 0.5f;
+  const float wyhi = wylo + static_cast<float>(2 * PX - 1);
   float T[PX], cr[PX], cg[PX], cb[PX], cd[PX];
   int32_t last[PX], stop_at[PX];
   bool done[PX];
@@ -131,6 +155,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
     const int pos0 = static_cast<int>(base - rg.x);
     for (int j = 0; j < n; ++j) {
       if (__all_sync(0xffffffffu, all_done)) break;
+      if (box_misses(S.Box[j], wylo, wyhi)) continue;
       const float4 A = S.A[j], B = S.B[j], C = S.C[j];
       const float dx = __fsub_rn(A.x, pxc);
       const float qadx = __fmul_rn(A.z, dx);
@@ -272,6 +297,8 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
   const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
   const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
+  const float wylo = static_cast<float>((threadIdx.x >> 5) * 2 * PX) + 0.5f;
+  const float wyhi = wylo + static_cast<float>(2 * PX - 1);
   const int4* tiles = at<int4>(ws, L.proj_tiles);
   float* pair_grads = at<float>(ws, L.pair_grads);
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
@@ -324,6 +351,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
     const int pos0 = static_cast<int>(base - rg.x);
     const int nw = min(n, warp_last - pos0);  // splats of this chunk this warp must visit
     for (int j = 0; j < nw; ++j) {
+      if (box_misses(S.Box[j], wylo, wyhi)) continue;
       const float4 A = S.A[j], B = S.B[j], C = S.C[j];
       const float dx = __fsub_rn(A.x, pxc);
       const float qadx = __fmul_rn(A.z, dx);

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, in
   const uint32_t* __restrict__ vin = a.vals[pass & 1];
   KeyT* __restrict__ kout = a.keys[(pass + 1) & 1];
   uint32_t* __restrict__ vout = a.vals[(pass + 1) & 1];
+  if (a.total_dev && *a.total_dev > static_cast<uint64_t>(a.n_host)) return;  // overflowed: reported, not sorted
   uint32_t n = static_cast<uint32_t>(a.n_host);
   if (a.n_dev) n = min(*a.n_dev, n);
   const uint32_t n_tiles = (n + kSortTileKeys - 1) / kSortTileKeys;
@@ -131,21 +132,32 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, in
       st_relaxed(&status[t], kFlagPrefix | cnt);
     } else {
       st_relaxed(&status[static_cast<size_t>(tile) * 256 + t], kFlagAggregate | cnt);
+      // Look back kLookahead predecessors per round trip: their statuses are loaded together
+      // and consumed in order until one is not ready yet (re-polled) or carries a prefix.
+      constexpr int kLookahead = 8;
       int64_t j = static_cast<int64_t>(tile) - 1;
       uint32_t spins = 0;
-      while (j >= 0) {
-        const uint32_t v = ld_relaxed(&status[static_cast<size_t>(j) * 256 + t]);
-        const uint32_t f = v & ~kValueMask;
-        if (f == 0) {
-          if (++spins > kSpinLimit) {
-            atomicOr(a.err, GS_DEVERR_TIMEOUT);
-            break;
-          }
-          continue;
+      bool found = false;
+      while (!found && j >= 0) {
+        uint32_t v[kLookahead];
+#pragma unroll
+        for (int q = 0; q < kLookahead; ++q)
+          v[q] = (j - q >= 0) ? ld_relaxed(&status[static_cast<size_t>(j - q) * 256 + t]) : 0u;
+        int consumed = 0;
+#pragma unroll
+        for (int q = 0; q < kLookahead; ++q) {
+          if (found || consumed != q || j - q < 0) continue;
+          const uint32_t f = v[q] & ~kValueMask;
+          if (f == 0) continue;  // not published yet: stop consuming, poll again from here
+          excl += v[q] & kValueMask;
+          ++consumed;
+          if (f == kFlagPrefix) found = true;
         }
-        excl += v & kValueMask;
-        if (f == kFlagPrefix) break;
-        --j;
+        j -= consumed;
+        if (consumed == 0 && ++spins > kSpinLimit) {
+          atomicOr(a.err, GS_DEVERR_TIMEOUT);
+          break;
+        }
       }
       st_relaxed(&status[static_cast<size_t>(tile) * 256 + t], kFlagPrefix | (excl + cnt));
     }
@@ -292,6 +304,7 @@ cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s) {
   a.passes = L.passes;
   a.key_bits = L.key_bits;
   a.first_bit = 32;
+  a.total_dev = &st->total_pairs;
   return launch_onesweep(a, s);
 }
 

@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the tracking and mapping-window fields")
     return ap.parse_args()
 
 
@@ -191,22 +192,37 @@ def run_ours(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---- device-resident timing: events around each step, L2 flushed between steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    # ---- per-stage breakdown (eager launches, events between the entry points)
+    n_stage = min(args.steps, 100)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(n_stage)]
+    for i in range(n_stage):
+        zero_grads()
+        flush.fill_(float(i))
+        step(evs[i])
+    torch.cuda.synchronize(dev)
+    stage_ms = {nm: [e[j].elapsed_time(e[j + 1]) for e in evs] for j, nm in enumerate(stage_names)}
+
+    # ---- the timed value: the whole mapping iteration replayed from one CUDA graph,
+    # CUDA events around each replay, L2 flushed (256 MB write) between replays
+    from paper_2509_06433_gb300.tracking import MappingStep
+    mstep = MappingStep(r, g, cams, rgb_t, depth_t, graph=True)
+    for _ in range(args.warmup):
+        mstep.replay()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
     clock_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
     os.makedirs(os.path.dirname(clock_path), exist_ok=True)
     with ClockSampler(clock_path) as clk:
         for i in range(args.steps):
-            zero_grads()
             flush.fill_(float(i))
-            step(evs[i])
+            ev0[i].record(stream)
+            mstep.replay()
+            ev1[i].record(stream)
         barrier()
-    step_ms = [e[0].elapsed_time(e[6]) for e in evs]
-    stage_ms = {nm: [e[j].elapsed_time(e[j + 1]) for e in evs] for j, nm in enumerate(stage_names)}
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = float(sum(step_ms))
     if world > 1:
-        import torch
         import torch.distributed as dist
         tt = torch.tensor([total_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -214,6 +230,13 @@ def run_ours(args, rank, world):
     code, err, pairs, evals = r.status()
     if code != 0:
         raise RuntimeError(f"device status {code} (error word {err}) in the timed region")
+    # the graph's gradients equal the eager step's (same kernels, deterministic)
+    zero_grads()
+    step()
+    torch.cuda.synchronize(dev)
+    for k in grads:
+        if not torch.equal(grads[k], mstep.grads[k]):
+            raise RuntimeError(f"graph replay and eager step disagree on {k}")
 
     # ---- end to end through the C ABI: pinned host inputs in, gradients + loss out
     host_in = [torch.as_tensor(a).pin_memory() for a in s.params()]
@@ -294,6 +317,130 @@ def run_ours(args, rank, world):
         "clocks": clocks,
     }
     return line
+
+
+# ----------------------------------------------------------------------------- secondary workloads
+
+def _pose_error(cam, ref):
+    from scipy.spatial.transform import Rotation
+    Ra = np.asarray(cam[4:13], np.float64).reshape(3, 3)
+    Rb = np.asarray(ref[4:13], np.float64).reshape(3, 3)
+    ang = float(np.degrees(np.linalg.norm(Rotation.from_matrix(Ra @ Rb.T).as_rotvec())))
+    ca = -Ra.T @ np.asarray(cam[13:16], np.float64)
+    cb = -Rb.T @ np.asarray(ref[13:16], np.float64)
+    return ang, float(np.linalg.norm(ca - cb))
+
+
+def measure_tracking(dev, iters=100, frames=3):
+    """Pose tracking (track300k): 100 pose-only fwd+bwd iterations per frame, each iteration
+    one CUDA-graph replay (render, L1, backward to the pose, on-device Adam step)."""
+    import torch
+    from paper_2509_06433_gb300 import api
+    from paper_2509_06433_gb300.tracking import Tracker
+    from scenes import make_scene
+    s = make_scene("track300k")
+    g = api.Gaussians.from_numpy(s.params(), device=dev)
+    true_cam = torch.as_tensor(s.cams).to(dev)
+    r = api.Rasterizer(s.W, s.H, 1, s.N, device=dev)
+    r.plan(g, true_cam)
+    obs = r.render(g, true_cam)  # the observed frame: a render at the true pose (input data)
+    start = torch.as_tensor(s.track_cams).to(dev)
+    cams = start.clone()
+    tr = Tracker(g, cams, s.W, s.H, obs["rgb"].clone(), obs["depth"].clone(), autotune=True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for f in range(frames):
+        cams.copy_(start)
+        tr.reset_optimizer()
+        flush.fill_(float(f))
+        e0.record()
+        tr.run(iters)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms += e0.elapsed_time(e1)
+    code = tr.status()[0]
+    before = _pose_error(s.track_cams[0], s.cams[0])
+    after = _pose_error(cams.cpu().numpy()[0], s.cams[0])
+    return {"workload": "track300k: 300k Gaussians (free + 3 planes), 640x480 f=525, start pose perturbed "
+                        "2 deg / 5 cm; 100 pose-only fwd+bwd iterations per frame, one CUDA graph per "
+                        "iteration; L2 flushed between frames",
+            "iters_per_s": frames * iters / (ms / 1e3), "ms_per_iter": ms / (frames * iters),
+            "rot_err_deg": [round(before[0], 4), round(after[0], 4)],
+            "trans_err_m": [round(before[1], 5), round(after[1], 5)], "status": code,
+            "px_per_thread": [tr.r.cfg.fwd_px_per_thread, tr.r.cfg.bwd_px_per_thread]}
+
+
+def measure_window(dev, reps=10):
+    """Mapping window (window500k: 500k Gaussians, K = 8 views): the batched form (one K-view
+    launch per stage, BF16 attributes, CUDA graph) against the plain form (8 single-view FP32
+    mapping steps launched eagerly one after the other)."""
+    import torch
+    from paper_2509_06433_gb300 import api, autotune
+    from paper_2509_06433_gb300.tracking import MappingStep
+    from scenes import make_scene
+    s = make_scene("window500k")
+    t = s.target
+    cams = torch.as_tensor(s.cams).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        ms = 0.0
+        for i in range(reps):
+            flush.fill_(float(i))
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms += e0.elapsed_time(e1)
+        return ms / reps
+
+    gb = api.Gaussians.from_numpy(s.params(), device=dev, dtype=torch.bfloat16)
+    rb = api.Rasterizer(s.W, s.H, s.K, s.N, device=dev)
+    pairs = rb.plan(gb, cams)
+    autotune.tune(rb, gb, cams)
+    tgt = rb.render(api.Gaussians.from_numpy(t.params(), device=dev, dtype=torch.bfloat16), cams)
+    rgb_t, depth_t = tgt["rgb"].clone(), tgt["depth"].clone()
+    rb.plan(gb, cams)
+    m = MappingStep(rb, gb, cams, rgb_t, depth_t, graph=True)
+    ms_batched = timed(m.replay)
+    assert rb.status()[0] == 0
+
+    g32 = api.Gaussians.from_numpy(s.params(), device=dev)
+    r1 = api.Rasterizer(s.W, s.H, 1, s.N, device=dev)
+    for k in range(s.K):
+        r1.plan(g32, cams[k:k + 1].contiguous())
+    views = [cams[k:k + 1].contiguous() for k in range(s.K)]
+    tg = [(rgb_t[k:k + 1].contiguous(), depth_t[k:k + 1].contiguous()) for k in range(s.K)]
+    out = r1.new_outputs()
+    g_rgb, g_depth = torch.empty_like(out["rgb"]), torch.empty_like(out["depth"])
+    loss = torch.zeros(1, device=dev)
+    grads = {"means": torch.zeros((s.N, 3), device=dev), "log_scales": torch.zeros((s.N, 3), device=dev),
+             "quats": torch.zeros((s.N, 4), device=dev), "opacity_logits": torch.zeros(s.N, device=dev),
+             "rgb": torch.zeros((s.N, 3), device=dev)}
+
+    def plain():
+        for v in grads.values():
+            v.zero_()
+        for k in range(s.K):
+            pose = torch.zeros((1, 6), device=dev)
+            api.gs_project(r1.cfg, g32, views[k], r1.ws)
+            api.gs_bin_sort(r1.cfg, r1.ws)
+            api.gs_raster_fwd(r1.cfg, r1.ws, out["rgb"], out["depth"], out["T"], out["last"])
+            api.gs_loss_l1(r1.cfg, out["rgb"], out["depth"], tg[k][0], tg[k][1], g_rgb, g_depth, loss, r1.ws)
+            api.gs_raster_bwd(r1.cfg, r1.ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth)
+            api.gs_project_bwd(r1.cfg, g32, views[k], r1.ws, {**grads, "pose": pose})
+
+    ms_plain = timed(plain)
+    assert r1.status()[0] == 0
+    return {"workload": "window500k: 500k Gaussians on 6 room walls + 10% free, K=8 views 640x480 on a "
+                        "0.3 m / +-10 deg random walk; fwd+bwd+L1 of all 8 views; L2 flushed between iterations",
+            "pairs": pairs,
+            "batched_bf16_graph_iters_per_s": 1e3 / ms_batched, "plain_fp32_sequential_iters_per_s": 1e3 / ms_plain,
+            "speedup": ms_plain / ms_batched,
+            "px_per_thread": [rb.cfg.fwd_px_per_thread, rb.cfg.bwd_px_per_thread]}
 
 
 def load_peaks():
@@ -384,6 +531,11 @@ def main():
         return 0
     line = run_ours(args, rank, world)
     if rank == 0:
+        if world == 1 and not args.no_extra:
+            import torch
+            dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+            line["tracking"] = measure_tracking(dev)
+            line["mapping_window"] = measure_window(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = oracle_step_rate(args.cpu_seconds)
         print(json.dumps(line))

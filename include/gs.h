@@ -219,6 +219,18 @@ GS_API gs_status_t gs_project_bwd(const gs_config_t* cfg, const gs_gaussians_t* 
 GS_API gs_status_t gs_screen_grads(const gs_config_t* cfg, const void* ws, size_t ws_bytes, float* d_mean2d, float* d_conic,
                             float* d_depth, float* d_opacity, float* d_rgb, void* stream);
 
+/* Pose update of render-based tracking (GS-SLAM variants that localise by optimising the
+ * camera pose against the rendered map, Sec. II-B). For each of the K views: one Adam step
+ * on the se(3) increment xi = (rho, phi) from the pose gradient of gs_project_bwd,
+ * xi = -(lr * m_hat / (sqrt(v_hat) + eps)) with lr_rho for rho and lr_phi for phi, then the
+ * left update T <- Exp(xi) T (rotation re-orthonormalised). d_cams [K] is updated in place;
+ * d_pose_grad [K,6] is read and, if zero_grad != 0, cleared for the next accumulation;
+ * d_state [K,16] floats (m[6], v[6], step count, 3 unused) must be zeroed before the first
+ * step. Device-only: suitable for capture in a CUDA graph. */
+GS_API gs_status_t gs_pose_adam_step(gs_camera_t* d_cams, float* d_pose_grad, float* d_state, int32_t K,
+                                     float lr_rho, float lr_phi, float beta1, float beta2, float eps, int32_t zero_grad,
+                                     void* stream);
+
 /* ---------------------------------------------------------------- sort primitive */
 
 /* Temporary bytes for gs_sort_pairs on n pairs (host call). */

@@ -132,6 +132,15 @@ def gs_read_status(cfg, ws, stream=None):
     return code, err.value, npairs.value, ev.value
 
 
+def gs_pose_adam_step(cams, pose_grad, state, lr_rho=1e-3, lr_phi=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                      zero_grad=True, stream=None):
+    """One on-device Adam step of every view's pose from its se(3) gradient (cams updated in place)."""
+    K = cams.shape[0]
+    call("gs_pose_adam_step", _p(cams), _p(pose_grad), _p(state), ctypes.c_int32(K), ctypes.c_float(lr_rho),
+         ctypes.c_float(lr_phi), ctypes.c_float(beta1), ctypes.c_float(beta2), ctypes.c_float(eps),
+         ctypes.c_int32(1 if zero_grad else 0), _s(stream))
+
+
 def gs_sort_pairs_tmp_size(n: int) -> int:
     b = ctypes.c_size_t()
     call("gs_sort_pairs_tmp_size", ctypes.c_int64(n), ctypes.byref(b))

@@ -1,0 +1,133 @@
+"""Render-based camera tracking and CUDA-graph-captured iterations.
+
+A tracking iteration renders the fixed Gaussian map at the current pose estimate,
+compares it with the observed frame (L1 on RGB + lambda L1 on depth), back-propagates
+to the se(3) pose only, and takes one Adam step on the pose (T <- Exp(xi) T), all on
+the device. ``Tracker`` captures one iteration in a CUDA graph and replays it, so an
+iteration costs one graph launch and no host round trip.
+
+``MappingStep`` does the same for a mapping iteration (fixed poses, gradients for every
+Gaussian parameter), so the K-view forward + backward of a mapping window replays as one
+graph.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+
+
+class _Captured:
+    def __init__(self, graph: bool):
+        self.use_graph = graph
+        self.graph = None
+
+    def _capture(self, body, warmup=2):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):  # first launches set kernel attributes outside the capture
+                body()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        if self.use_graph:
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                body()
+        self._body = body
+
+    def replay(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._body()
+
+
+class Tracker(_Captured):
+    """Pose tracking of K views against observed frames with a fixed map.
+
+    cams: [K,16] float32 CUDA tensor (updated in place by every iteration); rgb_obs
+    [K,3,H,W] and depth_obs [K,H,W]: the observed frames.
+    """
+
+    def __init__(self, g: api.Gaussians, cams: torch.Tensor, width: int, height: int, rgb_obs: torch.Tensor,
+                 depth_obs: torch.Tensor, lr_rho=2e-3, lr_phi=2e-3, lambda_depth=0.1, pair_headroom=1.5,
+                 graph=True, autotune=False):
+        super().__init__(graph)
+        self.g, self.cams = g, cams
+        K = cams.shape[0]
+        self.r = api.Rasterizer(width, height, K, g.N, device=cams.device, lambda_depth=lambda_depth)
+        total = self.r.plan(g, cams)
+        if total * pair_headroom > self.r.cap:
+            self.r._configure(int(total * pair_headroom) + 4096)
+        if autotune:
+            from . import autotune as at
+            at.tune(self.r, g, cams)
+        self.rgb_obs, self.depth_obs = rgb_obs, depth_obs
+        self.out = self.r.new_outputs()
+        d = cams.device
+        self.g_rgb = torch.empty_like(self.out["rgb"])
+        self.g_depth = torch.empty_like(self.out["depth"])
+        self.loss = torch.zeros(1, device=d)
+        self.pose_grad = torch.zeros((K, 6), device=d)
+        self.state = torch.zeros((K, 16), device=d)
+        self.lr = (lr_rho, lr_phi)
+        start = cams.clone()
+        self._capture(self._iteration)
+        cams.copy_(start)  # the warm-up iterations moved the pose: start from the given one
+        self.reset_optimizer()
+
+    def _iteration(self):
+        r, o = self.r, self.out
+        api.gs_project(r.cfg, self.g, self.cams, r.ws)
+        api.gs_bin_sort(r.cfg, r.ws)
+        api.gs_raster_fwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"])
+        api.gs_loss_l1(r.cfg, o["rgb"], o["depth"], self.rgb_obs, self.depth_obs, self.g_rgb, self.g_depth,
+                       self.loss, r.ws)
+        api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
+        api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, {"pose": self.pose_grad})
+        api.gs_pose_adam_step(self.cams, self.pose_grad, self.state, self.lr[0], self.lr[1])
+
+    def reset_optimizer(self):
+        self.state.zero_()
+        self.pose_grad.zero_()
+
+    def run(self, iters: int):
+        for _ in range(iters):
+            self.replay()
+        return self.cams
+
+    def status(self):
+        return self.r.status()
+
+
+class MappingStep(_Captured):
+    """One mapping iteration (fixed poses): render, L1 against the key-frames, backward to
+    every Gaussian parameter and the poses; gradients are zeroed at the start of the step."""
+
+    def __init__(self, r: api.Rasterizer, g: api.Gaussians, cams: torch.Tensor, rgb_t: torch.Tensor,
+                 depth_t: torch.Tensor, graph=True):
+        super().__init__(graph)
+        self.r, self.g, self.cams, self.rgb_t, self.depth_t = r, g, cams, rgb_t, depth_t
+        d = cams.device
+        N, K = g.N, cams.shape[0]
+        self.out = r.new_outputs()
+        self.g_rgb = torch.empty_like(self.out["rgb"])
+        self.g_depth = torch.empty_like(self.out["depth"])
+        self.loss = torch.zeros(1, device=d)
+        self.grads = {"means": torch.zeros((N, 3), device=d), "log_scales": torch.zeros((N, 3), device=d),
+                      "quats": torch.zeros((N, 4), device=d), "opacity_logits": torch.zeros(N, device=d),
+                      "rgb": torch.zeros((N, 3), device=d), "pose": torch.zeros((K, 6), device=d)}
+        self._capture(self._iteration)
+
+    def _iteration(self):
+        r, o = self.r, self.out
+        for v in self.grads.values():
+            v.zero_()
+        api.gs_project(r.cfg, self.g, self.cams, r.ws)
+        api.gs_bin_sort(r.cfg, r.ws)
+        api.gs_raster_fwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"])
+        api.gs_loss_l1(r.cfg, o["rgb"], o["depth"], self.rgb_t, self.depth_t, self.g_rgb, self.g_depth, self.loss,
+                       r.ws)
+        api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
+        api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, self.grads)

@@ -24,6 +24,7 @@ constexpr int kEmitThreads = 256;
 
 // Tiles touched by each item in depth order, and per-block totals for the scan.
 __global__ void __launch_bounds__(kProjBlock) k_sorted_counts(Layout L, uint8_t* __restrict__ ws) {
+  pdl_begin();
   const int64_t s = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
   uint32_t cnt = 0;
   if (s < L.KN) {
@@ -75,6 +76,7 @@ __device__ __forceinline__ uint64_t block_inclusive_scan1024(uint64_t x, uint64_
 // Exclusive scan of the per-block pair totals; total pair count, capacity check; clears the
 // pair sort's tile counters.
 __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(Layout L, uint8_t* __restrict__ ws) {
+  pdl_begin();
   const uint32_t* sums = at<uint32_t>(ws, L.block_sums);
   uint64_t* offs = at<uint64_t>(ws, L.block_offsets);
   __shared__ uint64_t tmp[32];
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(Layout L, uint8_t*
 // record the pair-parallel emission reads. Also stores the offset with the projection record
 // (the backward pass finds a pair's gradient slot from it).
 __global__ void __launch_bounds__(kProjBlock) k_item_offsets(Layout L, uint8_t* __restrict__ ws) {
+  pdl_begin();
   __shared__ uint32_t s_warp[kProjBlock / 32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t s = static_cast<int64_t>(blockIdx.x) * kProjBlock + t;
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(kProjBlock) k_item_offsets(Layout L, uint8_t* 
 // (ty, tx) then holds the number of pairs of tile (ty, tx). The grid is staged in shared
 // memory when it fits (row sums, then column sums), else summed in place in global memory.
 __global__ void k_tile_prefix(Layout L, uint8_t* __restrict__ ws) {
+  pdl_begin();
   __shared__ int32_t sg[kProjGridCells];
   const int stride = L.Tx + 1;
   const int cells = stride * (L.Ty + 1);
@@ -172,6 +176,7 @@ __global__ void k_tile_prefix(Layout L, uint8_t* __restrict__ ws) {
 // Exclusive scan of the per-tile pair counts over global tile ids: ranges (clamped to the
 // pairs actually emitted) and the digit histograms of the pair sort.
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* __restrict__ ws) {
+  pdl_begin();
   __shared__ uint64_t tmp[32];
   __shared__ uint32_t s_hist[4 * 256];
   for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
@@ -211,6 +216,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* _
 // Pairs [b * kEmitPairs, (b + 1) * kEmitPairs) of the emission order. Each pair finds its
 // item by binary search over the items' pair offsets, staged for the block's window.
 __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* __restrict__ ws) {
+  pdl_begin();
   __shared__ uint32_t s_off[kEmitPairs + 2];
   __shared__ int64_t s_lo, s_hi;
   const uint64_t n = at<Status>(ws, L.status)->num_pairs;
@@ -270,12 +276,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
 
 cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s) {
   auto* w = static_cast<uint8_t*>(ws);
-  k_sorted_counts<<<static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s>>>(L, w);
-  k_scan_blocks<<<1, kScanThreads, 0, s>>>(L, w);
-  k_item_offsets<<<static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s>>>(L, w);
-  k_tile_prefix<<<L.K, 256, 0, s>>>(L, w);
-  k_tile_scan<<<1, kScanThreads, 0, s>>>(L, w);
-  k_emit_pairs<<<static_cast<unsigned>(L.n_emit_blocks), kEmitThreads, 0, s>>>(L, w);
+  launch(k_sorted_counts, static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s, L, w);
+  launch(k_scan_blocks, 1, kScanThreads, 0, s, L, w);
+  launch(k_item_offsets, static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s, L, w);
+  launch(k_tile_prefix, L.K, 256, 0, s, L, w);
+  launch(k_tile_scan, 1, kScanThreads, 0, s, L, w);
+  launch(k_emit_pairs, static_cast<unsigned>(L.n_emit_blocks), kEmitThreads, 0, s, L, w);
   return cudaGetLastError();
 }
 

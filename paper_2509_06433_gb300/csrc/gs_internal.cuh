@@ -86,6 +86,33 @@ struct GaussPtrs {
   int dtype, means_dtype;
 };
 
+// ---------------------------------------------------------------------------- launches
+// Programmatic dependent launch: every kernel of the library begins with pdl_begin(), which
+// waits until the preceding grid of the stream has completed (its writes are then visible)
+// and lets the following grid start launching. Kernels are launched with the programmatic
+// stream-serialization attribute, so the launch latency of each kernel overlaps the tail of
+// the previous one. Outside such launches the two instructions are no-ops.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------------------- device helpers
 __device__ __forceinline__ float load_attr(const void* p, int64_t i, int dtype) {
   if (dtype == GS_F32) return static_cast<const float*>(p)[i];

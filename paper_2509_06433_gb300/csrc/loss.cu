@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(kThreads) k_loss(Layout L, const float* __rest
                                                   const float* __restrict__ depth, const float* __restrict__ rgb_t,
                                                   const float* __restrict__ depth_t, float* __restrict__ g_rgb,
                                                   float* __restrict__ g_depth, float* __restrict__ partials) {
+  pdl_begin();
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
   const int64_t total = HW * L.K;
   const float inv3 = 1.0f / (3.0f * static_cast<float>(HW));
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_loss(Layout L, const float* __rest
 }
 
 __global__ void k_loss_final(const float* __restrict__ partials, int n, float* __restrict__ out) {
+  pdl_begin();
   __shared__ float s[32];
   float acc = 0.0f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
@@ -66,9 +68,9 @@ __global__ void k_loss_final(const float* __restrict__ partials, int n, float* _
 cudaError_t launch_loss(const Layout& L, const float* rgb, const float* depth, const float* rgb_t,
                         const float* depth_t, float* g_rgb, float* g_depth, float* d_loss, void* ws, cudaStream_t s) {
   float* partials = at<float>(ws, L.loss_partials);
-  k_loss<<<static_cast<unsigned>(L.n_loss_blocks), kThreads, 0, s>>>(L, rgb, depth, rgb_t, depth_t, g_rgb, g_depth,
+  launch(k_loss, static_cast<unsigned>(L.n_loss_blocks), kThreads, 0, s, L, rgb, depth, rgb_t, depth_t, g_rgb, g_depth,
                                                                      partials);
-  k_loss_final<<<1, 1024, 0, s>>>(partials, static_cast<int>(L.n_loss_blocks), d_loss);
+  launch(k_loss_final, 1, 1024, 0, s, partials, static_cast<int>(L.n_loss_blocks), d_loss);
   return cudaGetLastError();
 }
 

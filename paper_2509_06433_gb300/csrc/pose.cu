@@ -33,6 +33,7 @@ __device__ __forceinline__ M3 mul(const M3& a, const M3& b) {
 
 __global__ void k_pose_adam(gs_camera_t* __restrict__ cams, float* __restrict__ grad, float* __restrict__ state, int K,
                             float lr_rho, float lr_phi, float b1, float b2, float eps, int zero_grad) {
+  pdl_begin();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   float* st = state + 16 * k;
@@ -115,7 +116,7 @@ extern "C" gs_status_t gs_pose_adam_step(gs_camera_t* d_cams, float* d_pose_grad
                                          int32_t zero_grad, void* stream) {
   if (!d_cams || !d_pose_grad || !d_state || K < 1 || K > 1024) return GS_ERR_INVALID_ARG;
   if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f)) return GS_ERR_INVALID_ARG;
-  gs::k_pose_adam<<<(K + 63) / 64, 64, 0, static_cast<cudaStream_t>(stream)>>>(d_cams, d_pose_grad, d_state, K, lr_rho,
+  gs::launch(gs::k_pose_adam, (K + 63) / 64, 64, 0, static_cast<cudaStream_t>(stream), d_cams, d_pose_grad, d_state, K, lr_rho,
                                                                                   lr_phi, beta1, beta2, eps, zero_grad);
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

@@ -81,6 +81,7 @@ __device__ __forceinline__ uint32_t pack16(int lo, int hi) {
 
 __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                        uint8_t* __restrict__ ws) {
+  pdl_begin();
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
   __shared__ uint32_t s_hist[4 * 256];
   // the block's rectangles are first added into a shared copy of its first view's difference
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
 }  // namespace
 
 cudaError_t launch_project(const Layout& L, const GaussPtrs& g, const gs_camera_t* cams, void* ws, cudaStream_t s) {
-  k_project<<<static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s>>>(L, g, cams, static_cast<uint8_t*>(ws));
+  launch(k_project, static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s, L, g, cams, static_cast<uint8_t*>(ws));
   return cudaGetLastError();
 }
 

@@ -77,6 +77,7 @@ __device__ __forceinline__ Sum10 sum_pairs_warp(const float* __restrict__ pg, ui
 __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                            const uint8_t* __restrict__ ws, gs_grads_t out,
                                                            float* __restrict__ pose_partials) {
+  pdl_begin();
   const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
   const bool valid = g < L.N;
   const int4* tiles = at<int4>(ws, L.proj_tiles);
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
 
 // pose[k][i] += sum over blocks of pose_partials[block][k][i], in block order.
 __global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_blocks, int K, float* __restrict__ pose) {
+  pdl_begin();
   const int k = blockIdx.x;
   const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float v = 0.0f;
@@ -272,6 +274,7 @@ __global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_bloc
 __global__ void __launch_bounds__(kPoseBlock) k_screen_grads(Layout L, const uint8_t* __restrict__ ws, float* d_mean2d,
                                                             float* d_conic, float* d_depth, float* d_opacity,
                                                             float* d_rgb) {
+  pdl_begin();
   const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
   const bool valid = g < L.N;  // no early return: the pair sums are warp-cooperative
   const int4* tiles = at<int4>(ws, L.proj_tiles);
@@ -310,16 +313,16 @@ cudaError_t launch_project_bwd(const Layout& L, const GaussPtrs& g, const gs_cam
                                const gs_grads_t& out, cudaStream_t s) {
   if (L.N == 0) return cudaSuccess;
   float* partials = at<float>(ws, L.pose_partials);
-  k_project_bwd<<<static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s>>>(L, g, cams, static_cast<uint8_t*>(ws),
+  launch(k_project_bwd, static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s, L, g, cams, static_cast<uint8_t*>(ws),
                                                                               out, partials);
-  if (out.pose) k_pose_reduce<<<L.K, 6 * 32, 0, s>>>(partials, L.n_pose_blocks, L.K, out.pose);
+  if (out.pose) launch(k_pose_reduce, L.K, 6 * 32, 0, s, partials, L.n_pose_blocks, L.K, out.pose);
   return cudaGetLastError();
 }
 
 cudaError_t launch_screen_grads(const Layout& L, const void* ws, float* d_mean2d, float* d_conic, float* d_depth,
                                 float* d_opacity, float* d_rgb, cudaStream_t s) {
   if (L.N == 0) return cudaSuccess;
-  k_screen_grads<<<static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s>>>(
+  launch(k_screen_grads, static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s, 
       L, static_cast<const uint8_t*>(ws), d_mean2d, d_conic, d_depth, d_opacity, d_rgb);
   return cudaGetLastError();
 }

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
                                                                  int32_t* __restrict__ out_last,
                                                                  uint64_t* __restrict__ evals_out,
                                                                  uint64_t* __restrict__ blended_out) {
+  pdl_begin();
   constexpr int kThreads = kTilePixels / PX;
   constexpr int kWarps = kThreads / 32;
   __shared__ Stage<kFwdChunk> S;
@@ -283,6 +284,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
                                                                  const float* __restrict__ g_rgb,
                                                                  const float* __restrict__ g_depth,
                                                                  const float* __restrict__ g_T) {
+  pdl_begin();
   constexpr int kThreads = kTilePixels / PX;
   constexpr int kWarps = kThreads / 32;
   __shared__ Stage<kBwdChunk> S;
@@ -352,46 +354,56 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
     const int nw = min(n, warp_last - pos0);  // splats of this chunk this warp must visit
     for (int j = 0; j < nw; ++j) {
       if (box_misses(S.Box[j], wylo, wyhi)) continue;
-      const float4 A = S.A[j], B = S.B[j], C = S.C[j];
+      const float4 A = S.A[j], B = S.B[j];
       const float dx = __fsub_rn(A.x, pxc);
       const float qadx = __fmul_rn(A.z, dx);
       const int pos = pos0 + j;
-      float v[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+      // phase 1: opacity and keep/skip decision for the thread's pixels
+      Alpha a[PX];
+      float dy[PX];
+      bool okq[PX];
       bool contrib = false;
 #pragma unroll
       for (int q = 0; q < PX; ++q) {
-        const float dy = __fsub_rn(A.y, pyc + static_cast<float>(q));
-        const Alpha a = splat_alpha(A, B, qadx, dx, dy);
-        const bool ok = a.keep && (pos < last[q]);
-        const bool open = ok && !(a.raw > kAlphaMax);  // the 0.99 clamp passes no gradient
+        dy[q] = __fsub_rn(A.y, pyc + static_cast<float>(q));
+        a[q] = splat_alpha(A, B, qadx, dx, dy[q]);
+        okq[q] = a[q].keep && (pos < last[q]);
+        contrib = contrib || okq[q];
+      }
+      // phase 2 (skipped when no pixel of the warp keeps the splat): gradient terms
+      if (!__any_sync(0xffffffffu, contrib)) continue;
+      const float4 C = S.C[j];
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < PX; ++q) {
+        const bool ok = okq[q];
+        const bool open = ok && !(a[q].raw > kAlphaMax);  // the 0.99 clamp passes no gradient
         const float Tq = T[q];
-        const float w = __fmul_rn(a.alpha, Tq);
+        const float w = __fmul_rn(a[q].alpha, Tq);
         const float cgz = C.x * gr[q] + C.y * gg[q] + C.z * gb[q] + B.z * gd[q];
         const float sg = Sg[q] - cgz * w;  // colour/depth behind this splat, weighted by dL/dpixel
-        const float dalpha = Tq * cgz - __fdividef(sg + hT[q], 1.0f - a.alpha);
+        const float dalpha = Tq * cgz - __fdividef(sg + hT[q], 1.0f - a[q].alpha);
         const float wm = ok ? w : 0.0f;
-        const float dpow = open ? a.alpha * dalpha : 0.0f;
+        const float dpow = open ? a[q].alpha * dalpha : 0.0f;
         const float dpl = dpow * kLn2;
+        const float yq = dy[q];
         v[5] += wm * gd[q];
         v[7] += wm * gr[q];
         v[8] += wm * gg[q];
         v[9] += wm * gb[q];
-        v[6] += open ? a.G * dalpha : 0.0f;
+        v[6] += open ? a[q].G * dalpha : 0.0f;
         v[2] += -0.5f * dx * dx * dpow;
-        v[3] += -dx * dy * dpow;
-        v[4] += -0.5f * dy * dy * dpow;
-        v[0] += (2.0f * qadx + A.w * dy) * dpl;
-        v[1] += (2.0f * B.x * dy + A.w * dx) * dpl;
+        v[3] += -dx * yq * dpow;
+        v[4] += -0.5f * yq * yq * dpow;
+        v[0] += (2.0f * qadx + A.w * yq) * dpl;
+        v[1] += (2.0f * B.x * yq + A.w * dx) * dpl;
         Sg[q] = ok ? sg : Sg[q];
-        T[q] = ok ? __fmaf_rn(-Tq, a.alpha, Tq) : Tq;
-        contrib = contrib || ok;
+        T[q] = ok ? __fmaf_rn(-Tq, a[q].alpha, Tq) : Tq;
       }
-      if (__any_sync(0xffffffffu, contrib)) {
-        warp_transpose_reduce16(v, lane);
-        if (!(lane & 1) && idx < 10) s_part[warp][j][idx] = v[0];
-      }
+      warp_transpose_reduce16(v, lane);
+      if (!(lane & 1) && idx < 10) s_part[warp][j][idx] = v[0];
     }
     __syncthreads();
     for (int jj = threadIdx.x; jj < n; jj += kThreads) {
@@ -435,9 +447,9 @@ cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* dept
   const unsigned grid = static_cast<unsigned>(L.n_tiles);
   const uint8_t* w = static_cast<const uint8_t*>(ws);
   switch (pick_px(L.fwd_px, kDefaultFwdPx)) {
-    case 1: k_raster_fwd<1><<<grid, kTilePixels, 0, s>>>(L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
-    case 2: k_raster_fwd<2><<<grid, kTilePixels / 2, 0, s>>>(L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
-    default: k_raster_fwd<4><<<grid, kTilePixels / 4, 0, s>>>(L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
+    case 1: launch(k_raster_fwd<1>, grid, kTilePixels, 0, s, L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
+    case 2: launch(k_raster_fwd<2>, grid, kTilePixels / 2, 0, s, L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
+    default: launch(k_raster_fwd<4>, grid, kTilePixels / 4, 0, s, L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
   }
   return cudaGetLastError();
 }
@@ -449,9 +461,9 @@ cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const
   const unsigned grid = static_cast<unsigned>(L.n_tiles);
   uint8_t* w = static_cast<uint8_t*>(ws);
   switch (pick_px(L.bwd_px, kDefaultBwdPx)) {
-    case 1: k_raster_bwd<1><<<grid, kTilePixels, 0, s>>>(L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
-    case 2: k_raster_bwd<2><<<grid, kTilePixels / 2, 0, s>>>(L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
-    default: k_raster_bwd<4><<<grid, kTilePixels / 4, 0, s>>>(L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
+    case 1: launch(k_raster_bwd<1>, grid, kTilePixels, 0, s, L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
+    case 2: launch(k_raster_bwd<2>, grid, kTilePixels / 2, 0, s, L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
+    default: launch(k_raster_bwd<4>, grid, kTilePixels / 4, 0, s, L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT); break;
   }
   return cudaGetLastError();
 }

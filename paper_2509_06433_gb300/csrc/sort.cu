@@ -72,6 +72,7 @@ __device__ __forceinline__ uint32_t digit_mask(const SortArgsT<KeyT>& a, int pas
 
 template <class KeyT>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, int pass) {
+  pdl_begin();
   extern __shared__ __align__(16) uint8_t smem_raw[];
   SortSmem<KeyT>& S = *reinterpret_cast<SortSmem<KeyT>*>(smem_raw);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, in
 
 // Digit histograms of every pass, and clearing of the look-back status of the used tiles.
 __global__ void k_sort_hist(SortArgs a) {
+  pdl_begin();
   __shared__ uint32_t s_hist[kMaxSortPasses * 256];
   for (int i = threadIdx.x; i < a.passes * 256; i += blockDim.x) s_hist[i] = 0;
   __syncthreads();
@@ -241,7 +243,7 @@ template <class KeyT>
 cudaError_t onesweep_passes(const SortArgsT<KeyT>& a, cudaStream_t s) {
   const int grid = sort_grid<KeyT>(a.max_tiles);
   for (int p = 0; p < a.passes; ++p)
-    k_onesweep<KeyT><<<grid, kSortThreads, sizeof(SortSmem<KeyT>), s>>>(a, p);
+    launch(k_onesweep<KeyT>, grid, kSortThreads, sizeof(SortSmem<KeyT>), s, a, p);
   return cudaGetLastError();
 }
 
@@ -256,7 +258,7 @@ cudaError_t launch_sort_prepare(const SortArgs& a, cudaStream_t s) {
   int64_t blocks = (a.n_host + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
-  k_sort_hist<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
+  launch(k_sort_hist, static_cast<unsigned>(blocks), 256, 0, s, a);
   return cudaGetLastError();
 }
 

@@ -242,6 +242,14 @@ GS_API gs_status_t gs_sort_pairs_tmp_size(int64_t n, size_t* bytes);
 GS_API gs_status_t gs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int32_t key_bits, void* tmp, size_t tmp_bytes,
                           uint32_t* d_err_word, void* stream);
 
+/* Diagnostic of the device-side error path (no counterpart in the paper): one 8-bit pass
+ * of the pair sort on n >= 7680 pairs with the first onesweep tile withheld, so the next
+ * tile's bounded look-back wait (about a second) runs out and sets GS_DEVERR_TIMEOUT in the
+ * device word d_err_word. The kernel then finishes normally; keys and vals are left in an
+ * unspecified order (all writes in bounds). tmp: gs_sort_pairs_tmp_size(n) bytes. */
+GS_API gs_status_t gs_sort_diag_withheld_tile(uint64_t* keys, uint32_t* vals, int64_t n, void* tmp, size_t tmp_bytes,
+                                              uint32_t* d_err_word, void* stream);
+
 /* Largest n accepted by gs_sort_pairs_noalloc. */
 #define GS_SORT_NOALLOC_MAX_PAIRS 1048576
 

@@ -26,7 +26,8 @@ GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 #: every entry point declared in include/gs.h
 EXPORTS = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
            "gs_raster_fwd", "gs_loss_l1", "gs_raster_bwd", "gs_project_bwd", "gs_screen_grads",
-           "gs_pose_adam_step", "gs_sort_pairs_tmp_size", "gs_sort_pairs", "gs_sort_pairs_noalloc")
+           "gs_pose_adam_step", "gs_sort_pairs_tmp_size", "gs_sort_pairs", "gs_sort_diag_withheld_tile",
+           "gs_sort_pairs_noalloc")
 
 
 class GsConfig(ctypes.Structure):
@@ -87,6 +88,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                 "gs_sort_pairs_tmp_size": [c_int64, P],
                 "gs_sort_pairs": [P, P, c_int64, c_int32, P, c_size_t, P, P],
                 "gs_sort_pairs_noalloc": [P, P, c_int64, c_int32, P, P],
+                "gs_sort_diag_withheld_tile": [P, P, c_int64, P, c_size_t, P, P],
                 "gs_pose_adam_step": [P, P, P, c_int32, c_float, c_float, c_float, c_float, c_float, c_int32, P],
             }
             for name, args in sig.items():

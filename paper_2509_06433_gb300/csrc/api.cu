@@ -304,3 +304,34 @@ gs_status_t gs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int32_t key
 }
 
 }  // extern "C"
+
+// Diagnostic: one 8-bit pass of the pair sort with tile 0 withheld. Nothing ever publishes
+// tile 0's look-back status, so tile 1's bounded wait must run out and set
+// GS_DEVERR_TIMEOUT in d_err_word. The keys come out unsorted (but every write stays in
+// bounds); the call exists to exercise the device-side error path.
+extern "C" gs_status_t gs_sort_diag_withheld_tile(uint64_t* keys, uint32_t* vals, int64_t n, void* tmp, size_t tmp_bytes,
+                                                  uint32_t* d_err_word, void* stream) {
+  if (n < 2 * gs::kSortTileKeys || n > (1LL << 30) - 1 || !keys || !vals || !tmp || !d_err_word)
+    return GS_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(tmp) % 256) != 0) return GS_ERR_INVALID_ARG;
+  const SortTmp t = sort_tmp_layout(n);
+  if (tmp_bytes < t.total) return GS_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  gs::SortArgs a{};
+  a.keys[0] = keys;
+  a.vals[0] = vals;
+  a.keys[1] = gs::at<uint64_t>(tmp, t.keys);
+  a.vals[1] = gs::at<uint32_t>(tmp, t.vals);
+  a.n_host = n;
+  a.hist = gs::at<uint32_t>(tmp, t.hist);
+  a.tile_status = gs::at<uint32_t>(tmp, t.status);
+  a.tile_ctr = gs::at<uint32_t>(tmp, t.ctr);
+  a.err = d_err_word;
+  a.max_tiles = t.max_tiles;
+  a.passes = 1;
+  a.key_bits = 8;
+  a.first_tile = 1;
+  cudaError_t e = gs::launch_sort_prepare(a, s);
+  if (e == cudaSuccess) e = gs::launch_onesweep(a, s);
+  return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}

@@ -21,7 +21,7 @@ constexpr int kSortTileKeys = kSortThreads * kSortItems;
 constexpr int kMaxSortPasses = 8;
 constexpr int kPairGradStride = 12;   // floats per pair gradient record (10 used)
 constexpr int kPoseBlock = 256;       // Gaussians per projection-backward block
-constexpr uint32_t kSpinLimit = 1u << 22;  // bounded decoupled look-back
+constexpr uint32_t kSpinLimit = 1u << 21;  // bounded decoupled look-back (about a second of polling)
 constexpr int kDefaultFwdPx = 2;      // pixels per thread of the compositing kernels when
 constexpr int kDefaultBwdPx = 2;      // gs_config_t leaves the choice to the library
 
@@ -155,6 +155,7 @@ struct SortArgsT {
   int key_bits;   // the last pass only looks at the bits below key_bits
   int first_bit;  // pass p sorts on bits [first_bit + 8p, first_bit + 8p + 8)
   const uint64_t* total_dev;  // if set and *total_dev > n_host (capacity overflow), do nothing
+  uint32_t first_tile;        // diagnostic: 1 withholds tile 0, so its successors' waits run out
 };
 using SortArgs = SortArgsT<uint64_t>;
 using SortArgs32 = SortArgsT<uint32_t>;

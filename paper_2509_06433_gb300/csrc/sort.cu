@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, in
   S.bucket[t] = block_exclusive_scan(a.hist[pass * 256 + t], S.scan_tmp);
 
   for (;;) {
-    if (t == 0) S.tile = atomicAdd(&a.tile_ctr[pass], 1u);
+    if (t == 0) S.tile = atomicAdd(&a.tile_ctr[pass], 1u) + a.first_tile;
     __syncthreads();
     const uint32_t tile = S.tile;
     if (tile >= n_tiles) break;

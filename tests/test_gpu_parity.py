@@ -304,3 +304,24 @@ def test_autotuner_picks_a_variant():
     assert (r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread) == res["choice"]
     check_images(to_np(r.render(g, ct)), oracle_fwd("fwd10k"))
     r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0
+
+
+def test_aerial_two_views_fp16_storage_forward_and_backward():
+    """Aerial workload shape (ground + boxes + large translucent Gaussians, 20 deg down-tilt)
+    with FP16 attribute storage over two views, against the oracle on the dequantised values."""
+    torch, api = torch_mods()
+    s = make_scene("aerial2m", n=30_000, K=2, W=320, H=180, f=225.0)
+    stored = [torch.as_tensor(a).to(torch.float16).float().numpy() for a in s.params()[1:]]
+    params = (s.means,) + tuple(stored)
+    orc = oracle.forward(params, s.cams, s.W, s.H)
+    r, g, ct, out = gpu_render(s.params(), s.cams, s.W, s.H, dtype=torch.float16)
+    d = read_discrete(r)
+    np.testing.assert_array_equal(d["keys"], orc["lists"].keys)
+    np.testing.assert_array_equal(d["vals"], orc["lists"].vals)
+    check_images(to_np(out), orc)
+    gr, gd = random_image(31, (s.K, 3, s.H, s.W)), random_image(32, (s.K, s.H, s.W))
+    og = oracle.backward(params, s.cams, s.W, s.H, orc["lists"], gr, gd)
+    grads = to_np(r.backward(g, ct, out, torch.as_tensor(gr).cuda(), torch.as_tensor(gd).cuda()))
+    for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose"):
+        e = rel_l2(grads[k], og[k])
+        assert e < GRAD_RTOL, (k, e)

@@ -43,8 +43,10 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->fwd_px = cfg->fwd_px_per_thread;
   L->bwd_px = cfg->bwd_px_per_thread;
   L->n_proj_blocks = L->KN > 0 ? (L->KN + kProjBlock - 1) / kProjBlock : 1;
-  L->max_sort_tiles = (L->cap + kSortTileKeys - 1) / kSortTileKeys;
-  L->max_item_tiles = L->KN > 0 ? (L->KN + kSortTileKeys - 1) / kSortTileKeys : 1;
+  L->item_sort_items = pick_sort_items(L->KN);
+  L->pair_sort_items = pick_sort_items(L->cap);
+  L->max_sort_tiles = sort_tiles(L->cap, L->pair_sort_items);
+  L->max_item_tiles = sort_tiles(L->KN, L->item_sort_items);
   L->n_pose_blocks = L->N > 0 ? (L->N + kPoseBlock - 1) / kPoseBlock : 1;
   const int64_t pixels = static_cast<int64_t>(L->K) * L->W * L->H;
   L->n_loss_blocks = (pixels + 255) / 256 < 1024 ? (pixels + 255) / 256 : 1024;
@@ -245,10 +247,12 @@ namespace {
 struct SortTmp {
   size_t keys, vals, hist, ctr, err, status, total;
   int64_t max_tiles;
+  int items;
 };
-SortTmp sort_tmp_layout(int64_t n) {
+SortTmp sort_tmp_layout(int64_t n, int items) {
   SortTmp t{};
-  t.max_tiles = n > 0 ? (n + kSortTileKeys - 1) / kSortTileKeys : 1;
+  t.items = items;
+  t.max_tiles = sort_tiles(n, items);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at_ = o;
@@ -268,7 +272,7 @@ SortTmp sort_tmp_layout(int64_t n) {
 
 gs_status_t gs_sort_pairs_tmp_size(int64_t n, size_t* bytes) {
   if (!bytes || n < 0 || n > (1LL << 30) - 1) return GS_ERR_INVALID_ARG;
-  *bytes = sort_tmp_layout(n).total;
+  *bytes = sort_tmp_layout(n, pick_sort_items(n)).total;
   return GS_OK;
 }
 
@@ -277,10 +281,11 @@ gs_status_t gs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int32_t key
   if (n < 0 || n > (1LL << 30) - 1 || key_bits < 1 || key_bits > 64) return GS_ERR_INVALID_ARG;
   if (n == 0) return GS_OK;
   if (!keys || !vals || !tmp || (reinterpret_cast<uintptr_t>(tmp) % kAlign) != 0) return GS_ERR_INVALID_ARG;
-  const SortTmp t = sort_tmp_layout(n);
+  const SortTmp t = sort_tmp_layout(n, pick_sort_items(n));
   if (tmp_bytes < t.total) return GS_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   SortArgs a{};
+  a.items = t.items;
   a.keys[0] = keys;
   a.vals[0] = vals;
   a.keys[1] = at<uint64_t>(tmp, t.keys);
@@ -314,10 +319,11 @@ extern "C" gs_status_t gs_sort_diag_withheld_tile(uint64_t* keys, uint32_t* vals
   if (n < 2 * gs::kSortTileKeys || n > (1LL << 30) - 1 || !keys || !vals || !tmp || !d_err_word)
     return GS_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(tmp) % 256) != 0) return GS_ERR_INVALID_ARG;
-  const SortTmp t = sort_tmp_layout(n);
+  const SortTmp t = sort_tmp_layout(n, gs::kSortItems);
   if (tmp_bytes < t.total) return GS_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   gs::SortArgs a{};
+  a.items = t.items;
   a.keys[0] = keys;
   a.vals[0] = vals;
   a.keys[1] = gs::at<uint64_t>(tmp, t.keys);

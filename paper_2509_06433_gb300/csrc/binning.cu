@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
   const uint64_t n = at<Status>(ws, L.status)->num_pairs;
   // clear the pair sort's look-back status (grid-stride over the tiles in use)
   {
-    const uint64_t used = (n + kSortTileKeys - 1) / kSortTileKeys * 256;
+    const uint64_t used = static_cast<uint64_t>(sort_tiles(static_cast<int64_t>(n), L.pair_sort_items)) * 256;
     const uint64_t gsize = static_cast<uint64_t>(gridDim.x) * kEmitThreads;
     uint32_t* sstat = at<uint32_t>(ws, L.sort_status);
     for (int p = 0; p < L.passes; ++p)

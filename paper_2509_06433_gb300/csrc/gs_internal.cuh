@@ -16,7 +16,7 @@ constexpr int kProjBlock = 256;       // (view, Gaussian) items per projection /
 constexpr int kEmitPairs = 2048;      // pairs emitted per emission block
 constexpr int kProjGridCells = 6144;  // largest (Tx+1)(Ty+1) difference grid kept in shared memory
 constexpr int kSortThreads = 256;     // onesweep block
-constexpr int kSortItems = 15;        // keys per thread per onesweep tile
+constexpr int kSortItems = 15;        // keys per thread per onesweep tile (default; 8 also built)
 constexpr int kSortTileKeys = kSortThreads * kSortItems;
 constexpr int kMaxSortPasses = 8;
 constexpr int kPairGradStride = 12;   // floats per pair gradient record (10 used)
@@ -44,11 +44,12 @@ struct Layout {
   int64_t n_tiles;          // K * Tx * Ty
   int tile_bits, key_bits;
   int passes;               // pair-sort passes over the tile bits: ceil(tile_bits / 8)
-  int64_t max_item_tiles;   // ceil(KN / kSortTileKeys): onesweep tiles of the per-item depth sort
+  int item_sort_items, pair_sort_items;  // keys per thread of the onesweep tiles of the two sorts
+  int64_t max_item_tiles;   // onesweep tiles of the per-item depth sort
   float near_plane, lambda_depth;
   int fwd_px, bwd_px;       // pixels per thread of the compositing kernels (0 = default)
   int64_t n_proj_blocks;    // ceil(KN / kProjBlock)
-  int64_t max_sort_tiles;   // ceil(cap / kSortTileKeys)
+  int64_t max_sort_tiles;   // onesweep tiles of the pair sort at capacity
   int64_t n_pose_blocks;    // ceil(N / kPoseBlock)
   int64_t n_loss_blocks;
   // byte offsets into the workspace
@@ -156,7 +157,17 @@ struct SortArgsT {
   int first_bit;  // pass p sorts on bits [first_bit + 8p, first_bit + 8p + 8)
   const uint64_t* total_dev;  // if set and *total_dev > n_host (capacity overflow), do nothing
   uint32_t first_tile;        // diagnostic: 1 withholds tile 0, so its successors' waits run out
+  int items;                  // keys per thread per tile: 8 or 15 (0: kSortItems)
 };
+__host__ __device__ inline int sort_items(int items) { return items == 8 ? items : kSortItems; }
+// onesweep tiles of n keys at `items` keys per thread
+__host__ __device__ inline int64_t sort_tiles(int64_t n, int items) {
+  const int64_t tk = static_cast<int64_t>(kSortThreads) * sort_items(items);
+  return n > 0 ? (n + tk - 1) / tk : 1;
+}
+// Keys per thread for a sort of up to n keys: small sorts take short tiles, so that enough
+// blocks share the work.
+inline int pick_sort_items(int64_t n) { return n <= 600000 ? 8 : kSortItems; }
 using SortArgs = SortArgsT<uint64_t>;
 using SortArgs32 = SortArgsT<uint32_t>;
 cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s);

@@ -12,11 +12,11 @@
 // operands, so the backward pass takes exactly the forward pass's skip and stop decisions
 // and recovers the same transmittance T_i front to back, without storing per-splat alphas.
 //
-// The backward pass sums each splat's 10 gradient terms over a warp's pixels (PX per lane,
-// then a transpose-reduce: 16 shuffles for 16 padded values), writes one partial per warp
-// into shared memory, and at the end of each chunk sums the warp partials in a fixed order
-// into one record per (splat, tile) pair of the pair-gradient buffer. No global atomics:
-// the gradients are deterministic.
+// The backward pass sums each splat's 10 gradient sums over a warp's pixels (PX per lane,
+// then a 12-shuffle warp reduction), writes one partial per warp into shared memory, and at
+// the end of each chunk sums the warp partials in a fixed order into one record per
+// (splat, tile) pair of the pair-gradient buffer. No global atomics: the gradients are
+// deterministic.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -37,13 +37,51 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 // Staged splat: A = (x, y, qa, qb), B = (qc, opacity, depth, -), C = (r, g, b, -) where
 // (x, y) is the 2D mean relative to the tile origin and power * log2(e) = qa dx^2 + qb dx dy + qc dy^2.
-// Box = (x - hx, x + hx, y - hy, y + hy) bounds the ellipse where opacity * exp(power) >= 1/255,
-// widened by a safety margin: outside it no pixel can keep the splat, so a warp whose pixel
-// centres all lie outside skips the splat without changing any decision.
+// rows: bit r is set when the splat's ellipse {opacity * 2^power >= 1/255}, widened by a safety
+// margin, meets the pixel-centre row y = r + 0.5 of the tile within the columns [0.5, 15.5].
+// A warp none of whose rows is set skips the splat without changing any decision.
 template <int CH>
 struct Stage {
-  float4 A[CH], B[CH], C[CH], Box[CH];
+  float4 A[CH], B[CH], C[CH];
+  uint32_t rows[CH];
 };
+
+// Rows of the tile (bit r: pixel-centre row r) met by the ellipse Q(d) = Qa dx^2 + Qb dx dy +
+// Qc dy^2 <= tau around (mx, my), inside the column strip [0.5, 15.5]. The ellipse's part
+// inside the strip is convex, so its y-extent is an interval: its ends are the ellipse's
+// top / bottom points when they lie inside the strip, else the ellipse's crossings of the
+// strip edge on their side. Margins: 2% + 2e-4 on tau (log2 units), 0.05 px on the strip, 0.05
+// px + 0.2% of the half-height on the interval. Anything that is not a proper ellipse keeps
+// every row.
+__device__ __forceinline__ uint32_t splat_rows(float mx, float my, float Qa, float Qb, float Qc, float opacity) {
+  const float tau0 = log2f(255.0f * opacity);
+  const float tau = tau0 + 0.02f * fabsf(tau0) + 2e-4f;
+  if (!(tau >= 0.0f)) return 0u;  // opacity below 1/255 (or NaN): no pixel keeps the splat
+  // determinant Qa Qc - (Qb/2)^2 with the products' rounding errors restored (no cancellation)
+  const float h = 0.5f * Qb;
+  const float p1 = Qa * Qc, p2 = h * h;
+  const float D = (p1 - p2) + (fmaf(Qa, Qc, -p1) - fmaf(h, h, -p2));
+  if (!(Qa > 0.0f) || !(Qc > 0.0f) || !(D > 0.0f)) return 0xffffu;
+  const float hx = sqrtf(tau * Qc / D), hy = sqrtf(tau * Qa / D);
+  if (!(hx < 1e7f) || !(hy < 1e7f)) return 0xffffu;
+  constexpr float xa = 0.5f - 0.05f, xb = 15.5f + 0.05f;
+  if (mx + hx < xa || mx - hx > xb) return 0u;
+  const float sl = h / Qa;  // the ellipse's widest chord at height dy is centred on mx - sl dy
+  const float xt = mx - sl * hy, xbot = mx + sl * hy;
+  // dy where the ellipse crosses x = xe (upper: sign +1)
+  auto cross = [&](float xe, float sign) {
+    const float dxe = xe - mx, ad = fabsf(dxe);
+    const float disc = fmaxf(D * (hx - ad) * (hx + ad), 0.0f);  // Qc tau - D dxe^2
+    return (fmaf(sign, sqrtf(disc), -h * dxe)) / Qc;
+  };
+  const float up = xt < xa ? cross(xa, 1.0f) : (xt > xb ? cross(xb, 1.0f) : hy);
+  const float dn = xbot < xa ? cross(xa, -1.0f) : (xbot > xb ? cross(xb, -1.0f) : -hy);
+  const float mm = fmaf(2e-3f, hy, 0.05f);
+  const float r0 = fmaxf(ceilf(my + dn - mm - 0.5f), 0.0f);
+  const float r1 = fminf(floorf(my + up + mm - 0.5f), 15.0f);
+  if (r0 > r1) return 0u;  // (a NaN bound leaves its side at the tile edge)
+  return (2u << static_cast<int>(r1)) - (1u << static_cast<int>(r0));
+}
 
 template <int CH>
 __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layout& L, const uint8_t* ws,
@@ -54,28 +92,12 @@ __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layou
   const float4 cn = at<float4>(ws, L.proj_conic)[kg];
   const float4 co = at<float4>(ws, L.color_opacity)[gid];
   const float x = __fadd_rn(__fsub_rn(uv.x, ox), uv.y), y = __fadd_rn(__fsub_rn(uv.z, oy), uv.w);
-  S.A[j] = make_float4(x, y, __fmul_rn(cn.x, -0.5f * kLog2e), __fmul_rn(cn.y, -kLog2e));
-  S.B[j] = make_float4(__fmul_rn(cn.z, -0.5f * kLog2e), co.w, cn.w, 0.0f);
+  const float qa = __fmul_rn(cn.x, -0.5f * kLog2e), qb = __fmul_rn(cn.y, -kLog2e), qc = __fmul_rn(cn.z, -0.5f * kLog2e);
+  S.A[j] = make_float4(x, y, qa, qb);
+  S.B[j] = make_float4(qc, co.w, cn.w, 0.0f);
   S.C[j] = make_float4(co.x, co.y, co.z, 0.0f);
-  // o exp(-d^T X d / 2) >= 1/255  <=>  d^T X d <= 2 ln(255 o); the ellipse's half-extents are
-  // sqrt(t Sigma2_xx), sqrt(t Sigma2_yy) with Sigma2 = X^-1 (X = conic). Margins: 1% on t, 0.05 px.
-  // (the 1.0001 keeps opacities within rounding of 1/255 from being skipped)
-  const float t = 2.0f * logf(255.0f * 1.0001f * co.w);
-  float hx = -1.0f, hy = -1.0f;
-  if (t >= 0.0f) {
-    const float detX = cn.x * cn.z - cn.y * cn.y;
-    const float tt = 1.01f * t / detX;
-    hx = sqrtf(tt * cn.z) + 0.05f;  // Sigma2_xx = C / det(X)
-    hy = sqrtf(tt * cn.x) + 0.05f;  // Sigma2_yy = A / det(X)
-    if (!(hx == hx) || !(hy == hy) || !(detX > 0.0f)) hx = hy = 1e30f;  // degenerate: never skip
-  }
-  S.Box[j] = make_float4(x - hx, x + hx, y - hy, y + hy);
+  S.rows[j] = splat_rows(x, y, -qa, -qb, -qc, co.w);
   return gid;
-}
-
-// True when the splat's box misses the pixel centres [0.5, 15.5] x [ylo, yhi] of a warp.
-__device__ __forceinline__ bool box_misses(const float4& b, float ylo, float yhi) {
-  return b.y < 0.5f || b.x > 15.5f || b.w < ylo || b.z > yhi;
 }
 
 // Opacity of a splat at pixel offset (dx, dy) with qadx = qa * dx. keep: the splat is not
@@ -129,8 +151,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
   const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
   // this warp's pixel rows: (2 * warp) * PX .. (2 * warp + 2) * PX - 1
-  const float wylo = static_cast<float>((threadIdx.x >> 5) * 2 * PX) + 0.5f;
-  const float wyhi = wylo + static_cast<float>(2 * PX - 1);
+  const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
   float T[PX], cr[PX], cg[PX], cb[PX], cd[PX];
   int32_t last[PX], stop_at[PX];
   bool done[PX];
@@ -156,7 +177,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
     const int pos0 = static_cast<int>(base - rg.x);
     for (int j = 0; j < n; ++j) {
       if (__all_sync(0xffffffffu, all_done)) break;
-      if (box_misses(S.Box[j], wylo, wyhi)) continue;
+      if (!(S.rows[j] & wrows)) continue;
       const float4 A = S.A[j], B = S.B[j], C = S.C[j];
       const float dx = __fsub_rn(A.x, pxc);
       const float qadx = __fmul_rn(A.z, dx);
@@ -228,45 +249,47 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
 
 // ============================================================================ backward
 
-// 16 values per lane -> each value summed over the warp. On return v[0] of lane l holds
-// the sum of value index ((l>>4)&1)*8 + ((l>>3)&1)*4 + ((l>>2)&1)*2 + ((l>>1)&1)
-// (lanes l and l^1 hold the same sum).
-__device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane) {
-  {
-    const bool hi = lane & 16;
+// Sum of 10 values over a warp, leaving each value in some lane (12 shuffles): halves of
+// the value set are exchanged across lane bit 4 (5 pairs), then bit 3 (2 pairs + 1 plain),
+// bit 2 (1 pair + 1 plain), bit 1 (1 pair), bit 0 (plain). On return, lane l with l & 1 == 0
+// holds value reduce10_index(l) when (l & 2) == 0 or (l & 12) == 0.
+__device__ __forceinline__ float warp_reduce10(const float (&x)[10], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float y[5];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float send = hi ? v[i] : v[i + 8];
-      const float keep = hi ? v[i + 8] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
+  for (int i = 0; i < 5; ++i) {
+    const float send = b4 ? x[i] : x[i + 5];
+    const float keep = b4 ? x[i + 5] : x[i];
+    y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
-  {
-    const bool hi = lane & 8;
+  float z[3];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float send = hi ? v[i] : v[i + 4];
-      const float keep = hi ? v[i + 4] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
+  for (int i = 0; i < 2; ++i) {
+    const float send = b3 ? y[2 * i] : y[2 * i + 1];
+    const float keep = b3 ? y[2 * i + 1] : y[2 * i];
+    z[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
+  z[2] = y[4] + __shfl_xor_sync(0xffffffffu, y[4], 8);
+  float w[2];
   {
-    const bool hi = lane & 4;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float send = hi ? v[i] : v[i + 2];
-      const float keep = hi ? v[i + 2] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
+    const float send = b2 ? z[0] : z[1];
+    const float keep = b2 ? z[1] : z[0];
+    w[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
+  w[1] = z[2] + __shfl_xor_sync(0xffffffffu, z[2], 4);
+  float u;
   {
-    const bool hi = lane & 2;
-    const float send = hi ? v[0] : v[1];
-    const float keep = hi ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    const float send = b1 ? w[0] : w[1];
+    const float keep = b1 ? w[1] : w[0];
+    u = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return u + __shfl_xor_sync(0xffffffffu, u, 1);
 }
+__device__ __forceinline__ int reduce10_index(int lane) {
+  const int half = (lane & 16) ? 5 : 0;
+  return (lane & 2) ? half + 4 : half + ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1);
+}
+__device__ __forceinline__ bool reduce10_writer(int lane) { return !(lane & 1) && (!(lane & 2) || !(lane & 12)); }
 
 __device__ __forceinline__ uint32_t pair_slot(const int4& tl, int tx, int ty) {
   const uint32_t x0 = static_cast<uint32_t>(tl.y) & 0xffffu, x1 = static_cast<uint32_t>(tl.y) >> 16;
@@ -275,6 +298,14 @@ __device__ __forceinline__ uint32_t pair_slot(const int4& tl, int tx, int ty) {
 }
 
 // Gradient record layout (floats): 0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 dz, 6 do, 7 dr, 8 dg, 9 db.
+//
+// Per pixel, with dpow = dL/dpower / ln 2 (zero where the splat is skipped or clamped) and
+// (dx, dy) the offset mean - pixel centre, the geometric terms are sums over the pixels of
+//   du = ln2 (2 qa dx + qb dy) dpow,  dv = ln2 (qb dx + 2 qc dy) dpow,
+//   dA = -dx^2 dpow / 2,  dB = -dx dy dpow,  dC = -dy^2 dpow / 2,  do = dpow / opacity.
+// A lane's pixels share dx, so it keeps only P0 = sum dpow, P1 = sum dy dpow, P2 = sum dy^2 dpow
+// and the warp reduces R = (dx P0, P1, dx^2 P0, dx P1, P2, P0); the splat's coefficients
+// qa, qb, qc, opacity are applied once per pair when the warp partials are summed.
 template <int PX>
 __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8_t* __restrict__ ws,
                                                                  const float* __restrict__ rgb,
@@ -299,8 +330,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
   const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
   const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
-  const float wylo = static_cast<float>((threadIdx.x >> 5) * 2 * PX) + 0.5f;
-  const float wyhi = wylo + static_cast<float>(2 * PX - 1);
+  const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
   const int4* tiles = at<int4>(ws, L.proj_tiles);
   float* pair_grads = at<float>(ws, L.pair_grads);
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
@@ -336,7 +366,8 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) max_last = max(max_last, s_maxlast[w]);
   const uint32_t stop = min(rg.y, rg.x + static_cast<uint32_t>(max_last));
-  const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+  const int idx = reduce10_index(lane);
+  const bool writer = reduce10_writer(lane);
   constexpr float kLn2 = 0.6931471805599453f;
 
   for (uint32_t base = rg.x; base < stop; base += kBwdChunk) {
@@ -353,7 +384,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
     const int pos0 = static_cast<int>(base - rg.x);
     const int nw = min(n, warp_last - pos0);  // splats of this chunk this warp must visit
     for (int j = 0; j < nw; ++j) {
-      if (box_misses(S.Box[j], wylo, wyhi)) continue;
+      if (!(S.rows[j] & wrows)) continue;
       const float4 A = S.A[j], B = S.B[j];
       const float dx = __fsub_rn(A.x, pxc);
       const float qadx = __fmul_rn(A.z, dx);
@@ -373,9 +404,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
       // phase 2 (skipped when no pixel of the warp keeps the splat): gradient terms
       if (!__any_sync(0xffffffffu, contrib)) continue;
       const float4 C = S.C[j];
-      float v[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+      float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f, cz = 0.0f, cr = 0.0f, cgr = 0.0f, cb = 0.0f;
 #pragma unroll
       for (int q = 0; q < PX; ++q) {
         const bool ok = okq[q];
@@ -387,38 +416,41 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
         const float dalpha = Tq * cgz - __fdividef(sg + hT[q], 1.0f - a[q].alpha);
         const float wm = ok ? w : 0.0f;
         const float dpow = open ? a[q].alpha * dalpha : 0.0f;
-        const float dpl = dpow * kLn2;
-        const float yq = dy[q];
-        v[5] += wm * gd[q];
-        v[7] += wm * gr[q];
-        v[8] += wm * gg[q];
-        v[9] += wm * gb[q];
-        v[6] += open ? a[q].G * dalpha : 0.0f;
-        v[2] += -0.5f * dx * dx * dpow;
-        v[3] += -dx * yq * dpow;
-        v[4] += -0.5f * yq * yq * dpow;
-        v[0] += (2.0f * qadx + A.w * yq) * dpl;
-        v[1] += (2.0f * B.x * yq + A.w * dx) * dpl;
+        const float ydp = dy[q] * dpow;
+        P0 += dpow;
+        P1 += ydp;
+        P2 = fmaf(dy[q], ydp, P2);
+        cz = fmaf(wm, gd[q], cz);
+        cr = fmaf(wm, gr[q], cr);
+        cgr = fmaf(wm, gg[q], cgr);
+        cb = fmaf(wm, gb[q], cb);
         Sg[q] = ok ? sg : Sg[q];
         T[q] = ok ? __fmaf_rn(-Tq, a[q].alpha, Tq) : Tq;
       }
-      warp_transpose_reduce16(v, lane);
-      if (!(lane & 1) && idx < 10) s_part[warp][j][idx] = v[0];
+      const float dxP0 = dx * P0;
+      const float v[10] = {dxP0, P1, dx * dxP0, dx * P1, P2, cz, P0, cr, cgr, cb};
+      const float r = warp_reduce10(v, lane);
+      if (writer) s_part[warp][j][idx] = r;
     }
     __syncthreads();
     for (int jj = threadIdx.x; jj < n; jj += kThreads) {
-      float a[10];
+      float R[10];
 #pragma unroll
       for (int q = 0; q < 10; ++q) {
         float acc = 0.0f;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) acc += s_part[w][jj][q];
-        a[q] = acc;
+        R[q] = acc;
       }
+      // R = (sum dx P0, sum P1, sum dx^2 P0, sum dx P1, sum P2, dz, sum P0, dr, dg, db)
+      const float4 A = S.A[jj], B = S.B[jj];
+      const float du = kLn2 * (2.0f * A.z * R[0] + A.w * R[1]);
+      const float dv = kLn2 * (2.0f * B.x * R[1] + A.w * R[0]);
+      const float dop = R[6] != 0.0f ? R[6] / B.y : 0.0f;
       float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(s_slot[jj]) * kPairGradStride);
-      dst[0] = make_float4(a[0], a[1], a[2], a[3]);
-      dst[1] = make_float4(a[4], a[5], a[6], a[7]);
-      dst[2] = make_float4(a[8], a[9], 0.0f, 0.0f);
+      dst[0] = make_float4(du, dv, -0.5f * R[2], -R[3]);
+      dst[1] = make_float4(-0.5f * R[4], R[5], dop, R[7]);
+      dst[2] = make_float4(R[8], R[9], 0.0f, 0.0f);
     }
     __syncthreads();
   }

@@ -52,10 +52,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
   return off + incl - x;
 }
 
-template <class KeyT>
+template <class KeyT, int IT>
 struct SortSmem {
-  KeyT keys[kSortTileKeys];
-  uint32_t vals[kSortTileKeys];
+  KeyT keys[kSortThreads * IT];
+  uint32_t vals[kSortThreads * IT];
   uint32_t warp_hist[kWarps][256];
   uint32_t bucket[256];       // exclusive scan of this pass's global digit histogram
   uint32_t global_base[256];  // destination of the tile's first key of each digit
@@ -70,20 +70,63 @@ __device__ __forceinline__ uint32_t digit_mask(const SortArgsT<KeyT>& a, int pas
   return rem >= 8 ? 0xffu : ((1u << rem) - 1u);
 }
 
-template <class KeyT>
+// Decoupled look-back for digit t of tile `tile` (> 0): the sum of the counts of all
+// lower-numbered tiles. The statuses of kLookahead predecessors are loaded together (one
+// round trip) and consumed in order until one is not published yet (polled again) or
+// carries an inclusive prefix (done). Gives up after kSpinLimit polls without progress.
+constexpr int kLookahead = 16;  // wider polling loads the L2 more than it saves round trips
+__device__ __forceinline__ uint32_t look_back(const uint32_t* status, uint32_t tile, int t, uint32_t* err) {
+  uint32_t excl = 0, spins = 0;
+  int64_t j = static_cast<int64_t>(tile) - 1;
+  for (;;) {
+    uint32_t v[kLookahead];
+#pragma unroll
+    for (int q = 0; q < kLookahead; ++q)
+      v[q] = (j - q >= 0) ? ld_relaxed(&status[static_cast<size_t>(j - q) * 256 + t]) : kFlagPrefix;
+    int consumed = 0;
+    bool found = false, blocked = false;
+#pragma unroll
+    for (int q = 0; q < kLookahead; ++q) {
+      const uint32_t f = v[q] & ~kValueMask;
+      if (found || blocked) continue;
+      if (f == 0) {
+        blocked = true;
+        continue;
+      }
+      excl += v[q] & kValueMask;
+      ++consumed;
+      found = (f == kFlagPrefix);
+    }
+    if (found) return excl;
+    j -= consumed;
+    if (consumed == 0 && ++spins > kSpinLimit) {
+      atomicOr(err, GS_DEVERR_TIMEOUT);
+      return excl;
+    }
+  }
+}
+
+// One pass over 8 digit bits. Tiles of kSortThreads * IT keys; a block takes tiles from a
+// dynamic counter until none are left. Per tile: rank the keys (warp histograms, ordered by
+// (warp, item, lane)), publish the tile's digit counts, place the keys in digit order in
+// shared memory, look back for the tile's global digit offsets, write the keys out.
+template <class KeyT, int IT>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, int pass) {
   pdl_begin();
+  constexpr int kTileKeys = kSortThreads * IT;
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  SortSmem<KeyT>& S = *reinterpret_cast<SortSmem<KeyT>*>(smem_raw);
+  SortSmem<KeyT, IT>& S = *reinterpret_cast<SortSmem<KeyT, IT>*>(smem_raw);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const KeyT* __restrict__ kin = a.keys[pass & 1];
-  const uint32_t* __restrict__ vin = a.vals[pass & 1];
-  KeyT* __restrict__ kout = a.keys[(pass + 1) & 1];
-  uint32_t* __restrict__ vout = a.vals[(pass + 1) & 1];
+  // (selects, not a dynamic index into the parameter arrays, which would copy them to local memory)
+  const bool odd = pass & 1;
+  const KeyT* __restrict__ kin = odd ? a.keys[1] : a.keys[0];
+  const uint32_t* __restrict__ vin = odd ? a.vals[1] : a.vals[0];
+  KeyT* __restrict__ kout = odd ? a.keys[0] : a.keys[1];
+  uint32_t* __restrict__ vout = odd ? a.vals[0] : a.vals[1];
   if (a.total_dev && *a.total_dev > static_cast<uint64_t>(a.n_host)) return;  // overflowed: reported, not sorted
   uint32_t n = static_cast<uint32_t>(a.n_host);
   if (a.n_dev) n = min(*a.n_dev, n);
-  const uint32_t n_tiles = (n + kSortTileKeys - 1) / kSortTileKeys;
+  const uint32_t n_tiles = (n + kTileKeys - 1) / kTileKeys;
   const int shift = a.first_bit + 8 * pass;
   const uint32_t dmask = digit_mask(a, pass);
   uint32_t* status = a.tile_status + static_cast<size_t>(pass) * a.max_tiles * 256;
@@ -97,87 +140,66 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, in
     if (tile >= n_tiles) break;
     for (int d = lane; d < 256; d += 32) S.warp_hist[warp][d] = 0;
     __syncwarp();
-    const uint32_t wbase = tile * kSortTileKeys + warp * (32 * kSortItems);
-    KeyT kr[kSortItems];
-    uint32_t vr[kSortItems], rr[kSortItems];
+    const uint32_t wbase = tile * kTileKeys + warp * (32 * IT);
+    uint32_t rr[IT], dd[IT], cnt = 0;
+    {
+      KeyT kr[IT];
+      uint32_t vr[IT];
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const uint32_t i = wbase + it * 32 + lane;
-      const bool valid = i < n;
-      kr[it] = valid ? kin[i] : static_cast<KeyT>(~static_cast<KeyT>(0));
-      vr[it] = valid ? vin[i] : 0u;
-    }
+      for (int it = 0; it < IT; ++it) {
+        const uint32_t i = wbase + it * 32 + lane;
+        const bool valid = i < n;
+        kr[it] = valid ? kin[i] : static_cast<KeyT>(~static_cast<KeyT>(0));
+        vr[it] = valid ? vin[i] : 0u;
+      }
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const uint32_t i = wbase + it * 32 + lane;
-      const bool valid = i < n;
-      const uint32_t d = valid ? static_cast<uint32_t>(kr[it] >> shift) & dmask : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      const uint32_t prior = valid ? S.warp_hist[warp][d] : 0u;
-      __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) S.warp_hist[warp][d] = prior + __popc(peers);
-      __syncwarp();
-      rr[it] = prior + __popc(peers & lanemask_lt());
-    }
-    __syncthreads();
-    // thread t owns digit t: prefix over warps and the tile's count
-    uint32_t cnt = 0;
+      for (int it = 0; it < IT; ++it) {
+        const uint32_t i = wbase + it * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t d = valid ? static_cast<uint32_t>(kr[it] >> shift) & dmask : 256u;
+        dd[it] = d;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t prior = valid ? S.warp_hist[warp][d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) S.warp_hist[warp][d] = prior + __popc(peers);
+        __syncwarp();
+        rr[it] = prior + __popc(peers & lanemask_lt());
+      }
+      __syncthreads();
+      // thread t owns digit t: prefix over warps and the tile's count
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const uint32_t c = S.warp_hist[w][t];
-      S.warp_hist[w][t] = cnt;
-      cnt += c;
-    }
-    uint32_t excl = 0;
-    if (tile == 0) {
-      st_relaxed(&status[t], kFlagPrefix | cnt);
-    } else {
-      st_relaxed(&status[static_cast<size_t>(tile) * 256 + t], kFlagAggregate | cnt);
-      // Look back kLookahead predecessors per round trip: their statuses are loaded together
-      // and consumed in order until one is not ready yet (re-polled) or carries a prefix.
-      constexpr int kLookahead = 8;
-      int64_t j = static_cast<int64_t>(tile) - 1;
-      uint32_t spins = 0;
-      bool found = false;
-      while (!found && j >= 0) {
-        uint32_t v[kLookahead];
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = S.warp_hist[w][t];
+        S.warp_hist[w][t] = cnt;
+        cnt += c;
+      }
+      // publish early: successors can look back past this tile while it places its keys
+      if (tile == 0)
+        st_relaxed(&status[t], kFlagPrefix | cnt);
+      else
+        st_relaxed(&status[static_cast<size_t>(tile) * 256 + t], kFlagAggregate | cnt);
+      S.local_start[t] = block_exclusive_scan(cnt, S.scan_tmp);
+      __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kLookahead; ++q)
-          v[q] = (j - q >= 0) ? ld_relaxed(&status[static_cast<size_t>(j - q) * 256 + t]) : 0u;
-        int consumed = 0;
-#pragma unroll
-        for (int q = 0; q < kLookahead; ++q) {
-          if (found || consumed != q || j - q < 0) continue;
-          const uint32_t f = v[q] & ~kValueMask;
-          if (f == 0) continue;  // not published yet: stop consuming, poll again from here
-          excl += v[q] & kValueMask;
-          ++consumed;
-          if (f == kFlagPrefix) found = true;
-        }
-        j -= consumed;
-        if (consumed == 0 && ++spins > kSpinLimit) {
-          atomicOr(a.err, GS_DEVERR_TIMEOUT);
-          break;
+      for (int it = 0; it < IT; ++it) {
+        if (dd[it] < 256u) {
+          const uint32_t pos = S.local_start[dd[it]] + S.warp_hist[warp][dd[it]] + rr[it];
+          S.keys[pos] = kr[it];
+          S.vals[pos] = vr[it];
         }
       }
-      st_relaxed(&status[static_cast<size_t>(tile) * 256 + t], kFlagPrefix | (excl + cnt));
     }
-    S.global_base[t] = S.bucket[t] + excl;
-    S.local_start[t] = block_exclusive_scan(cnt, S.scan_tmp);
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const uint32_t i = wbase + it * 32 + lane;
-      if (i < n) {
-        const uint32_t d = static_cast<uint32_t>(kr[it] >> shift) & dmask;
-        const uint32_t pos = S.local_start[d] + S.warp_hist[warp][d] + rr[it];
-        S.keys[pos] = kr[it];
-        S.vals[pos] = vr[it];
+    {
+      uint32_t excl = 0;
+      if (tile != 0) {
+        excl = look_back(status, tile, t, a.err);
+        st_relaxed(&status[static_cast<size_t>(tile) * 256 + t], kFlagPrefix | (excl + cnt));
       }
+      S.global_base[t] = S.bucket[t] + excl;
     }
     __syncthreads();
-    const uint32_t rem = n - tile * kSortTileKeys;
-    const uint32_t tile_n = rem < static_cast<uint32_t>(kSortTileKeys) ? rem : kSortTileKeys;
+    const uint32_t rem = n - tile * kTileKeys;
+    const uint32_t tile_n = rem < static_cast<uint32_t>(kTileKeys) ? rem : kTileKeys;
     for (uint32_t j = t; j < tile_n; j += kSortThreads) {
       const KeyT key = S.keys[j];
       const uint32_t d = static_cast<uint32_t>(key >> shift) & dmask;
@@ -206,7 +228,7 @@ __global__ void k_sort_hist(SortArgs a) {
   __syncthreads();
   for (int i = threadIdx.x; i < a.passes * 256; i += blockDim.x)
     if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
-  const uint64_t used = (n + kSortTileKeys - 1) / kSortTileKeys;
+  const uint64_t used = static_cast<uint64_t>(sort_tiles(static_cast<int64_t>(n), a.items));
   for (int p = 0; p < a.passes; ++p) {
     uint32_t* sp = a.tile_status + static_cast<uint64_t>(p) * a.max_tiles * 256;
     for (uint64_t i = gtid; i < used * 256; i += stride) sp[i] = 0;
@@ -224,14 +246,14 @@ int num_sms() {
   return sms;
 }
 
-template <class KeyT>
+template <class KeyT, int IT>
 int sort_grid(int64_t max_tiles) {
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
-    cudaFuncSetAttribute(k_onesweep<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(sizeof(SortSmem<KeyT>)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_onesweep<KeyT>, kSortThreads,
-                                                  sizeof(SortSmem<KeyT>));
+    cudaFuncSetAttribute(k_onesweep<KeyT, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(sizeof(SortSmem<KeyT, IT>)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_onesweep<KeyT, IT>, kSortThreads,
+                                                  sizeof(SortSmem<KeyT, IT>));
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   const int64_t resident = static_cast<int64_t>(blocks_per_sm) * num_sms();
@@ -239,12 +261,20 @@ int sort_grid(int64_t max_tiles) {
   return static_cast<int>(g > 0 ? g : 1);
 }
 
+template <class KeyT, int IT>
+cudaError_t onesweep_passes_it(const SortArgsT<KeyT>& a, cudaStream_t s) {
+  const int grid = sort_grid<KeyT, IT>(a.max_tiles);
+  for (int p = 0; p < a.passes; ++p)
+    launch(k_onesweep<KeyT, IT>, grid, kSortThreads, sizeof(SortSmem<KeyT, IT>), s, a, p);
+  return cudaGetLastError();
+}
+
 template <class KeyT>
 cudaError_t onesweep_passes(const SortArgsT<KeyT>& a, cudaStream_t s) {
-  const int grid = sort_grid<KeyT>(a.max_tiles);
-  for (int p = 0; p < a.passes; ++p)
-    launch(k_onesweep<KeyT>, grid, kSortThreads, sizeof(SortSmem<KeyT>), s, a, p);
-  return cudaGetLastError();
+  switch (sort_items(a.items)) {
+    case 8: return onesweep_passes_it<KeyT, 8>(a, s);
+    default: return onesweep_passes_it<KeyT, kSortItems>(a, s);
+  }
 }
 
 }  // namespace
@@ -281,6 +311,7 @@ cudaError_t launch_item_sort(const Layout& L, void* ws, cudaStream_t s) {
   a.tile_ctr = st->tile_ctr;
   a.err = &st->err;
   a.max_tiles = L.max_item_tiles;
+  a.items = L.item_sort_items;
   a.passes = 4;
   a.key_bits = 32;
   a.first_bit = 0;
@@ -303,6 +334,7 @@ cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s) {
   a.tile_ctr = st->tile_ctr + 4;
   a.err = &st->err;
   a.max_tiles = L.max_sort_tiles;
+  a.items = L.pair_sort_items;
   a.passes = L.passes;
   a.key_bits = L.key_bits;
   a.first_bit = 32;

@@ -270,7 +270,8 @@ def test_bf16_and_f16_storage_match_dequantised_oracle():
 def test_pixels_per_thread_variants_agree(name):
     """Every (forward, backward) pixels-per-thread variant takes the same decisions: the
     forward outputs are bit-identical; the gradients differ only by the order in which
-    pixels are summed (relative L2 below 1e-6)."""
+    pixels are summed in FP32 (relative L2 below 1e-5; the pose gradient, a sum over every
+    pair with cancellation, is the most sensitive)."""
     torch, api = torch_mods()
     s = scene(name)
     r, g, ct, _, _ = gpu_fwd(name)
@@ -288,7 +289,7 @@ def test_pixels_per_thread_variants_agree(name):
                 for k in ref:
                     if k.startswith("g_"):
                         e = rel_l2(got[k].cpu().numpy(), ref[k].cpu().numpy())
-                        assert e < 1e-6, (fpx, bpx, k, e)
+                        assert e < 1e-5, (fpx, bpx, k, e)
                     else:
                         assert torch.equal(ref[k], got[k]), (fpx, bpx, k)
     r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0

@@ -91,7 +91,7 @@ typedef struct {
   int32_t fwd_px_per_thread;  /* pixels per thread of gs_raster_fwd: 1, 2 or 4; 0 = library default */
   int32_t bwd_px_per_thread;  /* pixels per thread of gs_raster_bwd: 1, 2 or 4; 0 = library default.
                                  Every choice takes the same skip/stop decisions: forward outputs are
-                                 bit-identical, gradients differ only in summation order. */
+                                 bit-identical, gradients differ only in FP32 summation order. */
 } gs_config_t;
 
 /* Gaussian attributes. means may be F32 or BF16/F16 (means_dtype); the other four
@@ -123,12 +123,14 @@ typedef struct {
                             u32[8] sort tile counters, u64 evals that blended a splat */
   size_t proj_uv;        /* float4 [K*N]: u_hi, u_lo, v_hi, v_lo (u = u_hi + u_lo) */
   size_t proj_conic;     /* float4 [K*N]: conic A, B, C (Sigma2^-1 entries 00, 01, 11), depth z */
-  size_t proj_tiles;     /* int4 [K*N]: pair offset, x0 | x1 << 16, y0 | y1 << 16, tiles touched */
+  size_t proj_tiles;     /* int4 [K*N]: pair offset, x0 | x1 << 16, y0 | y1 << 16, tiles emitted */
   size_t proj_depth_key; /* u32 [K*N]: binary32 bits of the camera depth (sort key low word) */
   size_t proj_radius;    /* i32 [K*N]: pixel radius (0 when culled) */
   size_t color_opacity;  /* float4 [N]: r, g, b, opacity */
-  size_t keys_sorted;    /* u64 [pair_capacity], valid prefix num_pairs, after gs_bin_sort */
-  size_t vals_sorted;    /* u32 [pair_capacity]: Gaussian id of each sorted key */
+  size_t keys_sorted;    /* u64 [pair_capacity], valid prefix num_pairs, after gs_bin_sort:
+                            (global tile id << 32) | Gaussian id */
+  size_t vals_sorted;    /* u32 [pair_capacity]: emission index of each sorted pair (pairs of an
+                            item occupy [pair offset, pair offset + tiles emitted)) */
   size_t ranges;         /* u32 [K*Tx*Ty][2]: [start, end) of each global tile */
   size_t pair_grads;     /* float [pair_capacity][12]: per-pair gradients of gs_raster_bwd */
   int32_t sort_passes;   /* 8-bit LSD passes of the pair sort over the tile bits: ceil(ceil(log2(K*Tx*Ty)) / 8) */
@@ -159,19 +161,25 @@ GS_API gs_status_t gs_read_status(const gs_config_t* cfg, const void* ws, size_t
  *   Sigma2 = J R Sigma R^T J^T + 0.3 I,   conic = Sigma2^-1,
  *   radius = ceil(3 sqrt(lambda_max)),     lambda_max = mid + sqrt(max(0.1, ((a-c)/2)^2 + b^2)),
  *   rect   = tiles whose 16x16 square meets [u - r, u + r] x [v - r, v + r],
- * culling z <= near_plane and empty rectangles. The depth key, culls, radius and
- * rectangle are computed in binary32 in one fixed operation order (the design doc,
- * "discrete projection"), so they are reproducible bit for bit. d_cams: K cameras. */
+ * culling z <= near_plane and empty rectangles. Of the rectangle, an item emits (row by
+ * row) only the tiles whose square of pixel centres, widened by 0.05 px + 0.2% of the
+ * ellipse's half-extent, meets the ellipse d^T Sigma2^-1 d <= 2 (l + 0.02 |l| + 1.5e-4),
+ * l = ln(255 opacity): outside it the opacity stays below 1/255, so the skipped pairs
+ * could never be composited. The depth key, culls, radius, rectangle and emitted tiles
+ * are computed in binary32 in one fixed operation order (every step rounded once, with a
+ * deterministic exp and log built from + - * / sqrt and fma), so they are reproducible bit
+ * for bit. d_cams: K cameras. */
 GS_API gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, const gs_camera_t* d_cams, void* ws,
                        size_t ws_bytes, void* stream);
 
 /* Binning: sorts the (view, Gaussian) pairs of every tile by depth. Result: one pair per
- * (view, Gaussian, tile) with key = ((k*Tx*Ty + ty*Tx + tx) << 32) | depth bits and value
- * = g, in the order of a stable sort of those keys emitted in (k, g) order (equal keys keep
- * (k, g) order), plus per-tile [start, end) ranges. Computed as: a stable onesweep radix sort
- * of the K*N items on their 32-bit depth keys, an exclusive scan of tiles touched in that
- * order, emission in that order, and a stable onesweep radix sort of the pairs on the tile
- * bits only. The pair count stays on the device; more than pair_capacity pairs sets
+ * emitted (view, Gaussian, tile), in the order of a stable sort of the keys
+ * ((k*Tx*Ty + ty*Tx + tx) << 32) | depth bits emitted in (k, g) order (equal keys keep
+ * (k, g) order), plus per-tile [start, end) ranges. Each sorted pair is stored as key =
+ * ((k*Tx*Ty + ty*Tx + tx) << 32) | g and value = its emission index (the slot of its
+ * gradient record). Computed as: a stable onesweep radix sort of the K*N items on their
+ * 32-bit depth keys, an exclusive scan of tiles emitted in that order, emission in that
+ * order, and a stable onesweep radix sort of the pairs on the tile bits only. The pair count stays on the device; more than pair_capacity pairs sets
  * GS_DEVERR_PAIR_OVERFLOW and only the first pair_capacity pairs are emitted. Consumes the
  * state of the preceding gs_project on the same workspace (call it once per gs_project). */
 GS_API gs_status_t gs_bin_sort(const gs_config_t* cfg, void* ws, size_t ws_bytes, void* stream);

@@ -31,7 +31,8 @@ NEAR = 0.2
 TILE = 16
 
 #: default guard half-widths (relative) around the alpha >= 1/255 test, the
-#: T(1-alpha) < 1e-4 stop and the power > 0 test. See DESIGN.md, "threshold guard".
+#: T(1-alpha) < 1e-4 stop and the power > 0 test: a decision whose value lies within
+#: this band of its threshold is flagged, and the pixel is also rendered with it inverted.
 GUARD_ALPHA = 2e-5
 GUARD_T = 2e-4
 GUARD_POWER = 1e-5
@@ -70,11 +71,13 @@ _F = ctypes.c_float
 def _declare(L):
     L.orc_expdet_f32.argtypes = [_P, _P, _I64]
     L.orc_expdet_f32.restype = None
-    L.orc_project_mirror.argtypes = [_I64, _P, _P, _P, _I, _P, _I, _I, _I, _F, _P, _P, _P, _P, _P]
+    L.orc_logdet_f32.argtypes = [_P, _P, _I64]
+    L.orc_logdet_f32.restype = None
+    L.orc_project_mirror.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I, _I, _I, _F, _P, _P, _P, _P, _P, _P]
     L.orc_project_mirror.restype = None
     L.orc_project64.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P]
     L.orc_project64.restype = None
-    L.orc_bin.argtypes = [_I64, _I, _I, _I, _I, _P, _P, _P, _I64, _P, _P, _P]
+    L.orc_bin.argtypes = [_I64, _I, _I, _I, _I, _P, _P, _P, _P, _I64, _P, _P, _P]
     L.orc_bin.restype = _I64
     L.orc_render_fwd.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _D, _D, _D,
                                  _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
@@ -110,27 +113,37 @@ def expdet(x) -> np.ndarray:
     return y
 
 
+def logdet(x) -> np.ndarray:
+    x = _c(x, np.float32)
+    y = np.empty_like(x)
+    lib().orc_logdet_f32(_ptr(x), _ptr(y), x.size)
+    return y
+
+
 @dataclass
 class Mirror:
     depth_bits: np.ndarray  # [K*N] uint32
     radius: np.ndarray      # [K*N] int32
     rect: np.ndarray        # [K*N, 4] int32 x0, x1, y0, y1
-    count: np.ndarray       # [K*N] uint32
+    count: np.ndarray       # [K*N] uint32 tiles emitted
     uv: np.ndarray          # [K*N, 2] float32
+    ell: np.ndarray         # [K*N, 8] float32 widened ellipse: u, v, b, c, sqrt(det), hx, hy, kxy
 
 
-def project_mirror(means, log_scales, quats, cams, W, H, tile=TILE, near=NEAR) -> Mirror:
-    """FP32 discrete mirror of the projection (depth keys, culls, radius, tile rect)."""
+def project_mirror(means, log_scales, quats, logits, cams, W, H, tile=TILE, near=NEAR) -> Mirror:
+    """FP32 discrete mirror of the projection (depth keys, culls, radius, tile rect, and the
+    tiles of the rect that the widened alpha >= 1/255 ellipse meets)."""
     means = _c(means, np.float32)
     log_scales = _c(log_scales, np.float32)
     quats = _c(quats, np.float32)
+    logits = _c(np.asarray(logits).reshape(-1), np.float32)
     cams = _c(cams, np.float32).reshape(-1, 16)
     N, K = means.shape[0], cams.shape[0]
     out = Mirror(np.empty(K * N, np.uint32), np.empty(K * N, np.int32), np.empty((K * N, 4), np.int32),
-                 np.empty(K * N, np.uint32), np.empty((K * N, 2), np.float32))
-    lib().orc_project_mirror(N, _ptr(means), _ptr(log_scales), _ptr(quats), K, _ptr(cams), W, H, tile,
-                             near, _ptr(out.depth_bits), _ptr(out.radius), _ptr(out.rect), _ptr(out.count),
-                             _ptr(out.uv))
+                 np.empty(K * N, np.uint32), np.empty((K * N, 2), np.float32), np.empty((K * N, 8), np.float32))
+    lib().orc_project_mirror(N, _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(logits), K, _ptr(cams), W, H,
+                             tile, near, _ptr(out.depth_bits), _ptr(out.radius), _ptr(out.rect), _ptr(out.count),
+                             _ptr(out.uv), _ptr(out.ell))
     return out
 
 
@@ -151,7 +164,7 @@ def bin_pairs(m: Mirror, N, K, W, H, tile=TILE):
     keys = np.empty(P, np.uint64)
     vals = np.empty(P, np.uint32)
     ranges = np.empty((K * Tx * Ty, 2), np.uint32)
-    got = lib().orc_bin(N, K, W, H, tile, _ptr(m.count), _ptr(m.rect), _ptr(m.depth_bits), P,
+    got = lib().orc_bin(N, K, W, H, tile, _ptr(m.count), _ptr(m.rect), _ptr(m.ell), _ptr(m.depth_bits), P,
                         _ptr(keys), _ptr(vals), _ptr(ranges))
     assert got == P
     return keys, vals, ranges
@@ -250,9 +263,9 @@ class Lists:
 
 def discrete(params, cams, W, H, tile=TILE, near=NEAR) -> Lists:
     """Mirror + binning for float32-stored parameters."""
-    means, ls, qs = params[0], params[1], params[2]
+    means, ls, qs, lg = params[0], params[1], params[2], params[3]
     cams = np.asarray(cams, np.float32).reshape(-1, 16)
-    m = project_mirror(means, ls, qs, cams, W, H, tile, near)
+    m = project_mirror(means, ls, qs, lg, cams, W, H, tile, near)
     keys, vals, ranges = bin_pairs(m, np.asarray(means).shape[0], cams.shape[0], W, H, tile)
     return Lists(m, keys, vals, ranges)
 

@@ -25,8 +25,9 @@
 // ----------------
 // 1. orc_project_mirror: the FP32 "discrete mirror". It evaluates, in binary32
 //    with a fixed operation order, exactly the quantities that decide integers:
-//    the camera depth (sort key), the culls, the pixel radius and the tile
-//    rectangle. Both this mirror and the CUDA projection follow one written
+//    the camera depth (sort key), the culls, the pixel radius, the tile
+//    rectangle and, row by row, the tiles of the rectangle that the widened
+//    alpha >= 1/255 ellipse meets. Both this mirror and the CUDA projection follow one written
 //    operation order (the library header documents it), so keys, order and
 //    ranges can be compared bit for bit.
 // 2. orc_bin: pair emission in (view, Gaussian) order, std::stable_sort by the
@@ -86,15 +87,89 @@ float expdet(float x) {
   return p * scale;
 }
 
+// Deterministic binary32 natural logarithm of a positive normal x: x = m 2^e with m in
+// [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s) with s = (m - 1)/(m + 1), the atanh series to
+// s^9 by Horner's rule, and e ln2 added with the same head / tail split of ln2 as expdet.
+float logdet(float x) {
+  if (!(x > 0.0f) || !std::isfinite(x)) return x > 0.0f ? x : -INFINITY;
+  uint32_t bits;
+  std::memcpy(&bits, &x, 4);
+  if ((bits >> 23) == 0) return -INFINITY;  // subnormal: far below any level the mirror uses
+  int e = static_cast<int>(bits >> 23) - 127;
+  const uint32_t mb = (bits & 0x7fffffu) | 0x3f800000u;
+  float m;
+  std::memcpy(&m, &mb, 4);
+  if (m > 0x1.6a09e6p+0f) {  // sqrt(2)
+    m = m * 0.5f;
+    e += 1;
+  }
+  const float s = (m - 1.0f) / (m + 1.0f);
+  const float s2 = s * s;
+  float p = 0x1.c71c72p-4f;             // 1/9
+  p = std::fma(p, s2, 0x1.24924ap-3f);  // 1/7
+  p = std::fma(p, s2, 0x1.99999ap-3f);  // 1/5
+  p = std::fma(p, s2, 0x1.555556p-2f);  // 1/3
+  p = std::fma(p, s2, 1.0f);
+  const float lm = (2.0f * s) * p;
+  const float ef = static_cast<float>(e);
+  return std::fma(ef, 0x1.62e4p-1f, std::fma(ef, 0x1.7f7d1cp-20f, lm));
+}
+
+// The ellipse of a projected Gaussian inside which its opacity can reach 1/255, widened by
+// a safety margin, as the discrete mirror evaluates it: E = {d : d^T Sigma2^-1 d <= kap}
+// with kap = 2 (ln(255 o) + 0.02 |ln(255 o)| + 1.5e-4). Stored: the mean (u, v), Sigma2's
+// off-diagonal b and yy entry c, sqrt(det Sigma2), the half-extents hx = sqrt(kap a),
+// hy = sqrt(kap c), and kxy = b / a (the y offset, per unit x offset, of E's widest point).
+struct Ellipse {
+  float u, v, b, c, sdet, hx, hy, kxy;
+};
+
+// Tile columns [*xa, *xb] of tile row ty whose pixel centres' square, widened by
+// 0.05 px + 0.2% of the half-extent, meets E; clamped to [x0, x1). *xa > *xb: none.
+// E's part inside the row's (widened) strip of pixel-centre rows is convex; its x-extent
+// ends at E's leftmost / rightmost point when that lies inside the strip, else where E's
+// boundary crosses the strip edge on that point's side.
+void row_span(const Ellipse& E, int ty, int x0, int x1, int tile, int* xa, int* xb) {
+  *xa = 1;
+  *xb = 0;
+  const float tf = static_cast<float>(tile);
+  const float mgx = std::fma(0.002f, E.hx, 0.05f);
+  const float mgy = std::fma(0.002f, E.hy, 0.05f);
+  const float y_lo = static_cast<float>(ty) * tf;
+  const float Y0 = (y_lo + 0.5f) - mgy;
+  const float Y1 = (y_lo + (tf - 0.5f)) + mgy;
+  if (E.v + E.hy < Y0 || E.v - E.hy > Y1) return;
+  auto cross = [&](float Ye, float sgn) {
+    const float dye = Ye - E.v;
+    const float ad = std::fabs(dye);
+    const float w = std::sqrt(std::fmax((E.hy - ad) * (E.hy + ad), 0.0f));
+    return E.u + std::fma(sgn * E.sdet, w, E.b * dye) / E.c;
+  };
+  const float yR = std::fma(E.kxy, E.hx, E.v);
+  const float yL = std::fma(-E.kxy, E.hx, E.v);
+  const float xr = (yR >= Y0 && yR <= Y1) ? E.u + E.hx : (yR > Y1 ? cross(Y1, 1.0f) : cross(Y0, 1.0f));
+  const float xl = (yL >= Y0 && yL <= Y1) ? E.u - E.hx : (yL > Y1 ? cross(Y1, -1.0f) : cross(Y0, -1.0f));
+  const float inv_t = 1.0f / tf;
+  float fa = std::ceil(((xl - mgx) - (tf - 0.5f)) * inv_t);
+  float fb = std::floor(((xr + mgx) - 0.5f) * inv_t);
+  fa = std::fmax(fa, static_cast<float>(x0));
+  fb = std::fmin(fb, static_cast<float>(x1 - 1));
+  if (!(fa <= fb)) return;
+  *xa = static_cast<int>(fa);
+  *xb = static_cast<int>(fb);
+}
+
 struct MirrorOut {
   bool valid;
   float zc, u, v;
   int radius;
   int x0, x1, y0, y1;
+  uint32_t count;  // tiles of the rectangle whose row span meets the ellipse
+  Ellipse E;
 };
 
 // The FP32 operation order below is the contract shared with the CUDA projection.
-MirrorOut mirror_one(const float* p, const float* ls, const float* q, const float* cam,
+MirrorOut mirror_one(const float* p, const float* ls, const float* q, float logit, const float* cam,
                      int W, int H, int tile, float near) {
   MirrorOut o{};
   o.valid = false;
@@ -180,6 +255,22 @@ MirrorOut mirror_one(const float* p, const float* ls, const float* q, const floa
   o.y0 = static_cast<int>(y0f);
   o.y1 = static_cast<int>(y1f);
   o.valid = (o.x1 - o.x0) * (o.y1 - o.y0) > 0;
+  if (!o.valid) return o;
+  // 12. opacity level and the widened ellipse; tiles per row of the rectangle
+  const float ee = expdet(-logit);
+  const float op = 1.0f / (1.0f + ee);
+  const float L = logdet(255.0f * op);
+  const float Lm = (L + 0.02f * std::fabs(L)) + 1.5e-4f;
+  if (!(Lm >= 0.0f)) return o;  // the opacity never reaches 1/255: no pairs
+  const float kap = 2.0f * Lm;
+  o.E = Ellipse{u, v, bb, c, std::sqrt(det), std::sqrt(kap * a), std::sqrt(kap * c), bb / a};
+  uint32_t cnt = 0;
+  for (int ty = o.y0; ty < o.y1; ++ty) {
+    int xa, xb;
+    row_span(o.E, ty, o.x0, o.x1, tile, &xa, &xb);
+    if (xa <= xb) cnt += static_cast<uint32_t>(xb - xa + 1);
+  }
+  o.count = cnt;
   return o;
 }
 
@@ -360,16 +451,24 @@ void orc_expdet_f32(const float* x, float* y, int64_t n) {
   for (int64_t i = 0; i < n; ++i) y[i] = expdet(x[i]);
 }
 
+// Deterministic binary32 log used by the discrete mirror (exposed for its pin tests).
+void orc_logdet_f32(const float* x, float* y, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) y[i] = logdet(x[i]);
+}
+
 // FP32 discrete mirror over K views x N Gaussians. Outputs per (k, g), index k*N+g:
 // depth_bits (binary32 bits of the camera depth), radius, rect[4] = x0,x1,y0,y1
-// (tile indices, half-open), count = tiles touched (0 = culled), uv = binary32 mean2D.
-void orc_project_mirror(int64_t N, const float* means, const float* log_scales, const float* quats, int K,
-                        const float* cams, int W, int H, int tile, float near, uint32_t* depth_bits,
-                        int32_t* radius, int32_t* rect, uint32_t* count, float* uv) {
+// (tile indices, half-open), count = tiles emitted (0 = culled), uv = binary32 mean2D,
+// ell[8] = the widened ellipse (u, v, b, c, sqrt det, hx, hy, kxy; zeros when count = 0).
+void orc_project_mirror(int64_t N, const float* means, const float* log_scales, const float* quats,
+                        const float* logits, int K, const float* cams, int W, int H, int tile, float near,
+                        uint32_t* depth_bits, int32_t* radius, int32_t* rect, uint32_t* count, float* uv,
+                        float* ell) {
 #pragma omp parallel for schedule(static)
   for (int64_t kg = 0; kg < static_cast<int64_t>(K) * N; ++kg) {
     const int64_t k = kg / N, g = kg % N;
-    const MirrorOut m = mirror_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, cams + 16 * k, W, H, tile, near);
+    const MirrorOut m = mirror_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], cams + 16 * k, W, H,
+                                   tile, near);
     uint32_t bits;
     std::memcpy(&bits, &m.zc, 4);
     depth_bits[kg] = bits;
@@ -378,9 +477,12 @@ void orc_project_mirror(int64_t N, const float* means, const float* log_scales, 
     rect[4 * kg + 1] = m.valid ? m.x1 : 0;
     rect[4 * kg + 2] = m.valid ? m.y0 : 0;
     rect[4 * kg + 3] = m.valid ? m.y1 : 0;
-    count[kg] = m.valid ? static_cast<uint32_t>((m.x1 - m.x0) * (m.y1 - m.y0)) : 0u;
+    count[kg] = m.valid ? m.count : 0u;
     uv[2 * kg + 0] = m.u;
     uv[2 * kg + 1] = m.v;
+    const Ellipse E = (m.valid && m.count) ? m.E : Ellipse{};
+    const float e8[8] = {E.u, E.v, E.b, E.c, E.sdet, E.hx, E.hy, E.kxy};
+    for (int i = 0; i < 8; ++i) ell[8 * kg + i] = e8[i];
   }
 }
 
@@ -402,12 +504,14 @@ void orc_project64(int64_t N, const double* means, const double* log_scales, con
   }
 }
 
-// Pair emission in increasing (k, g) order, tiles row-major inside each rectangle;
-// key = (global tile id << 32) | depth bits, value = g; std::stable_sort by key keeps
-// equal keys in emission order. ranges[t] = [start, end) of global tile t (empty = [0,0)).
-// Returns P (the number of pairs), or -1 if P > capacity (nothing written then).
+// Pair emission in increasing (k, g) order, row by row through each rectangle, in each
+// row the columns of its span (row_span); key = (global tile id << 32) | depth bits,
+// value = g; std::stable_sort by key keeps equal keys in emission order.
+// ranges[t] = [start, end) of global tile t (empty = [0,0)). Returns P (the number of
+// pairs), or -1 if P > capacity (nothing written then).
 int64_t orc_bin(int64_t N, int K, int W, int H, int tile, const uint32_t* count, const int32_t* rect,
-                const uint32_t* depth_bits, int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges) {
+                const float* ell, const uint32_t* depth_bits, int64_t capacity, uint64_t* keys, uint32_t* vals,
+                uint32_t* ranges) {
   const int Tx = tiles_x(W, tile), Ty = tiles_y(H, tile);
   int64_t P = 0;
   for (int64_t kg = 0; kg < static_cast<int64_t>(K) * N; ++kg) P += count[kg];
@@ -419,14 +523,20 @@ int64_t orc_bin(int64_t N, int K, int W, int H, int tile, const uint32_t* count,
     if (!count[kg]) continue;
     const int64_t k = kg / N, g = kg % N;
     const int32_t* r = rect + 4 * kg;
-    for (int ty = r[2]; ty < r[3]; ++ty)
-      for (int tx = r[0]; tx < r[1]; ++tx) {
+    const float* e = ell + 8 * kg;
+    const Ellipse E{e[0], e[1], e[2], e[3], e[4], e[5], e[6], e[7]};
+    for (int ty = r[2]; ty < r[3]; ++ty) {
+      int xa, xb;
+      row_span(E, ty, r[0], r[1], tile, &xa, &xb);
+      for (int tx = xa; tx <= xb; ++tx) {
         const uint64_t tid = static_cast<uint64_t>(k) * Tx * Ty + static_cast<uint64_t>(ty) * Tx + tx;
         k_emit[o] = (tid << 32) | depth_bits[kg];
         v_emit[o] = static_cast<uint32_t>(g);
         ++o;
       }
+    }
   }
+  if (o != P) return -1;  // the spans disagree with the counts (cannot happen)
   std::vector<int64_t> idx(P);
   std::iota(idx.begin(), idx.end(), 0);
   std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return k_emit[a] < k_emit[b]; });

@@ -1,19 +1,21 @@
 // Tile binning of the projected Gaussians, after the (view, Gaussian) items have been
 // stably sorted by camera depth:
-//   k_sorted_counts   tiles touched per item in depth order, per-block totals
+//   k_sorted_counts   tiles emitted per item in depth order, per-block totals
 //   k_scan_blocks     exclusive scan of the block totals, pair count, capacity check
-//   k_item_offsets    per item (depth order): first pair index, rectangle, depth key, ids
-//   k_tile_prefix     2D prefix sum of each view's rectangle difference grid = pairs per tile
+//   k_item_offsets    per item (depth order): first pair index, rectangle, ids
+//   k_tile_prefix     row-wise prefix sum of each view's span grid = pairs per tile
 //   k_tile_scan       tile ranges [start, end) and the digit histograms of the pair sort
-//   k_emit_pairs      one (key, value) pair per (view, Gaussian, tile), 2048 pairs per block
+//   k_emit_pairs      one (key, value) pair per emitted (view, Gaussian, tile), 2048 pairs per block
 //
-// key   = ((k * Tx * Ty + ty * Tx + tx) << 32) | bits(camera depth)   (depth > 0, so the
-//         float bit pattern orders like the depth)
-// value = Gaussian id g.
-// Pairs are emitted item by item in (depth bits, k*N + g) order, tiles row-major inside each
-// rectangle. The pair sort then orders the tile bits only (stable), which leaves every tile's
-// pairs in (depth bits, k*N + g) order: the order of a stable sort of the full keys. Because
-// the sort orders by tile, the ranges are the exclusive scan of the per-tile pair counts.
+// An item emits, row by row through its tile rectangle, the tiles of each row's span that
+// its widened alpha >= 1/255 ellipse meets (row_span).
+// key   = ((k * Tx * Ty + ty * Tx + tx) << 32) | g
+// value = the pair's emission index (its slot in the per-pair gradient buffer).
+// Pairs are emitted item by item in (depth bits, k*N + g) order. The pair sort then orders
+// the tile bits only (stable), which leaves every tile's pairs in (depth bits, k*N + g)
+// order: the order of a stable sort of ((tile << 32) | depth bits) keys emitted in (k, g)
+// order. Because the sort orders by tile, the ranges are the exclusive scan of the per-tile
+// pair counts.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -130,16 +132,15 @@ __global__ void __launch_bounds__(kProjBlock) k_item_offsets(Layout L, uint8_t* 
       const int4 tl = tiles[kg];
       tiles[kg].x = static_cast<int>(off < cap ? off : cap);
       const uint32_t k = static_cast<uint32_t>(kg / static_cast<uint64_t>(L.N));
-      at<int4>(ws, L.item_rect)[s] =
-          make_int4(tl.y, tl.z, static_cast<int>(at<uint32_t>(ws, L.proj_depth_key)[kg]), 0);
+      at<int4>(ws, L.item_rect)[s] = make_int4(tl.y, tl.z, static_cast<int>(kg), 0);
       at<uint2>(ws, L.item_kg)[s] = make_uint2(k, kg - k * static_cast<uint32_t>(L.N));
     }
   }
 }
 
-// One block per view: in-place 2D prefix sum of the (Ty+1) x (Tx+1) difference grid; cell
+// One block per view: in-place row-wise prefix sum of the (Ty+1) x (Tx+1) span grid; cell
 // (ty, tx) then holds the number of pairs of tile (ty, tx). The grid is staged in shared
-// memory when it fits (row sums, then column sums), else summed in place in global memory.
+// memory when it fits, else summed in place in global memory.
 __global__ void k_tile_prefix(Layout L, uint8_t* __restrict__ ws) {
   pdl_begin();
   __shared__ int32_t sg[kProjGridCells];
@@ -152,17 +153,9 @@ __global__ void k_tile_prefix(Layout L, uint8_t* __restrict__ ws) {
     for (int i = threadIdx.x; i < cells; i += blockDim.x) sg[i] = gg[i];
     __syncthreads();
   }
-  for (int y = threadIdx.x; y <= L.Ty; y += blockDim.x) {
+  for (int y = threadIdx.x; y < L.Ty; y += blockDim.x) {
     int32_t acc = 0;
     for (int x = 0; x <= L.Tx; ++x) {
-      acc += g[y * stride + x];
-      g[y * stride + x] = acc;
-    }
-  }
-  __syncthreads();
-  for (int x = threadIdx.x; x <= L.Tx; x += blockDim.x) {
-    int32_t acc = 0;
-    for (int y = 0; y <= L.Ty; ++y) {
       acc += g[y * stride + x];
       g[y * stride + x] = acc;
     }
@@ -250,6 +243,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
   __syncthreads();
   const int4* rects = at<int4>(ws, L.item_rect);
   const uint2* kgs = at<uint2>(ws, L.item_kg);
+  const Ellipse* ells = at<Ellipse>(ws, L.proj_ell);
   uint64_t* keys = at<uint64_t>(ws, L.keys[0]);
   uint32_t* vals = at<uint32_t>(ws, L.vals[0]);
   const uint64_t tiles_per_view = static_cast<uint64_t>(L.Tx) * L.Ty;
@@ -262,13 +256,26 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
     }
     const int4 rc = rects[lo + a];
     const uint2 kg = kgs[lo + a];
-    const uint32_t r = jj - s_off[a];
-    const uint32_t x0 = static_cast<uint32_t>(rc.x) & 0xffffu, w = (static_cast<uint32_t>(rc.x) >> 16) - x0;
-    const uint32_t y0 = static_cast<uint32_t>(rc.y) & 0xffffu;
-    const uint32_t ty = y0 + r / w, tx = x0 + r % w;
+    const Ellipse E = ells[rc.z];
+    // the pair's tile: the r-th of the item's row spans, rows in increasing order
+    int r = static_cast<int>(jj - s_off[a]);
+    const int x0 = rc.x & 0xffff, x1 = static_cast<int>(static_cast<uint32_t>(rc.x) >> 16);
+    const int y0 = rc.y & 0xffff, y1 = static_cast<int>(static_cast<uint32_t>(rc.y) >> 16);
+    int tx = x0, ty = y0;
+    for (int y = y0; y < y1; ++y) {
+      const int2 sp = row_span(E, y, x0, x1);
+      const int w = sp.y - sp.x + 1;
+      if (w <= 0) continue;
+      if (r < w) {
+        ty = y;
+        tx = sp.x + r;
+        break;
+      }
+      r -= w;
+    }
     const uint64_t tid = static_cast<uint64_t>(kg.x) * tiles_per_view + static_cast<uint64_t>(ty) * L.Tx + tx;
-    keys[j] = (tid << 32) | static_cast<uint32_t>(rc.z);
-    vals[j] = kg.y;
+    keys[j] = (tid << 32) | kg.y;
+    vals[j] = jj;
   }
 }
 

@@ -52,16 +52,17 @@ struct Layout {
   int64_t max_sort_tiles;   // onesweep tiles of the pair sort at capacity
   int64_t n_pose_blocks;    // ceil(N / kPoseBlock)
   int64_t n_loss_blocks;
-  // byte offsets into the workspace
-  size_t status, proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, color_opacity, block_sums,
+  // byte offsets into the workspace (proj_ell: Ellipse [K*N], the widened alpha >= 1/255 ellipse)
+  size_t status, proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, proj_ell, color_opacity, block_sums,
       block_offsets, keys[2], vals[2], ranges, hist, sort_status, pair_grads, pose_partials, loss_partials;
   // per-item depth sort (u32 depth key, u32 item index), its histograms and look-back status,
   // and the tiles touched by each item in depth order
   size_t item_keys[2], item_vals[2], item_hist, item_status, sorted_counts;
-  // in depth order: exclusive pair offset of each item (KN + 1 entries), its rectangle and
-  // depth key (int4: x0|x1<<16, y0|y1<<16, depth bits, -), its (view, Gaussian id)
+  // in depth order: exclusive pair offset of each item (KN + 1 entries), its rectangle
+  // (int4: x0|x1<<16, y0|y1<<16, -, -), its (view, Gaussian id)
   size_t item_offsets, item_rect, item_kg;
-  // per view a (Ty+1) x (Tx+1) difference grid of the items' tile rectangles -> pairs per tile
+  // per view a (Ty+1) x (Tx+1) grid: +1 / -1 at the first / one-past-last tile of every
+  // emitted row span; its row-wise prefix sum is the number of pairs of each tile
   size_t tile_diff;
   int64_t n_emit_blocks;    // ceil(cap / kEmitPairs)
   size_t total;
@@ -119,6 +120,53 @@ __device__ __forceinline__ float load_attr(const void* p, int64_t i, int dtype) 
   if (dtype == GS_F32) return static_cast<const float*>(p)[i];
   if (dtype == GS_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
   return __half2float(static_cast<const __half*>(p)[i]);
+}
+
+// ---------------------------------------------------------------------------- pair culling
+// The widened ellipse of a projected Gaussian inside which its opacity can reach 1/255, as
+// the discrete projection evaluates it in binary32: E = {d : d^T Sigma2^-1 d <= kap} with
+// kap = 2 (ln(255 o) + 0.02 |ln(255 o)| + 1.5e-4), o = 1 / (1 + exp(-logit)). Stored: the
+// mean (u, v), Sigma2's off-diagonal b and yy entry c, sqrt(det Sigma2), the half-extents
+// hx = sqrt(kap a), hy = sqrt(kap c), and kxy = b / a (the y offset, per unit x offset, of
+// E's leftmost / rightmost points).
+struct Ellipse {
+  float u, v, b, c, sdet, hx, hy, kxy;
+};
+
+// Tile columns [xa, xb] (returned as x, y; xa > xb: none) of tile row ty whose square of
+// pixel centres, widened by 0.05 px + 0.2% of the half-extent, meets E; clamped to [x0, x1).
+// E's part inside the row's strip is convex, so its x-extent ends at E's leftmost /
+// rightmost point when that lies inside the strip, else where E's boundary crosses the
+// strip edge on that point's side. Every step is one binary32 rounding in a fixed order,
+// so the projection (counts) and the emission (tiles) reproduce each other bit for bit.
+__device__ __forceinline__ float ellipse_cross(const Ellipse& E, float Ye, float sgn) {
+  const float dye = __fsub_rn(Ye, E.v);
+  const float ad = fabsf(dye);
+  const float w = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(E.hy, ad), __fadd_rn(E.hy, ad)), 0.0f));
+  return __fadd_rn(E.u, __fdiv_rn(__fmaf_rn(__fmul_rn(sgn, E.sdet), w, __fmul_rn(E.b, dye)), E.c));
+}
+__device__ __forceinline__ int2 row_span(const Ellipse& E, int ty, int x0, int x1) {
+  const int2 none = make_int2(1, 0);
+  const float tf = static_cast<float>(kTile);
+  const float mgx = __fmaf_rn(0.002f, E.hx, 0.05f);
+  const float mgy = __fmaf_rn(0.002f, E.hy, 0.05f);
+  const float y_lo = __fmul_rn(static_cast<float>(ty), tf);
+  const float Y0 = __fsub_rn(__fadd_rn(y_lo, 0.5f), mgy);
+  const float Y1 = __fadd_rn(__fadd_rn(y_lo, __fsub_rn(tf, 0.5f)), mgy);
+  if (__fadd_rn(E.v, E.hy) < Y0 || __fsub_rn(E.v, E.hy) > Y1) return none;
+  const float yR = __fmaf_rn(E.kxy, E.hx, E.v);
+  const float yL = __fmaf_rn(-E.kxy, E.hx, E.v);
+  const float xr = (yR >= Y0 && yR <= Y1) ? __fadd_rn(E.u, E.hx)
+                                          : (yR > Y1 ? ellipse_cross(E, Y1, 1.0f) : ellipse_cross(E, Y0, 1.0f));
+  const float xl = (yL >= Y0 && yL <= Y1) ? __fsub_rn(E.u, E.hx)
+                                          : (yL > Y1 ? ellipse_cross(E, Y1, -1.0f) : ellipse_cross(E, Y0, -1.0f));
+  const float inv_t = 1.0f / tf;
+  float fa = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(xl, mgx), __fsub_rn(tf, 0.5f)), inv_t));
+  float fb = floorf(__fmul_rn(__fsub_rn(__fadd_rn(xr, mgx), 0.5f), inv_t));
+  fa = fmaxf(fa, static_cast<float>(x0));
+  fb = fminf(fb, static_cast<float>(x1 - 1));
+  if (!(fa <= fb)) return none;
+  return make_int2(static_cast<int>(fa), static_cast<int>(fb));
 }
 
 // Launchers (each defined in its own translation unit). All return cudaGetLastError().

@@ -1,10 +1,11 @@
 // Projection of 3D Gaussians (Sec. II-A scene model) for K views: 2D mean, conic,
-// depth, pixel radius and tile rectangle of every (view, Gaussian) item.
+// depth, pixel radius, tile rectangle and the tiles of that rectangle which the widened
+// alpha >= 1/255 ellipse meets (counted row by row) of every (view, Gaussian) item.
 //
 // Two arithmetic regimes live here:
-//  * the DISCRETE path (camera depth used as the sort key, the culls, the radius and
-//    the tile rectangle) runs in binary32 in one fixed operation order, with explicit
-//    round-to-nearest intrinsics so the compiler cannot fuse or reorder anything;
+//  * the DISCRETE path (camera depth used as the sort key, the culls, the radius, the
+//    tile rectangle and the emitted tiles) runs in binary32 in one fixed operation order,
+//    with explicit round-to-nearest intrinsics so the compiler cannot fuse or reorder anything;
 //  * the CONTINUOUS path carries the camera-space mean and the 2D mean as unevaluated
 //    float pairs (hi + lo, Dot2-style compensated arithmetic), so the 2D mean that the
 //    compositing uses is accurate to ~1e-12 px instead of ~4e-5 px at 640 px.
@@ -32,6 +33,31 @@ __device__ __forceinline__ float exp_det(float x) {
   p = __fmaf_rn(p, r, 1.0f);
   const int k = static_cast<int>(kf);
   return __fmul_rn(p, __int_as_float((k + 127) << 23));
+}
+
+// Deterministic binary32 natural logarithm of a positive normal x: x = m 2^e with m in
+// [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m - 1)/(m + 1), by the atanh series to s^9
+// (Horner), plus e ln2 with the head / tail split of ln2 used by exp_det. Within 4 ulp.
+__device__ __forceinline__ float log_det(float x) {
+  if (!(x > 0.0f) || !isfinite(x)) return x > 0.0f ? x : -INFINITY;
+  const uint32_t bits = __float_as_uint(x);
+  if ((bits >> 23) == 0) return -INFINITY;
+  int e = static_cast<int>(bits >> 23) - 127;
+  float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+  if (m > 0x1.6a09e6p+0f) {
+    m = __fmul_rn(m, 0.5f);
+    e += 1;
+  }
+  const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+  const float s2 = __fmul_rn(s, s);
+  float p = 0x1.c71c72p-4f;
+  p = __fmaf_rn(p, s2, 0x1.24924ap-3f);
+  p = __fmaf_rn(p, s2, 0x1.99999ap-3f);
+  p = __fmaf_rn(p, s2, 0x1.555556p-2f);
+  p = __fmaf_rn(p, s2, 1.0f);
+  const float lm = __fmul_rn(__fmul_rn(2.0f, s), p);
+  const float ef = static_cast<float>(e);
+  return __fmaf_rn(ef, 0x1.62e4p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, lm));
 }
 
 struct FF {
@@ -108,8 +134,8 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
     for (int j = 0; j < 4; ++j) q[j] = load_attr(G.quats, 4 * g + j, G.dtype);
     const float* R = cam.R;
     const float* t = cam.t;
+    const float lg = load_attr(G.logits, g, G.dtype);
     if (k == 0) {
-      const float lg = load_attr(G.logits, g, G.dtype);
       const float c0 = load_attr(G.rgb, 3 * g + 0, G.dtype);
       const float c1 = load_attr(G.rgb, 3 * g + 1, G.dtype);
       const float c2 = load_attr(G.rgb, 3 * g + 2, G.dtype);
@@ -205,18 +231,29 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
       y0 = static_cast<int>(y0f);
       y1 = static_cast<int>(y1f);
       radius = static_cast<int>(rf);
-      count = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
-      if (count == 0) {
+      if ((x1 - x0) * (y1 - y0) == 0) {
         x0 = x1 = y0 = y1 = radius = 0;
       } else {
-        // rectangle into the view's difference grid: its 2D prefix sum is the pairs per tile
-        int32_t* dg = (use_sgrid && k == k_block)
-                          ? s_grid
-                          : at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * gcells;
-        atomicAdd(&dg[y0 * gstride + x0], 1);
-        atomicAdd(&dg[y0 * gstride + x1], -1);
-        atomicAdd(&dg[y1 * gstride + x0], -1);
-        atomicAdd(&dg[y1 * gstride + x1], 1);
+        // the widened alpha >= 1/255 ellipse and, row by row, the rectangle's tiles it meets
+        const float op = __fdiv_rn(1.0f, __fadd_rn(1.0f, exp_det(-lg)));
+        const float Lg = log_det(__fmul_rn(255.0f, op));
+        const float Lm = __fadd_rn(__fadd_rn(Lg, __fmul_rn(0.02f, fabsf(Lg))), 1.5e-4f);
+        if (Lm >= 0.0f) {
+          const float kap = __fmul_rn(2.0f, Lm);
+          const Ellipse E{u, v, bb, c, __fsqrt_rn(det), __fsqrt_rn(__fmul_rn(kap, a)), __fsqrt_rn(__fmul_rn(kap, c)),
+                          __fdiv_rn(bb, a)};
+          at<Ellipse>(ws, L.proj_ell)[idx] = E;
+          int32_t* dg = (use_sgrid && k == k_block)
+                            ? s_grid
+                            : at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * gcells;
+          for (int ty = y0; ty < y1; ++ty) {
+            const int2 sp = row_span(E, ty, x0, x1);
+            if (sp.x > sp.y) continue;
+            count += static_cast<uint32_t>(sp.y - sp.x + 1);
+            atomicAdd(&dg[ty * gstride + sp.x], 1);  // row-wise prefix sum: pairs per tile
+            atomicAdd(&dg[ty * gstride + sp.y + 1], -1);
+          }
+        }
       }
     }
     at<uint32_t>(ws, L.proj_depth_key)[idx] = __float_as_uint(zc);

@@ -5,8 +5,8 @@
 // shared and every splat record loaded from shared memory serves PX pixels. The per-pixel
 // update is branch-free (a masked blend with weight 0 leaves every accumulator bit for bit
 // unchanged), so the PX pixel chains interleave. The tile's depth-sorted list is walked in
-// chunks staged in shared memory as three float4 per splat (coalesced loads of the sorted
-// Gaussian ids, one gather of the projected record each).
+// chunks staged in shared memory as three float4 and a row mask per splat (coalesced loads
+// of the sorted keys, whose low word is the Gaussian id, one gather of the projected record each).
 //
 // Both kernels evaluate a splat's opacity with the same inline function on the same
 // operands, so the backward pass takes exactly the forward pass's skip and stop decisions
@@ -85,8 +85,8 @@ __device__ __forceinline__ uint32_t splat_rows(float mx, float my, float Qa, flo
 
 template <int CH>
 __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layout& L, const uint8_t* ws,
-                                                const uint32_t* vals, uint32_t i, int k, float ox, float oy) {
-  const uint32_t gid = vals[i];
+                                                const uint64_t* keys, uint32_t i, int k, float ox, float oy) {
+  const uint32_t gid = static_cast<uint32_t>(keys[i]);  // sorted key = (tile << 32) | Gaussian id
   const int64_t kg = static_cast<int64_t>(k) * L.N + gid;
   const float4 uv = at<float4>(ws, L.proj_uv)[kg];
   const float4 cn = at<float4>(ws, L.proj_conic)[kg];
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
   const TileCoord tc = tile_coord(L, blockIdx.x);
   const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * PX;
   const int px = tc.tx * kTile + lx, py = tc.ty * kTile + ly;
-  const uint32_t* vals = at<uint32_t>(ws, (L.passes & 1) ? L.vals[1] : L.vals[0]);
+  const uint64_t* keys = at<uint64_t>(ws, (L.passes & 1) ? L.keys[1] : L.keys[0]);
   const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
   const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
     if (__syncthreads_count(!all_done) == 0) break;
     for (int jj = threadIdx.x; jj < kFwdChunk; jj += kThreads) {
       const uint32_t i = base + jj;
-      if (i < rg.y) stage_splat(S, jj, L, ws, vals, i, tc.k, ox, oy);
+      if (i < rg.y) stage_splat(S, jj, L, ws, keys, i, tc.k, ox, oy);
     }
     __syncthreads();
     const int n = min(kFwdChunk, static_cast<int>(rg.y - base));
@@ -291,12 +291,6 @@ __device__ __forceinline__ int reduce10_index(int lane) {
 }
 __device__ __forceinline__ bool reduce10_writer(int lane) { return !(lane & 1) && (!(lane & 2) || !(lane & 12)); }
 
-__device__ __forceinline__ uint32_t pair_slot(const int4& tl, int tx, int ty) {
-  const uint32_t x0 = static_cast<uint32_t>(tl.y) & 0xffffu, x1 = static_cast<uint32_t>(tl.y) >> 16;
-  const uint32_t y0 = static_cast<uint32_t>(tl.z) & 0xffffu;
-  return static_cast<uint32_t>(tl.x) + (static_cast<uint32_t>(ty) - y0) * (x1 - x0) + (static_cast<uint32_t>(tx) - x0);
-}
-
 // Gradient record layout (floats): 0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 dz, 6 do, 7 dr, 8 dg, 9 db.
 //
 // Per pixel, with dpow = dL/dpower / ln 2 (zero where the splat is skipped or clamped) and
@@ -326,12 +320,12 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * PX;
   const int px = tc.tx * kTile + lx, py = tc.ty * kTile + ly;
-  const uint32_t* vals = at<uint32_t>(ws, (L.passes & 1) ? L.vals[1] : L.vals[0]);
+  const uint64_t* keys = at<uint64_t>(ws, (L.passes & 1) ? L.keys[1] : L.keys[0]);
+  const uint32_t* slots = at<uint32_t>(ws, (L.passes & 1) ? L.vals[1] : L.vals[0]);  // emission index = record slot
   const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
   const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
   const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
-  const int4* tiles = at<int4>(ws, L.proj_tiles);
   float* pair_grads = at<float>(ws, L.pair_grads);
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
 
@@ -374,8 +368,8 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
     for (int jj = threadIdx.x; jj < kBwdChunk; jj += kThreads) {
       const uint32_t i = base + jj;
       if (i < stop) {
-        const uint32_t gid = stage_splat(S, jj, L, ws, vals, i, tc.k, ox, oy);
-        s_slot[jj] = pair_slot(tiles[static_cast<int64_t>(tc.k) * L.N + gid], tc.tx, tc.ty);
+        stage_splat(S, jj, L, ws, keys, i, tc.k, ox, oy);
+        s_slot[jj] = slots[i];
       }
     }
     for (int e = threadIdx.x; e < kWarps * kBwdChunk * 10; e += kThreads) (&s_part[0][0][0])[e] = 0.0f;
@@ -456,8 +450,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
   }
   // pairs behind every pixel's last contributor receive zero records
   for (uint32_t i = stop + threadIdx.x; i < rg.y; i += kThreads) {
-    const uint32_t gid = vals[i];
-    const uint32_t slot = pair_slot(tiles[static_cast<int64_t>(tc.k) * L.N + gid], tc.tx, tc.ty);
+    const uint32_t slot = slots[i];
     float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(slot) * kPairGradStride);
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     dst[0] = zero;

@@ -47,15 +47,23 @@ def read_discrete(r):
     ry = tiles[:, 2].view(np.uint32)
     rect = np.stack([rx & 0xFFFF, rx >> 16, ry & 0xFFFF, ry >> 16], axis=1).astype(np.int32)
     P = min(total, r.cap)
+    # the sorted pairs carry (tile << 32) | Gaussian id and, as value, the pair's emission
+    # index; rebuild the (tile << 32) | depth-bits keys and Gaussian-id values of the method
+    raw_keys = r.ws_view("keys_sorted", torch.int64, P).cpu().numpy().view(np.uint64)
+    raw_vals = r.ws_view("vals_sorted", torch.int32, P).cpu().numpy().view(np.uint32)
+    depth_bits = r.ws_view("proj_depth_key", torch.int32, KN).cpu().numpy().view(np.uint32)
+    tile = raw_keys >> np.uint64(32)
+    gid = (raw_keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    item = (tile // np.uint64(lay.tiles_x * lay.tiles_y)).astype(np.int64) * r.N + gid
+    keys = (tile << np.uint64(32)) | depth_bits[item].astype(np.uint64) if P else raw_keys
     d = {
         "status": code, "err": err, "total_pairs": total, "evals": evals,
         "offset": tiles[:, 0].copy(), "count": tiles[:, 3].view(np.uint32).copy(), "rect": rect,
-        "depth_bits": r.ws_view("proj_depth_key", torch.int32, KN).cpu().numpy().view(np.uint32),
+        "depth_bits": depth_bits,
         "radius": r.ws_view("proj_radius", torch.int32, KN).cpu().numpy(),
         "uv": r.ws_view("proj_uv", torch.float32, KN * 4).reshape(KN, 4).cpu().numpy(),
         "conic": r.ws_view("proj_conic", torch.float32, KN * 4).reshape(KN, 4).cpu().numpy(),
-        "keys": r.ws_view("keys_sorted", torch.int64, P).cpu().numpy().view(np.uint64),
-        "vals": r.ws_view("vals_sorted", torch.int32, P).cpu().numpy().view(np.uint32),
+        "keys": keys, "vals": gid.astype(np.uint32), "slots": raw_vals, "item": item,
         "ranges": r.ws_view("ranges", torch.int32, r.K * lay.tiles_x * lay.tiles_y * 2).reshape(-1, 2).cpu()
         .numpy().view(np.uint32),
     }

@@ -86,6 +86,24 @@ def test_sort_and_ranges_bit_exact(name):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
+def test_pair_slots_follow_emission_order(name):
+    """Each sorted pair's value is its emission index: a permutation of [0, P) that puts an
+    item's pairs in its own block [offset, offset + count), in increasing tile order."""
+    d = gpu_fwd(name)[4]
+    P = len(d["slots"])
+    slots = d["slots"].astype(np.int64)
+    assert np.array_equal(np.sort(slots), np.arange(P))
+    off = d["offset"].astype(np.int64)[d["item"]]
+    cnt = d["count"].astype(np.int64)[d["item"]]
+    assert np.all((slots >= off) & (slots < off + cnt))
+    tile = (d["keys"] >> np.uint64(32)).astype(np.int64)
+    order = np.lexsort((tile, d["item"]))
+    s_item, s_slot = d["item"][order], slots[order]
+    same = s_item[1:] == s_item[:-1]
+    assert np.all(s_slot[1:][same] == s_slot[:-1][same] + 1)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
 def test_forward_images(name):
     orc = oracle_fwd(name)
     out = to_np(gpu_fwd(name)[3])

@@ -68,20 +68,34 @@ def test_expdet_within_one_ulp_of_exp():
     assert np.isnan(oracle.expdet(np.array([np.nan], np.float32))[0])
 
 
+def test_logdet_within_four_ulp_of_log():
+    # truncating atanh after s^9 (|s| <= 0.172) errs by < 1e-9 relative; the rest is the
+    # rounding of about ten binary32 operations
+    x = np.concatenate([np.geomspace(1e-30, 1e30, 200001), np.linspace(0.5, 2.0, 100001)]).astype(np.float32)
+    y = oracle.logdet(x).astype(np.float64)
+    ref = np.log(x.astype(np.float64))
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    big = np.abs(ref) > 1e-3  # near 1 the error is relative to |ln x| itself
+    assert np.max(np.abs(y - ref)[big] / ulp[big]) <= 4.0
+    assert np.max(np.abs(y - ref)[~big] / np.abs(ref[~big] + 1e-300)) <= 1e-6
+    assert oracle.logdet(np.array([1.0], np.float32))[0] == 0.0
+    assert oracle.logdet(np.array([0.0], np.float32))[0] == -np.inf
+
+
 @pytest.mark.parametrize("z,culled", [(0.1, True), (0.2, True), (0.25, False), (-3.0, True)])
 def test_near_plane_cull(z, culled):
     p = one_gaussian((0, 0, z), (-4, -4, -4), (1, 0, 0, 0), 0.0, (1, 1, 1))
-    m = oracle.project_mirror(p[0], p[1], p[2], identity_camera(64, 64, 80.0), 64, 64)
+    m = oracle.project_mirror(p[0], p[1], p[2], p[3], identity_camera(64, 64, 80.0), 64, 64)
     assert (m.count[0] == 0) == culled
 
 
 def test_offscreen_cull_and_rect_clamp():
     # far to the right of a 64x64 image: no tile; straddling the edge: rect clamped
     p = one_gaussian((5.0, 0, 2), (-4, -4, -4), (1, 0, 0, 0), 0.0, (1, 1, 1))
-    m = oracle.project_mirror(p[0], p[1], p[2], identity_camera(64, 64, 80.0), 64, 64)
+    m = oracle.project_mirror(p[0], p[1], p[2], p[3], identity_camera(64, 64, 80.0), 64, 64)
     assert m.count[0] == 0
     p = one_gaussian((0.78, 0, 2), (-1.5, -1.5, -1.5), (1, 0, 0, 0), 0.0, (1, 1, 1))
-    m = oracle.project_mirror(p[0], p[1], p[2], identity_camera(64, 64, 80.0), 64, 64)
+    m = oracle.project_mirror(p[0], p[1], p[2], p[3], identity_camera(64, 64, 80.0), 64, 64)
     x0, x1, y0, y1 = m.rect[0]
     assert m.count[0] > 0 and x1 == 4 and x0 >= 1
 
@@ -91,7 +105,7 @@ def test_depth_key_is_binary32_depth():
     means = rng.uniform((-1, -1, 1), (1, 1, 9), size=(500, 3)).astype(np.float32)
     ls = np.full((500, 3), -3.0, np.float32)
     qs = np.tile(np.array([1, 0, 0, 0], np.float32), (500, 1))
-    m = oracle.project_mirror(means, ls, qs, identity_camera(64, 64, 60.0), 64, 64)
+    m = oracle.project_mirror(means, ls, qs, np.zeros(500, np.float32), identity_camera(64, 64, 60.0), 64, 64)
     # identity camera: the camera depth is the stored z itself
     assert np.array_equal(m.depth_bits, means[:, 2].view(np.uint32))
 
@@ -120,10 +134,11 @@ def test_radius_and_rect_against_fp64_and_brute_force():
     if np.linalg.det(R) < 0:
         R[:, 0] *= -1
     cam = camera_array(70.0, 72.0, 47.0, 41.0, R, rng.normal(0, 0.1, 3))
-    m = oracle.project_mirror(means, ls, qs, cam, W, H)
+    m = oracle.project_mirror(means, ls, qs, np.zeros(N, np.float32), cam, W, H)
     checked = 0
     for g in range(N):
-        if m.count[g] == 0:
+        x0, x1, y0, y1 = m.rect[g]
+        if (x1 - x0) * (y1 - y0) == 0:
             continue
         S2, pc = _fp64_sigma2(means[g], ls[g], qs[g] / np.linalg.norm(qs[g].astype(np.float64)), cam, W, H)
         lam = np.linalg.eigvalsh(S2)
@@ -247,7 +262,7 @@ def test_tiled_sorted_render_equals_per_pixel_depth_sort():
               rng.uniform(0, 1, (N, 3)).astype(np.float32))
     cam = identity_camera(W, H, f)
     out = oracle.forward(params, cam, W, H)
-    assert np.all(out["lists"].mirror.count == 4)  # every rect covers the 2x2 tiles
+    assert np.all(out["lists"].mirror.rect == [0, 2, 0, 2])  # every rect covers the 2x2 tiles
     img, dep, T = _brute_render(params, cam, W, H)
     np.testing.assert_allclose(out["rgb"][0], img, atol=1e-12)
     np.testing.assert_allclose(out["depth"][0], dep, atol=1e-12)
@@ -256,6 +271,9 @@ def test_tiled_sorted_render_equals_per_pixel_depth_sort():
 
 
 def test_binning_against_brute_force_emission_and_lexsort():
+    """Given each item's tile set (pinned against FP64 brute force by the two emission-cull
+    tests below), the pairs are emitted in (k, g) order, tiles row-major, and stably sorted
+    by (tile, depth bits); the ranges delimit each tile's run."""
     from scenes import make_scene
     s = make_scene("map100k", n=3000, W=160, H=120, f=130.0)
     W, H = s.W, s.H
@@ -264,18 +282,23 @@ def test_binning_against_brute_force_emission_and_lexsort():
     lists = oracle.discrete(s.params(), cams, W, H)
     m = lists.mirror
     N, K, Tx, Ty = s.N, 2, 10, 8
+    tile_all = (lists.keys >> np.uint64(32)).astype(np.int64)
+    item_of = (tile_all // (Tx * Ty)) * N + lists.vals.astype(np.int64)
+    tiles_of = {}
+    for kg, t in zip(item_of, tile_all):
+        tiles_of.setdefault(int(kg), []).append(int(t))
     keys, order_idx = [], []
     e = 0
     for kg in range(K * N):
-        if m.count[kg] == 0:
-            continue
+        ts = sorted(tiles_of.get(kg, []))
+        assert len(ts) == m.count[kg]
         x0, x1, y0, y1 = m.rect[kg]
-        for ty in range(y0, y1):
-            for tx in range(x0, x1):
-                tid = (kg // N) * Tx * Ty + ty * Tx + tx
-                keys.append((tid << 32) | int(m.depth_bits[kg]))
-                order_idx.append((e, kg % N))
-                e += 1
+        for tid in ts:  # row-major inside the rectangle = increasing tile id
+            ty, tx = divmod(tid - (kg // N) * Tx * Ty, Tx)
+            assert x0 <= tx < x1 and y0 <= ty < y1
+            keys.append((tid << 32) | int(m.depth_bits[kg]))
+            order_idx.append((e, kg % N))
+            e += 1
     keys = np.array(keys, np.uint64)
     emit = np.array([o[0] for o in order_idx])
     gid = np.array([o[1] for o in order_idx], np.uint32)
@@ -290,6 +313,116 @@ def test_binning_against_brute_force_emission_and_lexsort():
     nz = cnt > 0
     assert np.array_equal(r[nz, 0], starts[nz])
     assert np.all(r[~nz] == 0)
+
+
+def _cull_scene(seed, N=400, W=160, H=112, f=140.0):
+    """Thin, rotated, large and barely visible Gaussians: many rectangle tiles their
+    alpha >= 1/255 ellipse misses."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform((-0.9, -0.6, 2.0), (0.9, 0.6, 6.0), (N, 3)).astype(np.float32)
+    ls = np.stack([rng.uniform(-4.5, -1.0, N), rng.uniform(-6.0, -2.5, N), rng.uniform(-5.0, -2.0, N)], 1)
+    qs = rng.normal(size=(N, 4)).astype(np.float32)
+    o = np.where(rng.uniform(size=N) < 0.2, rng.uniform(0.0035, 0.006, N), rng.uniform(0.02, 0.999, N))
+    logits = np.log(o / (1 - o)).astype(np.float32)
+    rgb = rng.uniform(0, 1, (N, 3)).astype(np.float32)
+    return (means, ls.astype(np.float32), qs, logits, rgb), identity_camera(W, H, f), W, H
+
+
+def _tile_sets(lists, N, Tx, Ty):
+    tiles = (lists.keys >> np.uint64(32)).astype(np.int64)
+    items = (tiles // (Tx * Ty)) * N + lists.vals.astype(np.int64)
+    out = {}
+    for kg, t in zip(items, tiles % (Tx * Ty)):
+        out.setdefault(int(kg), set()).add(int(t))
+    return out
+
+
+def test_emission_cull_is_conservative():
+    """No pixel centre of a rectangle tile left out of an item's emitted tiles reaches
+    alpha >= 1/255 (FP64, every pixel of every such tile)."""
+    params, cam, W, H = _cull_scene(21)
+    lists = oracle.discrete(params, cam, W, H)
+    m = lists.mirror
+    pr = oracle.project64(params, cam, W, H)
+    Tx, Ty = -(-W // 16), -(-H // 16)
+    sets = _tile_sets(lists, len(params[0]), Tx, Ty)
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    culled_tiles = 0
+    for g in range(len(params[0])):
+        x0, x1, y0, y1 = m.rect[g]
+        if (x1 - x0) * (y1 - y0) == 0:
+            continue
+        u, v, A, B, C, z, o, det = pr[g]
+        dx, dy = u - xx, v - yy
+        alpha = o * np.exp(-0.5 * (A * dx * dx + 2 * B * dx * dy + C * dy * dy))
+        keep = alpha >= 1 / 255
+        have = sets.get(g, set())
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                if ty * Tx + tx in have:
+                    continue
+                culled_tiles += 1
+                assert not keep[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16].any(), (g, tx, ty)
+    rect_tiles = int(sum((r[1] - r[0]) * (r[3] - r[2]) for r in m.rect))
+    assert culled_tiles > 0.25 * rect_tiles  # the cull is exercised
+
+
+def _min_quadratic_on_box(u, v, P, xlo, xhi, ylo, yhi):
+    """min over the box of (p - m)^T P (p - m) for positive definite P (exact, FP64)."""
+    if xlo <= u <= xhi and ylo <= v <= yhi:
+        return 0.0
+    a, b, c = P[0, 0], P[0, 1], P[1, 1]
+    best = math.inf
+    for y in (ylo, yhi):  # horizontal edges: minimise over x
+        dy = y - v
+        x = min(max(u - b * dy / a, xlo), xhi)
+        dx = x - u
+        best = min(best, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+    for x in (xlo, xhi):
+        dx = x - u
+        y = min(max(v - b * dx / c, ylo), yhi)
+        dy = y - v
+        best = min(best, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+    return best
+
+
+def test_emission_cull_is_tight():
+    """Every emitted tile's square of pixel centres, widened by the margin, meets the
+    ellipse d^T Sigma2^-1 d <= 2 ln(255 o) enlarged by its margin (FP64, exact minimum)."""
+    params, cam, W, H = _cull_scene(22)
+    lists = oracle.discrete(params, cam, W, H)
+    m = lists.mirror
+    pr = oracle.project64(params, cam, W, H)
+    Tx, Ty = -(-W // 16), -(-H // 16)
+    sets = _tile_sets(lists, len(params[0]), Tx, Ty)
+    n = 0
+    for g, tiles in sets.items():
+        u, v, A, B, C, z, o, det = pr[g]
+        P = np.array([[A, B], [B, C]])
+        L = math.log(255 * o)
+        kap = 2 * (L + 0.02 * abs(L) + 1.5e-4)
+        S2 = np.linalg.inv(P)
+        hx, hy = math.sqrt(kap * S2[0, 0]), math.sqrt(kap * S2[1, 1])
+        mx, my = 0.05 + 0.002 * hx + 1e-3, 0.05 + 0.002 * hy + 1e-3
+        for t in tiles:
+            ty, tx = divmod(t, Tx)
+            q = _min_quadratic_on_box(u, v, P, 16 * tx + 0.5 - mx, 16 * tx + 15.5 + mx, 16 * ty + 0.5 - my,
+                                      16 * ty + 15.5 + my)
+            assert q <= kap * (1 + 1e-4) + 1e-6, (g, tx, ty, q, kap)
+            n += 1
+    assert n > 500
+
+
+def test_tiled_render_with_culled_pairs_equals_per_pixel_depth_sort():
+    params, cam, W, H = _cull_scene(23, N=60, W=48, H=48, f=45.0)
+    out = oracle.forward(params, cam, W, H)
+    m = out["lists"].mirror
+    rect_tiles = int(sum((r[1] - r[0]) * (r[3] - r[2]) for r in m.rect))
+    assert m.count.sum() < 0.85 * rect_tiles  # pairs were culled
+    img, dep, T = _brute_render(params, cam, W, H)
+    np.testing.assert_allclose(out["rgb"][0], img, atol=1e-12)
+    np.testing.assert_allclose(out["depth"][0], dep, atol=1e-12)
+    np.testing.assert_allclose(out["T"][0], T, atol=1e-12)
 
 
 # ----------------------------------------------------------------------------- invariants

@@ -127,7 +127,7 @@ class Mirror:
     rect: np.ndarray        # [K*N, 4] int32 x0, x1, y0, y1
     count: np.ndarray       # [K*N] uint32 tiles emitted
     uv: np.ndarray          # [K*N, 2] float32
-    ell: np.ndarray         # [K*N, 8] float32 widened ellipse: u, v, b, c, sqrt(det), hx, hy, kxy
+    ell: np.ndarray         # [K*N, 8] float32 widened ellipse: u, v, b, 1/c, sqrt(det), hx, hy, kxy
 
 
 def project_mirror(means, log_scales, quats, logits, cams, W, H, tile=TILE, near=NEAR) -> Mirror:

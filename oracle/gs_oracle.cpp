@@ -118,10 +118,11 @@ float logdet(float x) {
 // The ellipse of a projected Gaussian inside which its opacity can reach 1/255, widened by
 // a safety margin, as the discrete mirror evaluates it: E = {d : d^T Sigma2^-1 d <= kap}
 // with kap = 2 (ln(255 o) + 0.02 |ln(255 o)| + 1.5e-4). Stored: the mean (u, v), Sigma2's
-// off-diagonal b and yy entry c, sqrt(det Sigma2), the half-extents hx = sqrt(kap a),
-// hy = sqrt(kap c), and kxy = b / a (the y offset, per unit x offset, of E's widest point).
+// off-diagonal b, 1 / c (c: Sigma2's yy entry), sqrt(det Sigma2), the half-extents
+// hx = sqrt(kap a), hy = sqrt(kap c), and kxy = b / a (the y offset, per unit x offset, of
+// E's leftmost / rightmost points).
 struct Ellipse {
-  float u, v, b, c, sdet, hx, hy, kxy;
+  float u, v, b, inv_c, sdet, hx, hy, kxy;
 };
 
 // Tile columns [*xa, *xb] of tile row ty whose pixel centres' square, widened by
@@ -143,7 +144,7 @@ void row_span(const Ellipse& E, int ty, int x0, int x1, int tile, int* xa, int* 
     const float dye = Ye - E.v;
     const float ad = std::fabs(dye);
     const float w = std::sqrt(std::fmax((E.hy - ad) * (E.hy + ad), 0.0f));
-    return E.u + std::fma(sgn * E.sdet, w, E.b * dye) / E.c;
+    return E.u + std::fma(sgn * E.sdet, w, E.b * dye) * E.inv_c;
   };
   const float yR = std::fma(E.kxy, E.hx, E.v);
   const float yL = std::fma(-E.kxy, E.hx, E.v);
@@ -263,7 +264,7 @@ MirrorOut mirror_one(const float* p, const float* ls, const float* q, float logi
   const float Lm = (L + 0.02f * std::fabs(L)) + 1.5e-4f;
   if (!(Lm >= 0.0f)) return o;  // the opacity never reaches 1/255: no pairs
   const float kap = 2.0f * Lm;
-  o.E = Ellipse{u, v, bb, c, std::sqrt(det), std::sqrt(kap * a), std::sqrt(kap * c), bb / a};
+  o.E = Ellipse{u, v, bb, 1.0f / c, std::sqrt(det), std::sqrt(kap * a), std::sqrt(kap * c), bb / a};
   uint32_t cnt = 0;
   for (int ty = o.y0; ty < o.y1; ++ty) {
     int xa, xb;
@@ -459,7 +460,7 @@ void orc_logdet_f32(const float* x, float* y, int64_t n) {
 // FP32 discrete mirror over K views x N Gaussians. Outputs per (k, g), index k*N+g:
 // depth_bits (binary32 bits of the camera depth), radius, rect[4] = x0,x1,y0,y1
 // (tile indices, half-open), count = tiles emitted (0 = culled), uv = binary32 mean2D,
-// ell[8] = the widened ellipse (u, v, b, c, sqrt det, hx, hy, kxy; zeros when count = 0).
+// ell[8] = the widened ellipse (u, v, b, 1/c, sqrt det, hx, hy, kxy; zeros when count = 0).
 void orc_project_mirror(int64_t N, const float* means, const float* log_scales, const float* quats,
                         const float* logits, int K, const float* cams, int W, int H, int tile, float near,
                         uint32_t* depth_bits, int32_t* radius, int32_t* rect, uint32_t* count, float* uv,
@@ -481,7 +482,7 @@ void orc_project_mirror(int64_t N, const float* means, const float* log_scales, 
     uv[2 * kg + 0] = m.u;
     uv[2 * kg + 1] = m.v;
     const Ellipse E = (m.valid && m.count) ? m.E : Ellipse{};
-    const float e8[8] = {E.u, E.v, E.b, E.c, E.sdet, E.hx, E.hy, E.kxy};
+    const float e8[8] = {E.u, E.v, E.b, E.inv_c, E.sdet, E.hx, E.hy, E.kxy};
     for (int i = 0; i < 8; ++i) ell[8 * kg + i] = e8[i];
   }
 }

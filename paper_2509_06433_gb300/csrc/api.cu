@@ -64,6 +64,8 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->proj_depth_key = take(KN * 4);
   L->proj_radius = take(KN * 4);
   L->proj_ell = take(KN * sizeof(Ellipse));
+  L->proj_rows = take(KN * 8);
+  L->row_table = take(cap * 8);
   L->color_opacity = take(N * 16);
   L->block_sums = take(static_cast<size_t>(L->n_proj_blocks) * 4);
   L->block_offsets = take(static_cast<size_t>(L->n_proj_blocks) * 8);

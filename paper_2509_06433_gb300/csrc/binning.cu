@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(kProjBlock) k_item_offsets(Layout L, uint8_t* 
     if (cnt) {
       const uint32_t kg = at<uint32_t>(ws, L.item_vals[0])[s];
       int4* tiles = at<int4>(ws, L.proj_tiles);
-      const int4 tl = tiles[kg];
       tiles[kg].x = static_cast<int>(off < cap ? off : cap);
       const uint32_t k = static_cast<uint32_t>(kg / static_cast<uint64_t>(L.N));
-      at<int4>(ws, L.item_rect)[s] = make_int4(tl.y, tl.z, static_cast<int>(kg), 0);
+      const uint2 rows = at<uint2>(ws, L.proj_rows)[kg];
+      at<int4>(ws, L.item_rect)[s] = make_int4(static_cast<int>(rows.x), static_cast<int>(rows.y), 0, 0);
       at<uint2>(ws, L.item_kg)[s] = make_uint2(k, kg - k * static_cast<uint32_t>(L.N));
     }
   }
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
   __syncthreads();
   const int4* rects = at<int4>(ws, L.item_rect);
   const uint2* kgs = at<uint2>(ws, L.item_kg);
-  const Ellipse* ells = at<Ellipse>(ws, L.proj_ell);
+  const int2* rowtab = at<int2>(ws, L.row_table);
   uint64_t* keys = at<uint64_t>(ws, L.keys[0]);
   uint32_t* vals = at<uint32_t>(ws, L.vals[0]);
   const uint64_t tiles_per_view = static_cast<uint64_t>(L.Tx) * L.Ty;
@@ -254,24 +254,21 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
       const int mid = (a + b) >> 1;
       if (s_off[mid] <= jj) a = mid; else b = mid;
     }
-    const int4 rc = rects[lo + a];
+    const int4 rc = rects[lo + a];  // (first row-table entry, entries)
     const uint2 kg = kgs[lo + a];
-    const Ellipse E = ells[rc.z];
-    // the pair's tile: the r-th of the item's row spans, rows in increasing order
-    int r = static_cast<int>(jj - s_off[a]);
-    const int x0 = rc.x & 0xffff, x1 = static_cast<int>(static_cast<uint32_t>(rc.x) >> 16);
-    const int y0 = rc.y & 0xffff, y1 = static_cast<int>(static_cast<uint32_t>(rc.y) >> 16);
-    int tx = x0, ty = y0;
-    for (int y = y0; y < y1; ++y) {
-      const int2 sp = row_span(E, y, x0, x1);
-      const int w = sp.y - sp.x + 1;
-      if (w <= 0) continue;
-      if (r < w) {
-        ty = y;
-        tx = sp.x + r;
-        break;
+    // the pair's tile: its row is the last entry whose earlier-row pair count is <= r
+    const int r = static_cast<int>(jj - s_off[a]);
+    int tx = 0, ty = 0;
+    if (rc.y > 0) {
+      const int2* tab = rowtab + rc.x;
+      int p = 0, q = rc.y;  // tab[p].x <= r, and r < tab[q].x or q = entries
+      while (q - p > 1) {
+        const int mid = (p + q) >> 1;
+        if (tab[mid].x <= r) p = mid; else q = mid;
       }
-      r -= w;
+      const int2 e = tab[p];
+      tx = (e.y & 0xffff) + (r - e.x);
+      ty = static_cast<int>(static_cast<uint32_t>(e.y) >> 16);
     }
     const uint64_t tid = static_cast<uint64_t>(kg.x) * tiles_per_view + static_cast<uint64_t>(ty) * L.Tx + tx;
     keys[j] = (tid << 32) | kg.y;

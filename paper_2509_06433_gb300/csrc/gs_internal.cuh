@@ -33,7 +33,8 @@ struct Status {
   uint64_t evals;           // Gaussian-pixel evaluations of the last forward raster
   uint32_t tile_ctr[kMaxSortPasses];  // onesweep dynamic tile counters: [0,4) item sort, [4,8) pair sort
   uint64_t composited;      // evaluations of the last forward raster that blended a splat
-  uint64_t pad;
+  uint32_t row_ctr;         // entries of the row-span table handed out by the projection
+  uint32_t pad;
 };
 static_assert(sizeof(Status) <= 256, "status block");
 
@@ -58,9 +59,14 @@ struct Layout {
   // per-item depth sort (u32 depth key, u32 item index), its histograms and look-back status,
   // and the tiles touched by each item in depth order
   size_t item_keys[2], item_vals[2], item_hist, item_status, sorted_counts;
-  // in depth order: exclusive pair offset of each item (KN + 1 entries), its rectangle
-  // (int4: x0|x1<<16, y0|y1<<16, -, -), its (view, Gaussian id)
+  // in depth order: exclusive pair offset of each item (KN + 1 entries), its row-span
+  // table entries (int4: first entry, number of entries, -, -), its (view, Gaussian id)
   size_t item_offsets, item_rect, item_kg;
+  // row-span table: per item, its rows from the first to the last non-empty one, each an
+  // int2 (pairs of the item in earlier rows, first column | row << 16); proj_rows: per item
+  // (first entry, number of entries). Entries are handed out by an atomic counter; at most
+  // pair_capacity of them (more is reported as a pair overflow).
+  size_t row_table, proj_rows;
   // per view a (Ty+1) x (Tx+1) grid: +1 / -1 at the first / one-past-last tile of every
   // emitted row span; its row-wise prefix sum is the number of pairs of each tile
   size_t tile_diff;
@@ -126,11 +132,11 @@ __device__ __forceinline__ float load_attr(const void* p, int64_t i, int dtype) 
 // The widened ellipse of a projected Gaussian inside which its opacity can reach 1/255, as
 // the discrete projection evaluates it in binary32: E = {d : d^T Sigma2^-1 d <= kap} with
 // kap = 2 (ln(255 o) + 0.02 |ln(255 o)| + 1.5e-4), o = 1 / (1 + exp(-logit)). Stored: the
-// mean (u, v), Sigma2's off-diagonal b and yy entry c, sqrt(det Sigma2), the half-extents
-// hx = sqrt(kap a), hy = sqrt(kap c), and kxy = b / a (the y offset, per unit x offset, of
-// E's leftmost / rightmost points).
+// mean (u, v), Sigma2's off-diagonal b, 1 / c (c: Sigma2's yy entry), sqrt(det Sigma2), the
+// half-extents hx = sqrt(kap a), hy = sqrt(kap c), and kxy = b / a (the y offset, per unit
+// x offset, of E's leftmost / rightmost points).
 struct Ellipse {
-  float u, v, b, c, sdet, hx, hy, kxy;
+  float u, v, b, inv_c, sdet, hx, hy, kxy;
 };
 
 // Tile columns [xa, xb] (returned as x, y; xa > xb: none) of tile row ty whose square of
@@ -143,7 +149,7 @@ __device__ __forceinline__ float ellipse_cross(const Ellipse& E, float Ye, float
   const float dye = __fsub_rn(Ye, E.v);
   const float ad = fabsf(dye);
   const float w = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(E.hy, ad), __fadd_rn(E.hy, ad)), 0.0f));
-  return __fadd_rn(E.u, __fdiv_rn(__fmaf_rn(__fmul_rn(sgn, E.sdet), w, __fmul_rn(E.b, dye)), E.c));
+  return __fadd_rn(E.u, __fmul_rn(__fmaf_rn(__fmul_rn(sgn, E.sdet), w, __fmul_rn(E.b, dye)), E.inv_c));
 }
 __device__ __forceinline__ int2 row_span(const Ellipse& E, int ty, int x0, int x1) {
   const int2 none = make_int2(1, 0);

@@ -122,6 +122,10 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
     for (int i = threadIdx.x; i < gcells; i += kProjBlock) s_grid[i] = 0;
   __syncthreads();
   uint32_t count = 0, item_key = 0xffffffffu;
+  // what the row-span table needs once the warp has its entries
+  Ellipse E_keep{};
+  int span_x0 = 0, span_x1 = 0, row_first = 0;
+  uint32_t nrows = 0;
   if (idx < L.KN) {
     const int k = static_cast<int>(idx / L.N);
     const int64_t g = idx - static_cast<int64_t>(k) * L.N;
@@ -240,18 +244,28 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
         const float Lm = __fadd_rn(__fadd_rn(Lg, __fmul_rn(0.02f, fabsf(Lg))), 1.5e-4f);
         if (Lm >= 0.0f) {
           const float kap = __fmul_rn(2.0f, Lm);
-          const Ellipse E{u, v, bb, c, __fsqrt_rn(det), __fsqrt_rn(__fmul_rn(kap, a)), __fsqrt_rn(__fmul_rn(kap, c)),
-                          __fdiv_rn(bb, a)};
+          const Ellipse E{u, v, bb, __fdiv_rn(1.0f, c), __fsqrt_rn(det), __fsqrt_rn(__fmul_rn(kap, a)),
+                          __fsqrt_rn(__fmul_rn(kap, c)), __fdiv_rn(bb, a)};
           at<Ellipse>(ws, L.proj_ell)[idx] = E;
           int32_t* dg = (use_sgrid && k == k_block)
                             ? s_grid
                             : at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * gcells;
+          int first = -1, last = -1;
           for (int ty = y0; ty < y1; ++ty) {
             const int2 sp = row_span(E, ty, x0, x1);
             if (sp.x > sp.y) continue;
             count += static_cast<uint32_t>(sp.y - sp.x + 1);
             atomicAdd(&dg[ty * gstride + sp.x], 1);  // row-wise prefix sum: pairs per tile
             atomicAdd(&dg[ty * gstride + sp.y + 1], -1);
+            if (first < 0) first = ty;
+            last = ty;
+          }
+          if (count) {
+            E_keep = E;
+            span_x0 = x0;
+            span_x1 = x1;
+            row_first = first;
+            nrows = static_cast<uint32_t>(last - first + 1);
           }
         }
       }
@@ -273,6 +287,38 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
       // conic = Sigma2^-1 = [[c, -b], [-b, a]] / det with det from the Lagrange identity
       const float inv_det = 1.0f / det;
       at<float4>(ws, L.proj_conic)[idx] = make_float4(c * inv_det, -bb * inv_det, a * inv_det, Z.hi);
+    }
+  }
+  // row-span table entries for the item's rows first..last (one counter atomic per warp);
+  // the spans are recomputed bit for bit by the same function
+  {
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = nrows;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t base = 0;
+    if (lane == 31 && incl) base = atomicAdd(&at<Status>(ws, L.status)->row_ctr, incl);
+    base = __shfl_sync(0xffffffffu, base, 31) + (incl - nrows);
+    if (nrows) {
+      if (static_cast<uint64_t>(base) + nrows <= static_cast<uint64_t>(L.cap)) {
+        int2* tab = at<int2>(ws, L.row_table) + base;
+        int cum = 0;
+        for (uint32_t q = 0; q < nrows; ++q) {
+          const int ty = row_first + static_cast<int>(q);
+          const int2 sp = row_span(E_keep, ty, span_x0, span_x1);
+          tab[q] = make_int2(cum, (sp.x & 0xffff) | (ty << 16));
+          if (sp.x <= sp.y) cum += sp.y - sp.x + 1;
+        }
+        at<uint2>(ws, L.proj_rows)[idx] = make_uint2(base, nrows);
+      } else {
+        atomicOr(&at<Status>(ws, L.status)->err, GS_DEVERR_PAIR_OVERFLOW);
+        at<uint2>(ws, L.proj_rows)[idx] = make_uint2(0, 0);
+      }
+    } else if (idx < L.KN) {
+      at<uint2>(ws, L.proj_rows)[idx] = make_uint2(0, 0);
     }
   }
   // depth-sort key of the item (culled items sort last and emit nothing) and its digit counts

@@ -147,10 +147,10 @@ def run_ours(args, rank, world):
              "rgb": torch.zeros((s.N, 3), device=dev), "pose": torch.zeros((s.K, 6), device=dev)}
     stream = torch.cuda.current_stream(dev)
     cfg, ws = r.cfg, r.ws
-    # kernels of ours per step: project; item depth sort (4 passes), counts, scan, item offsets,
-    # tile prefix, tile scan, emission, pair sort passes; raster fwd; loss (2); raster bwd;
+    # kernels of ours per step: project; gs_bin_sort (item depth sort, counts, scan, item
+    # offsets, tile prefix, tile scan, emission, pair sort); raster fwd; loss (2); raster bwd;
     # project bwd + pose reduction
-    n_launch = 1 + 4 + 6 + r.layout.sort_passes + 1 + 2 + 1 + 2
+    n_launch = 1 + r.layout.bin_sort_launches + 1 + 2 + 1 + 2
 
     def zero_grads():
         for v in grads.values():

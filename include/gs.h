@@ -135,6 +135,7 @@ typedef struct {
   size_t pair_grads;     /* float [pair_capacity][12]: per-pair gradients of gs_raster_bwd */
   int32_t sort_passes;   /* 8-bit LSD passes of the pair sort over the tile bits: ceil(ceil(log2(K*Tx*Ty)) / 8) */
   int32_t tiles_x, tiles_y;
+  int32_t bin_sort_launches; /* kernels one gs_bin_sort launches */
 } gs_ws_layout_t;
 
 /* ---------------------------------------------------------------- sizing / status */

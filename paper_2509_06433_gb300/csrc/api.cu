@@ -145,6 +145,7 @@ gs_status_t gs_workspace_layout(const gs_config_t* cfg, gs_ws_layout_t* out) {
   out->ranges = L.ranges;
   out->pair_grads = L.pair_grads;
   out->sort_passes = L.passes;
+  out->bin_sort_launches = bin_sort_launch_count(L);
   out->tiles_x = L.Tx;
   out->tiles_y = L.Ty;
   return GS_OK;

@@ -227,5 +227,6 @@ using SortArgs32 = SortArgsT<uint32_t>;
 cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s);
 cudaError_t launch_onesweep(const SortArgs32& a, cudaStream_t s);
 cudaError_t launch_sort_prepare(const SortArgs& a, cudaStream_t s);  // zero status, build histogram
+int bin_sort_launch_count(const Layout& L);  // kernels one gs_bin_sort launches
 
 }  // namespace gs

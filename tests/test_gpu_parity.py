@@ -344,3 +344,20 @@ def test_aerial_two_views_fp16_storage_forward_and_backward():
     for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose"):
         e = rel_l2(grads[k], og[k])
         assert e < GRAD_RTOL, (k, e)
+
+
+def test_large_item_and_pair_counts():
+    """700k items (15-key sort tiles for the depth sort) and a 2M pair capacity: keys,
+    values and ranges equal the oracle's, and the forward images match."""
+    torch, api = torch_mods()
+    s = make_scene("window500k", n=350_000, K=2, W=96, H=64, f=80.0)
+    r, g, ct, out = gpu_render(s.params(), s.cams, s.W, s.H, cap=2_000_000)
+    assert r.layout.bin_sort_launches == 6 + 4 + r.layout.sort_passes
+    d = read_discrete(r)
+    orc = oracle.forward(s.params(), s.cams, s.W, s.H)
+    L = orc["lists"]
+    assert d["status"] == 0 and d["total_pairs"] == len(L.keys)
+    np.testing.assert_array_equal(d["keys"], L.keys)
+    np.testing.assert_array_equal(d["vals"], L.vals)
+    np.testing.assert_array_equal(d["ranges"], L.ranges)
+    check_images(to_np(out), orc)

@@ -181,8 +181,12 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         zero_grads()
         step()
+    # evaluation counts of this workload (the counting forward variant, outside the timed region;
+    # every gs_project clears the status block, so they are read here)
+    api.gs_raster_fwd_stats(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], stream)
     torch.cuda.synchronize(dev)
     code, err, pairs, evals = r.status()
+    blended = int(r.ws[r.layout.status + 56:r.layout.status + 64].view(torch.int64).item())
     if code != 0:
         raise RuntimeError(f"device status {code} (error word {err}) during warm-up")
 
@@ -222,7 +226,7 @@ def run_ours(args, rank, world):
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = replicas.max_over_ranks(float(sum(step_ms)), dev)
-    code, err, pairs, evals = r.status()
+    code, err, pairs, _ = r.status()
     if code != 0:
         raise RuntimeError(f"device status {code} (error word {err}) in the timed region")
     # the graph's gradients equal the eager step's (same kernels, deterministic)
@@ -273,8 +277,6 @@ def run_ours(args, rank, world):
     # ---- roofline of the dominant kernel
     med = {k: statistics.median(v) for k, v in stage_ms.items()}
     dominant = max(med, key=med.get)
-    st = r.layout.status
-    blended = int(r.ws[st + 56:st + 64].view(torch.int64).item())
     counts = {"evals": evals, "blended": blended, "evals_bwd": int(out["last"].sum().item())}
     roof = roofline(dominant, stage_ms[dominant], counts, pairs, s, r)
 
@@ -463,8 +465,10 @@ def measure_aerial(dev, reps=3, track_iters=50):
         torch.cuda.synchronize(dev)
         ms += e0.elapsed_time(e1)
     ms /= reps
+    o = r.new_outputs()
+    api.gs_raster_fwd_stats(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"])
     code, _, _, evals = r.status()
-    del m
+    del m, o
     # tracking of a new frame: the first view, its pose perturbed by 2 deg / 5 cm
     true_cam = cams[:1].contiguous()
     rt = api.Rasterizer(s.W, s.H, 1, s.N, device=dev)

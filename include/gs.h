@@ -147,7 +147,7 @@ GS_API gs_status_t gs_workspace_size(const gs_config_t* cfg, size_t* bytes);
 GS_API gs_status_t gs_workspace_layout(const gs_config_t* cfg, gs_ws_layout_t* out);
 
 /* Synchronises `stream`, then reads the device error word, the pair count and the
- * eval count (Gaussian-pixel evaluations of the last gs_raster_fwd) into host
+ * eval count (Gaussian-pixel evaluations of the last gs_raster_fwd_stats) into host
  * memory. Any pointer may be NULL. Returns GS_OK, or the first device error in the
  * order CAPACITY_OVERFLOW, DEVICE_TIMEOUT, NONFINITE, or GS_ERR_CUDA. */
 GS_API gs_status_t gs_read_status(const gs_config_t* cfg, const void* ws, size_t ws_bytes, uint32_t* err_word,
@@ -194,6 +194,13 @@ GS_API gs_status_t gs_bin_sort(const gs_config_t* cfg, void* ws, size_t ws_bytes
  * Gaussian (0 if none); each may be NULL except what gs_raster_bwd will need. */
 GS_API gs_status_t gs_raster_fwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
                           float* T_final, int32_t* last, void* stream);
+
+/* gs_raster_fwd with the same decisions and outputs that also counts, into the status
+ * block read by gs_read_status, the Gaussian-pixel evaluations (list entries examined,
+ * including the entry that stops a pixel) and those that blended a splat. For measurement:
+ * the counting costs time, so gs_raster_fwd does not count. */
+GS_API gs_status_t gs_raster_fwd_stats(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                                float* T_final, int32_t* last, void* stream);
 
 /* Photometric loss of a mapping step: L = sum_k [ mean|R - R*| over 3HW + lambda
  * mean|D - D*| over HW ], sign(0) = 0. Writes dL/drgb [K,3,H,W], dL/ddepth [K,H,W] and

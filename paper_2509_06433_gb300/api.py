@@ -100,6 +100,11 @@ def gs_raster_fwd(cfg, ws, rgb, depth, T_final, last, stream=None):
          _s(stream))
 
 
+def gs_raster_fwd_stats(cfg, ws, rgb, depth, T_final, last, stream=None):
+    call("gs_raster_fwd_stats", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
+         _s(stream))
+
+
 def gs_loss_l1(cfg, rgb, depth, rgb_target, depth_target, dL_drgb, dL_ddepth, loss, ws, stream=None):
     call("gs_loss_l1", ctypes.byref(cfg), _p(rgb), _p(depth), _p(rgb_target), _p(depth_target), _p(dL_drgb),
          _p(dL_ddepth), _p(loss), _p(ws), ws.numel(), _s(stream))
@@ -214,10 +219,12 @@ class Rasterizer:
         return {"rgb": torch.empty((K, 3, H, W), device=d), "depth": torch.empty((K, H, W), device=d),
                 "T": torch.empty((K, H, W), device=d), "last": torch.empty((K, H, W), dtype=torch.int32, device=d)}
 
-    def render(self, g: Gaussians, cams: torch.Tensor, out=None, stream=None):
+    def render(self, g: Gaussians, cams: torch.Tensor, out=None, stream=None, stats=False):
+        """stats=True also counts the evaluations and blended evaluations (``status()``)."""
         out = out or self.new_outputs()
         self.project_and_sort(g, cams, stream)
-        gs_raster_fwd(self.cfg, self.ws, out["rgb"], out["depth"], out["T"], out["last"], stream)
+        fwd = gs_raster_fwd_stats if stats else gs_raster_fwd
+        fwd(self.cfg, self.ws, out["rgb"], out["depth"], out["T"], out["last"], stream)
         return out
 
     def loss_l1(self, out, rgb_target, depth_target, stream=None):

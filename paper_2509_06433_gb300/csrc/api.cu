@@ -202,7 +202,15 @@ gs_status_t gs_raster_fwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, flo
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
-  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, static_cast<cudaStream_t>(stream)));
+  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, false, static_cast<cudaStream_t>(stream)));
+}
+
+gs_status_t gs_raster_fwd_stats(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                                float* T_final, int32_t* last, void* stream) {
+  Layout L;
+  gs_status_t st = check(cfg, ws, ws_bytes, &L);
+  if (st != GS_OK) return st;
+  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, true, static_cast<cudaStream_t>(stream)));
 }
 
 gs_status_t gs_loss_l1(const gs_config_t* cfg, const float* rgb, const float* depth, const float* rgb_target,

@@ -182,7 +182,7 @@ cudaError_t launch_item_sort(const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s);
 
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
-                              cudaStream_t s);
+                              bool stats, cudaStream_t s);
 cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const float* depth, const float* T_final,
                               const int32_t* last, const float* dL_drgb, const float* dL_ddepth, const float* dL_dT,
                               cudaStream_t s);

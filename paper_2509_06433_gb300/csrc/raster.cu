@@ -130,7 +130,14 @@ __device__ __forceinline__ TileCoord tile_coord(const Layout& L, int64_t tile_g)
 }
 
 // ============================================================================ forward
-template <int PX>
+// Per pixel, amin is the opacity a splat must reach to be kept: 1/255 while the pixel is
+// open, +inf once it has stopped (or lies outside the image), so a stopped pixel skips every
+// later splat without a separate flag. A kept splat that does not stop the pixel is blended
+// through ae = alpha (else ae = 0): w = ae T and T <- T - ae T leave every accumulator bit for
+// bit unchanged when ae = 0, so the blend needs no selects. STATS = true also counts the
+// evaluations (list entries examined, including the one that stops a pixel) and the blended
+// ones; the decisions and outputs are the same.
+template <int PX, bool STATS>
 __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
                                                                  float* __restrict__ out_rgb,
                                                                  float* __restrict__ out_depth,
@@ -141,6 +148,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
   pdl_begin();
   constexpr int kThreads = kTilePixels / PX;
   constexpr int kWarps = kThreads / 32;
+  const float kInf = __int_as_float(0x7f800000);
   __shared__ Stage<kFwdChunk> S;
   __shared__ uint32_t s_red[2][kWarps];
   const TileCoord tc = tile_coord(L, blockIdx.x);
@@ -152,9 +160,8 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
   // this warp's pixel rows: (2 * warp) * PX .. (2 * warp + 2) * PX - 1
   const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
-  float T[PX], cr[PX], cg[PX], cb[PX], cd[PX];
+  float T[PX], cr[PX], cg[PX], cb[PX], cd[PX], amin[PX];
   int32_t last[PX], stop_at[PX];
-  bool done[PX];
   uint32_t blended = 0;
   bool all_done = true;
 #pragma unroll
@@ -163,8 +170,9 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
     cr[q] = cg[q] = cb[q] = cd[q] = 0.0f;
     last[q] = 0;
     stop_at[q] = -1;
-    done[q] = !(px < L.W && py + q < L.H);
-    all_done = all_done && done[q];
+    const bool outside = !(px < L.W && py + q < L.H);
+    amin[q] = outside ? kInf : kAlphaMin;
+    all_done = all_done && outside;
   }
   for (uint32_t base = rg.x; base < rg.y; base += kFwdChunk) {
     if (__syncthreads_count(!all_done) == 0) break;
@@ -176,33 +184,41 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
     const int n = min(kFwdChunk, static_cast<int>(rg.y - base));
     const int pos0 = static_cast<int>(base - rg.x);
     for (int j = 0; j < n; ++j) {
-      if (__all_sync(0xffffffffu, all_done)) break;
+      if ((j & 7) == 0) {  // warp-uniform early exit, checked every 8 splats (extra ones are no-ops)
+        all_done = true;
+#pragma unroll
+        for (int q = 0; q < PX; ++q) all_done = all_done && (amin[q] == kInf);
+        if (__all_sync(0xffffffffu, all_done)) break;
+      }
       if (!(S.rows[j] & wrows)) continue;
       const float4 A = S.A[j], B = S.B[j], C = S.C[j];
       const float dx = __fsub_rn(A.x, pxc);
       const float qadx = __fmul_rn(A.z, dx);
       const int pos = pos0 + j;
-      all_done = true;
 #pragma unroll
       for (int q = 0; q < PX; ++q) {
         // pixel-centre offsets are formed the same way whatever PX is, so every variant
         // takes bit-identical decisions
-        const Alpha a = splat_alpha(A, B, qadx, dx, __fsub_rn(A.y, pyc + static_cast<float>(q)));
-        const bool ok = a.keep && !done[q];
-        const float Tn = __fmaf_rn(-T[q], a.alpha, T[q]);
-        const bool stop = ok && (Tn < kTStop);
-        const bool blend = ok && !stop;
-        const float w = blend ? __fmul_rn(a.alpha, T[q]) : 0.0f;
+        const float dy = __fsub_rn(A.y, pyc + static_cast<float>(q));
+        const float p = __fmaf_rn(dx, __fmaf_rn(A.w, dy, qadx), __fmul_rn(__fmul_rn(B.x, dy), dy));
+        const float alpha = fminf(__fmul_rn(B.y, ex2_approx(p)), kAlphaMax);
+        const bool keep = (p <= 0.0f) && (alpha >= amin[q]);
+        const float Tn = __fmaf_rn(-T[q], alpha, T[q]);
+        const bool stop = keep && (Tn < kTStop);
+        const bool blend = keep && !stop;
+        const float ae = blend ? alpha : 0.0f;
+        const float w = __fmul_rn(ae, T[q]);
         cr[q] = __fmaf_rn(C.x, w, cr[q]);
         cg[q] = __fmaf_rn(C.y, w, cg[q]);
         cb[q] = __fmaf_rn(C.z, w, cb[q]);
         cd[q] = __fmaf_rn(B.z, w, cd[q]);
-        T[q] = blend ? Tn : T[q];
+        T[q] = __fmaf_rn(-T[q], ae, T[q]);
         last[q] = blend ? pos + 1 : last[q];
-        stop_at[q] = stop ? pos : stop_at[q];
-        blended += blend ? 1u : 0u;
-        done[q] = done[q] || stop;
-        all_done = all_done && done[q];
+        amin[q] = stop ? kInf : amin[q];
+        if (STATS) {
+          stop_at[q] = stop ? pos : stop_at[q];
+          blended += blend ? 1u : 0u;
+        }
       }
     }
   }
@@ -213,7 +229,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
   for (int q = 0; q < PX; ++q) {
     const int y = py + q;
     if (px < L.W && y < L.H) {
-      evals += static_cast<uint32_t>(stop_at[q] >= 0 ? stop_at[q] + 1 : len);
+      if (STATS) evals += static_cast<uint32_t>(stop_at[q] >= 0 ? stop_at[q] + 1 : len);
       const int64_t pix = static_cast<int64_t>(y) * L.W + px;
       if (out_rgb) {
         out_rgb[(static_cast<int64_t>(tc.k) * 3 + 0) * HW + pix] = cr[q];
@@ -225,25 +241,27 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
       if (out_last) out_last[tc.k * HW + pix] = last[q];
     }
   }
-  uint32_t e = evals, c = blended;
+  if (STATS) {
+    uint32_t e = evals, c = blended;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_xor_sync(0xffffffffu, e, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s_red[0][threadIdx.x >> 5] = e;
-    s_red[1][threadIdx.x >> 5] = c;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t te = 0, tcn = 0;
-    for (int w = 0; w < kWarps; ++w) {
-      te += s_red[0][w];
-      tcn += s_red[1][w];
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
     }
-    if (te) atomicAdd(reinterpret_cast<unsigned long long*>(evals_out), static_cast<unsigned long long>(te));
-    if (tcn) atomicAdd(reinterpret_cast<unsigned long long*>(blended_out), static_cast<unsigned long long>(tcn));
+    if ((threadIdx.x & 31) == 0) {
+      s_red[0][threadIdx.x >> 5] = e;
+      s_red[1][threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t te = 0, tcn = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        te += s_red[0][w];
+        tcn += s_red[1][w];
+      }
+      if (te) atomicAdd(reinterpret_cast<unsigned long long*>(evals_out), static_cast<unsigned long long>(te));
+      if (tcn) atomicAdd(reinterpret_cast<unsigned long long*>(blended_out), static_cast<unsigned long long>(tcn));
+    }
   }
 }
 
@@ -401,25 +419,26 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
       float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f, cz = 0.0f, cr = 0.0f, cgr = 0.0f, cb = 0.0f;
 #pragma unroll
       for (int q = 0; q < PX; ++q) {
+        // aok = alpha for a kept splat, else 0: then w = 0 and Sg, T stay bit for bit unchanged
         const bool ok = okq[q];
         const bool open = ok && !(a[q].raw > kAlphaMax);  // the 0.99 clamp passes no gradient
         const float Tq = T[q];
-        const float w = __fmul_rn(a[q].alpha, Tq);
+        const float aok = ok ? a[q].alpha : 0.0f;
+        const float w = __fmul_rn(aok, Tq);
         const float cgz = C.x * gr[q] + C.y * gg[q] + C.z * gb[q] + B.z * gd[q];
-        const float sg = Sg[q] - cgz * w;  // colour/depth behind this splat, weighted by dL/dpixel
+        const float sg = __fmaf_rn(-cgz, w, Sg[q]);  // colour/depth behind this splat, weighted by dL/dpixel
         const float dalpha = Tq * cgz - __fdividef(sg + hT[q], 1.0f - a[q].alpha);
-        const float wm = ok ? w : 0.0f;
-        const float dpow = open ? a[q].alpha * dalpha : 0.0f;
+        const float dpow = (open ? a[q].alpha : 0.0f) * dalpha;
         const float ydp = dy[q] * dpow;
         P0 += dpow;
         P1 += ydp;
         P2 = fmaf(dy[q], ydp, P2);
-        cz = fmaf(wm, gd[q], cz);
-        cr = fmaf(wm, gr[q], cr);
-        cgr = fmaf(wm, gg[q], cgr);
-        cb = fmaf(wm, gb[q], cb);
-        Sg[q] = ok ? sg : Sg[q];
-        T[q] = ok ? __fmaf_rn(-Tq, a[q].alpha, Tq) : Tq;
+        cz = fmaf(w, gd[q], cz);
+        cr = fmaf(w, gr[q], cr);
+        cgr = fmaf(w, gg[q], cgr);
+        cb = fmaf(w, gb[q], cb);
+        Sg[q] = sg;
+        T[q] = __fmaf_rn(-Tq, aok, Tq);
       }
       const float dxP0 = dx * P0;
       const float v[10] = {dxP0, P1, dx * dxP0, dx * P1, P2, cz, P0, cr, cgr, cb};
@@ -464,17 +483,29 @@ int pick_px(int requested, int fallback) { return (requested == 1 || requested =
 }  // namespace
 
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
-                              cudaStream_t s) {
+                              bool stats, cudaStream_t s) {
   Status* st = at<Status>(ws, L.status);
-  cudaMemsetAsync(&st->evals, 0, sizeof(uint64_t), s);
-  cudaMemsetAsync(&st->composited, 0, sizeof(uint64_t), s);
+  if (stats) {
+    cudaMemsetAsync(&st->evals, 0, sizeof(uint64_t), s);
+    cudaMemsetAsync(&st->composited, 0, sizeof(uint64_t), s);
+  }
   if (L.n_tiles == 0) return cudaGetLastError();
   const unsigned grid = static_cast<unsigned>(L.n_tiles);
   const uint8_t* w = static_cast<const uint8_t*>(ws);
-  switch (pick_px(L.fwd_px, kDefaultFwdPx)) {
-    case 1: launch(k_raster_fwd<1>, grid, kTilePixels, 0, s, L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
-    case 2: launch(k_raster_fwd<2>, grid, kTilePixels / 2, 0, s, L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
-    default: launch(k_raster_fwd<4>, grid, kTilePixels / 4, 0, s, L, w, rgb, depth, T_final, last, &st->evals, &st->composited); break;
+  uint64_t *ev = &st->evals, *cp = &st->composited;
+  const int px = pick_px(L.fwd_px, kDefaultFwdPx);
+  if (stats) {
+    switch (px) {
+      case 1: launch(k_raster_fwd<1, true>, grid, kTilePixels, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
+      case 2: launch(k_raster_fwd<2, true>, grid, kTilePixels / 2, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
+      default: launch(k_raster_fwd<4, true>, grid, kTilePixels / 4, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
+    }
+  } else {
+    switch (px) {
+      case 1: launch(k_raster_fwd<1, false>, grid, kTilePixels, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
+      case 2: launch(k_raster_fwd<2, false>, grid, kTilePixels / 2, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
+      default: launch(k_raster_fwd<4, false>, grid, kTilePixels / 4, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
+    }
   }
   return cudaGetLastError();
 }

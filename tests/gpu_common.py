@@ -31,7 +31,7 @@ def gpu_render(params, cams, W, H, cap=None, dtype=None, means_dtype=None):
     ct = cams_tensor(cams)
     r = api.Rasterizer(W, H, ct.shape[0], g.N, pair_capacity=cap)
     r.plan(g, ct)
-    out = r.render(g, ct)
+    out = r.render(g, ct, stats=True)
     torch.cuda.synchronize()
     return r, g, ct, out
 

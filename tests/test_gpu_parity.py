@@ -313,6 +313,25 @@ def test_pixels_per_thread_variants_agree(name):
     r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0
 
 
+def test_counting_forward_equals_plain_forward():
+    """gs_raster_fwd_stats takes the same decisions and writes the same outputs as
+    gs_raster_fwd (bit for bit); only it updates the evaluation counters."""
+    torch, api = torch_mods()
+    s = scene("map100k")
+    r, g, ct, ref, d = gpu_fwd("map100k")
+    for px in (1, 2, 4):
+        r.cfg.fwd_px_per_thread = px
+        a, b = r.new_outputs(), r.new_outputs()
+        api.gs_raster_fwd(r.cfg, r.ws, a["rgb"], a["depth"], a["T"], a["last"])
+        api.gs_raster_fwd_stats(r.cfg, r.ws, b["rgb"], b["depth"], b["T"], b["last"])
+        torch.cuda.synchronize()
+        for k in a:
+            assert torch.equal(a[k], b[k]), (px, k)
+            assert torch.equal(a[k], ref[k]), (px, k)
+        assert r.status()[3] == d["evals"]
+    r.cfg.fwd_px_per_thread = 0
+
+
 def test_autotuner_picks_a_variant():
     torch, api = torch_mods()
     from paper_2509_06433_gb300 import autotune

@@ -132,10 +132,13 @@ typedef struct {
   size_t vals_sorted;    /* u32 [pair_capacity]: emission index of each sorted pair (pairs of an
                             item occupy [pair offset, pair offset + tiles emitted)) */
   size_t ranges;         /* u32 [K*Tx*Ty][2]: [start, end) of each global tile */
-  size_t pair_grads;     /* float [pair_capacity][12]: per-pair gradients of gs_raster_bwd */
+  size_t pair_grads;     /* float [pair_capacity][12]: per-pair gradients of gs_raster_bwd, valid
+                            where the pair's bit in pair_valid is set (other pairs: zero) */
   int32_t sort_passes;   /* 8-bit LSD passes of the pair sort over the tile bits: ceil(ceil(log2(K*Tx*Ty)) / 8) */
   int32_t tiles_x, tiles_y;
   int32_t bin_sort_launches; /* kernels one gs_bin_sort launches */
+  size_t pair_valid;     /* u32 [ceil(pair_capacity / 32)]: bit (slot & 31) of word slot / 32 is set
+                            when gs_raster_bwd wrote the record of the pair with that slot */
 } gs_ws_layout_t;
 
 /* ---------------------------------------------------------------- sizing / status */

@@ -51,7 +51,8 @@ class GsWsLayout(ctypes.Structure):
                 ("proj_tiles", c_size_t), ("proj_depth_key", c_size_t), ("proj_radius", c_size_t),
                 ("color_opacity", c_size_t), ("keys_sorted", c_size_t), ("vals_sorted", c_size_t),
                 ("ranges", c_size_t), ("pair_grads", c_size_t), ("sort_passes", c_int32), ("tiles_x", c_int32),
-                ("tiles_y", c_int32), ("bin_sort_launches", c_int32)]
+                ("tiles_y", c_int32), ("bin_sort_launches", c_int32),
+                ("pair_valid", c_size_t)]
 
 
 class GsError(RuntimeError):

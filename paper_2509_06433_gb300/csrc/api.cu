@@ -66,6 +66,7 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->proj_ell = take(KN * sizeof(Ellipse));
   L->proj_rows = take(KN * 8);
   L->row_table = take(cap * 8);
+  L->pair_valid = take((cap + 31) / 32 * 4);
   L->color_opacity = take(N * 16);
   L->block_sums = take(static_cast<size_t>(L->n_proj_blocks) * 4);
   L->block_offsets = take(static_cast<size_t>(L->n_proj_blocks) * 8);
@@ -144,6 +145,7 @@ gs_status_t gs_workspace_layout(const gs_config_t* cfg, gs_ws_layout_t* out) {
   out->vals_sorted = L.vals[L.passes & 1];
   out->ranges = L.ranges;
   out->pair_grads = L.pair_grads;
+  out->pair_valid = L.pair_valid;
   out->sort_passes = L.passes;
   out->bin_sort_launches = bin_sort_launch_count(L);
   out->tiles_x = L.Tx;

@@ -221,6 +221,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
     for (int p = 0; p < L.passes; ++p)
       for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kEmitThreads + threadIdx.x; i < used; i += gsize)
         sstat[static_cast<uint64_t>(p) * L.max_sort_tiles * 256 + i] = 0;
+    // and the per-pair record bits of the backward pass
+    uint32_t* valid = at<uint32_t>(ws, L.pair_valid);
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kEmitThreads + threadIdx.x; i < (n + 31) / 32; i += gsize)
+      valid[i] = 0;
   }
   const uint64_t start = static_cast<uint64_t>(blockIdx.x) * kEmitPairs;
   if (start >= n) return;

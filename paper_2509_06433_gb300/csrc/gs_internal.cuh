@@ -67,6 +67,10 @@ struct Layout {
   // (first entry, number of entries). Entries are handed out by an atomic counter; at most
   // pair_capacity of them (more is reported as a pair overflow).
   size_t row_table, proj_rows;
+  // one bit per pair slot: set by gs_raster_bwd for every record it writes (pairs in front of
+  // every pixel's last contributor of their tile); the other records are never written, their
+  // gradient is zero. Cleared by the emission.
+  size_t pair_valid;
   // per view a (Ty+1) x (Tx+1) grid: +1 / -1 at the first / one-past-last tile of every
   // emitted row span; its row-wise prefix sum is the number of pairs of each tile
   size_t tile_diff;

@@ -19,20 +19,58 @@ struct Sum10 {
   float v[10];
 };
 
-// Sums records [off, off + cnt) clipped to the workspace capacity (pairs past the capacity
-// were never emitted when the pair count overflowed; the error word reports that case).
-__device__ __forceinline__ Sum10 sum_pairs(const float* __restrict__ pg, uint32_t off, uint32_t cnt, int64_t cap) {
+// Sums the records of slots [off, off + cnt) whose bit is set in `valid` (the others were
+// not written: zero gradient), in increasing slot order, clipped to the workspace capacity
+// (pairs past the capacity were never emitted when the pair count overflowed; the error word
+// reports that case).
+__device__ __forceinline__ void add_record(float (&v)[10], const float* __restrict__ pg, uint32_t slot) {
+  const float4* r = reinterpret_cast<const float4*>(pg + static_cast<size_t>(slot) * kPairGradStride);
+  const float4 a = r[0], b = r[1], c = r[2];
+  v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w;
+  v[4] += b.x; v[5] += b.y; v[6] += b.z; v[7] += b.w;
+  v[8] += c.x; v[9] += c.y;
+}
+
+__device__ __forceinline__ void clip(uint32_t off, uint32_t& cnt, int64_t cap) {
   if (static_cast<int64_t>(off) >= cap) cnt = 0;
   else if (static_cast<int64_t>(off) + cnt > cap) cnt = static_cast<uint32_t>(cap - off);
+}
+
+__device__ __forceinline__ Sum10 sum_pairs(const float* __restrict__ pg, const uint32_t* __restrict__ valid,
+                                           uint32_t off, uint32_t cnt, int64_t cap) {
+  clip(off, cnt, cap);
   Sum10 s;
 #pragma unroll
   for (int i = 0; i < 10; ++i) s.v[i] = 0.0f;
-  for (uint32_t j = 0; j < cnt; ++j) {
-    const float4* r = reinterpret_cast<const float4*>(pg + static_cast<size_t>(off + j) * kPairGradStride);
-    const float4 a = r[0], b = r[1], c = r[2];
-    s.v[0] += a.x; s.v[1] += a.y; s.v[2] += a.z; s.v[3] += a.w;
-    s.v[4] += b.x; s.v[5] += b.y; s.v[6] += b.z; s.v[7] += b.w;
-    s.v[8] += c.x; s.v[9] += c.y;
+  // groups of 4 slots: the marked records' loads are independent (predicated), so they are in
+  // flight together; unmarked slots load nothing
+  uint32_t wi = 0xffffffffu, word = 0;
+  for (uint32_t j = 0; j < cnt; j += 4) {
+    float4 a[4], b[4], c[4];
+    bool on[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t slot = off + j + q;
+      if ((slot >> 5) != wi) {
+        wi = slot >> 5;
+        word = valid[wi];
+      }
+      on[q] = (j + q < cnt) && ((word >> (slot & 31)) & 1u);
+      a[q] = b[q] = c[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (on[q]) {
+        const float4* r = reinterpret_cast<const float4*>(pg + static_cast<size_t>(slot) * kPairGradStride);
+        a[q] = r[0];
+        b[q] = r[1];
+        c[q] = r[2];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!on[q]) continue;
+      s.v[0] += a[q].x; s.v[1] += a[q].y; s.v[2] += a[q].z; s.v[3] += a[q].w;
+      s.v[4] += b[q].x; s.v[5] += b[q].y; s.v[6] += b[q].z; s.v[7] += b[q].w;
+      s.v[8] += c[q].x; s.v[9] += c[q].y;
+    }
   }
   return s;
 }
@@ -41,29 +79,25 @@ __device__ __forceinline__ Sum10 sum_pairs(const float* __restrict__ pg, uint32_
 // by the whole warp (lane-strided partial sums, then a fixed butterfly), the others sum
 // their own serially. Every lane of the warp must call it. Deterministic.
 constexpr uint32_t kCoopPairs = 32;
-__device__ __forceinline__ Sum10 sum_pairs_warp(const float* __restrict__ pg, uint32_t off, uint32_t cnt,
-                                                int64_t cap, bool active) {
+__device__ __forceinline__ Sum10 sum_pairs_warp(const float* __restrict__ pg, const uint32_t* __restrict__ valid,
+                                                uint32_t off, uint32_t cnt, int64_t cap, bool active) {
   const int lane = threadIdx.x & 31;
   if (!active) cnt = 0;
   const bool big = cnt > kCoopPairs;
-  Sum10 mine = sum_pairs(pg, off, big ? 0u : cnt, cap);
+  Sum10 mine = sum_pairs(pg, valid, off, big ? 0u : cnt, cap);
   uint32_t pending = __ballot_sync(0xffffffffu, big);
   while (pending) {
     const int src = __ffs(pending) - 1;
     pending &= pending - 1;
     const uint32_t o = __shfl_sync(0xffffffffu, off, src);
     uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
-    if (static_cast<int64_t>(o) >= cap) c = 0;
-    else if (static_cast<int64_t>(o) + c > cap) c = static_cast<uint32_t>(cap - o);
+    clip(o, c, cap);
     Sum10 part;
 #pragma unroll
     for (int i = 0; i < 10; ++i) part.v[i] = 0.0f;
     for (uint32_t j = lane; j < c; j += 32) {
-      const float4* r = reinterpret_cast<const float4*>(pg + static_cast<size_t>(o + j) * kPairGradStride);
-      const float4 a = r[0], b = r[1], d = r[2];
-      part.v[0] += a.x; part.v[1] += a.y; part.v[2] += a.z; part.v[3] += a.w;
-      part.v[4] += b.x; part.v[5] += b.y; part.v[6] += b.z; part.v[7] += b.w;
-      part.v[8] += d.x; part.v[9] += d.y;
+      const uint32_t slot = o + j;
+      if ((valid[slot >> 5] >> (slot & 31)) & 1u) add_record(part.v, pg, slot);
     }
 #pragma unroll
     for (int i = 0; i < 10; ++i)
@@ -82,6 +116,7 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
   const bool valid = g < L.N;
   const int4* tiles = at<int4>(ws, L.proj_tiles);
   const float* pg = at<float>(ws, L.pair_grads);
+  const uint32_t* pvalid = at<uint32_t>(ws, L.pair_valid);
   __shared__ float s_red[kPoseBlock / 32][6];
 
   float p[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, lg = 0.0f;
@@ -112,7 +147,8 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
     float pose[6] = {0, 0, 0, 0, 0, 0};
     int4 tl = make_int4(0, 0, 0, 0);
     if (valid) tl = tiles[static_cast<int64_t>(k) * L.N + g];
-    const Sum10 s = sum_pairs_warp(pg, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
+    const Sum10 s =
+        sum_pairs_warp(pg, pvalid, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
     if (tl.w > 0) {
       const float gu = s.v[0], gv = s.v[1], gA = s.v[2], gB = s.v[3], gC = s.v[4], gz = s.v[5];
       d_op += s.v[6];
@@ -279,12 +315,14 @@ __global__ void __launch_bounds__(kPoseBlock) k_screen_grads(Layout L, const uin
   const bool valid = g < L.N;  // no early return: the pair sums are warp-cooperative
   const int4* tiles = at<int4>(ws, L.proj_tiles);
   const float* pg = at<float>(ws, L.pair_grads);
+  const uint32_t* pvalid = at<uint32_t>(ws, L.pair_valid);
   float op = 0.0f, c[3] = {0, 0, 0};
   for (int k = 0; k < L.K; ++k) {
     const int64_t kg = static_cast<int64_t>(k) * L.N + g;
     int4 tl = make_int4(0, 0, 0, 0);
     if (valid) tl = tiles[kg];
-    const Sum10 s = sum_pairs_warp(pg, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
+    const Sum10 s =
+        sum_pairs_warp(pg, pvalid, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
     if (!valid) continue;
     if (d_mean2d) {
       d_mean2d[2 * kg] = s.v[0];

@@ -15,8 +15,9 @@
 // The backward pass sums each splat's 10 gradient sums over a warp's pixels (PX per lane,
 // then a 12-shuffle warp reduction), writes one partial per warp into shared memory, and at
 // the end of each chunk sums the warp partials in a fixed order into one record per
-// (splat, tile) pair of the pair-gradient buffer. No global atomics: the gradients are
-// deterministic.
+// (splat, tile) pair of the pair-gradient buffer, marking the pair in a bit mask; pairs
+// behind every pixel's last contributor of their tile get no record (their gradient is
+// zero). No floating-point atomics: the gradients are deterministic.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
   const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
   float* pair_grads = at<float>(ws, L.pair_grads);
+  uint32_t* pair_valid = at<uint32_t>(ws, L.pair_valid);
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
 
   float T[PX], Sg[PX], hT[PX], gr[PX], gg[PX], gb[PX], gd[PX];
@@ -460,22 +462,16 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
       const float du = kLn2 * (2.0f * A.z * R[0] + A.w * R[1]);
       const float dv = kLn2 * (2.0f * B.x * R[1] + A.w * R[0]);
       const float dop = R[6] != 0.0f ? R[6] / B.y : 0.0f;
-      float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(s_slot[jj]) * kPairGradStride);
+      const uint32_t slot = s_slot[jj];
+      float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(slot) * kPairGradStride);
       dst[0] = make_float4(du, dv, -0.5f * R[2], -R[3]);
       dst[1] = make_float4(-0.5f * R[4], R[5], dop, R[7]);
       dst[2] = make_float4(R[8], R[9], 0.0f, 0.0f);
+      atomicOr(&pair_valid[slot >> 5], 1u << (slot & 31));
     }
     __syncthreads();
   }
-  // pairs behind every pixel's last contributor receive zero records
-  for (uint32_t i = stop + threadIdx.x; i < rg.y; i += kThreads) {
-    const uint32_t slot = slots[i];
-    float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(slot) * kPairGradStride);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    dst[0] = zero;
-    dst[1] = zero;
-    dst[2] = zero;
-  }
+  // pairs behind every pixel's last contributor get no record: their bit stays clear
 }
 
 int pick_px(int requested, int fallback) { return (requested == 1 || requested == 2 || requested == 4) ? requested : fallback; }

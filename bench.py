@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the tracking and mapping-window fields")
+    ap.add_argument("--px", default=None,
+                    help="pixels per thread of the forward and backward compositing kernels, e.g. 2,4 "
+                         "(default: autotuned on the workload)")
     return ap.parse_args()
 
 
@@ -137,7 +140,12 @@ def run_ours(args, rank, world):
     rgb_t, depth_t = tgt["rgb"].clone(), tgt["depth"].clone()
     r.plan(g, cams)
     from paper_2509_06433_gb300 import autotune
-    tuned = autotune.tune(r, g, cams)
+    if args.px:
+        fpx, bpx = (int(x) for x in args.px.split(","))
+        r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = fpx, bpx
+        tuned = {"fwd": None, "bwd": None, "choice": (fpx, bpx)}
+    else:
+        tuned = autotune.tune(r, g, cams)
     out = r.new_outputs()
     g_rgb = torch.empty_like(out["rgb"])
     g_depth = torch.empty_like(out["depth"])
@@ -515,6 +523,22 @@ FLOP_FWD_BLEND = 11.0
 FLOP_BWD_BLEND = 44.0
 
 
+def measured_traffic(stage):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, or None when the
+    kernel's source has changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_map100k.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) == 4 and not line.startswith("#") and f[0] == stage:
+            src = os.path.join(ROOT, f[1])
+            if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == f[2]:
+                return int(f[3])
+    return None
+
+
 def roofline(stage, ms_list, counts, pairs, s, r):
     import torch
     peaks, src = load_peaks()
@@ -529,7 +553,7 @@ def roofline(stage, ms_list, counts, pairs, s, r):
         else:
             flop = FLOP_EVAL * counts["evals_bwd"] + FLOP_BWD_BLEND * counts["blended"]
         return {"kernel": stage, "bound": "alu", "achieved": flop / t / 1e12, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": flop / t / 1e12 / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": flop / t / 1e12 / fp32_peak_tflops, "traffic": measured_traffic(stage),
                 "peak_source": f"FP32 = {sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz (max clock; {src} peaks file)"}
     # HBM-bound stages: algorithmic bytes
     passes = r.layout.sort_passes
@@ -540,7 +564,7 @@ def roofline(stage, ms_list, counts, pairs, s, r):
               "project_bwd": N * 56 + pairs * 48 + N * 56}.get(stage, 0)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     return {"kernel": stage, "bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": bytes_ / t / 1e9 / hbm, "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+            "frac": bytes_ / t / 1e9 / hbm, "traffic": measured_traffic(stage), "peak_source": f"hbm_gbs ({src})"}
 
 
 # ----------------------------------------------------------------------------- oracle (CPU)

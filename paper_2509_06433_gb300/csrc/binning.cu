@@ -5,7 +5,7 @@
 //   k_item_offsets    per item (depth order): first pair index, rectangle, ids
 //   k_tile_prefix     row-wise prefix sum of each view's span grid = pairs per tile
 //   k_tile_scan       tile ranges [start, end) and the digit histograms of the pair sort
-//   k_emit_pairs      one (key, value) pair per emitted (view, Gaussian, tile), 2048 pairs per block
+//   k_emit_pairs      one (key, value) pair per emitted (view, Gaussian, tile), 1024 pairs per block
 //
 // An item emits, row by row through its tile rectangle, the tiles of each row's span that
 // its widened alpha >= 1/255 ellipse meets (row_span).
@@ -206,11 +206,22 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* _
   for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) hist[i] = s_hist[i];
 }
 
-// Pairs [b * kEmitPairs, (b + 1) * kEmitPairs) of the emission order. Each pair finds its
-// item by binary search over the items' pair offsets, staged for the block's window.
+// Pairs [b * kEmitPairs, (b + 1) * kEmitPairs) of the emission order. The block stages its
+// window of items (pair offsets, row-table ranges, view and Gaussian ids) and, when they fit,
+// the window items' row-span entries in shared memory; each pair then finds its item and its
+// row by binary searches in shared memory.
+constexpr int kEmitRows = 1024;  // row-span entries staged per block (else read from the table)
+
 __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* __restrict__ ws) {
   pdl_begin();
+  constexpr int kPerThread = (kEmitPairs + 1 + kEmitThreads - 1) / kEmitThreads;  // items per thread in the scan
   __shared__ uint32_t s_off[kEmitPairs + 2];
+  __shared__ uint32_t s_rt[kEmitPairs + 1];    // first row-table entry of each window item
+  __shared__ uint32_t s_nk[kEmitPairs + 1];    // entries | view << 16
+  __shared__ uint32_t s_g[kEmitPairs + 1];     // Gaussian id
+  __shared__ uint32_t s_rbase[kEmitPairs + 1];  // first staged entry of each window item
+  __shared__ int2 s_rows[kEmitRows];
+  __shared__ uint32_t s_warp[kEmitThreads / 32];
   __shared__ int64_t s_lo, s_hi;
   const uint64_t n = at<Status>(ws, L.status)->num_pairs;
   // clear the pair sort's look-back status (grid-stride over the tiles in use)
@@ -242,12 +253,63 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
   }
   __syncthreads();
   const int64_t lo = s_lo;
-  const int win = static_cast<int>(s_hi - lo + 1);  // <= kEmitPairs: every emitting item has a pair here
-  for (int i = threadIdx.x; i <= win; i += kEmitThreads) s_off[i] = offsets[lo + i];
-  __syncthreads();
+  // every item of the window emits (items that emit nothing sort last), so win <= kEmitPairs
+  const int win = static_cast<int>(s_hi - lo + 1);
   const int4* rects = at<int4>(ws, L.item_rect);
   const uint2* kgs = at<uint2>(ws, L.item_kg);
   const int2* rowtab = at<int2>(ws, L.row_table);
+  for (int i = threadIdx.x; i <= win; i += kEmitThreads) s_off[i] = offsets[lo + i];
+  for (int i = threadIdx.x; i < win; i += kEmitThreads) {
+    const int4 rc = rects[lo + i];  // (first row-table entry, entries)
+    const uint2 kg = kgs[lo + i];
+    s_rt[i] = static_cast<uint32_t>(rc.x);
+    s_nk[i] = static_cast<uint32_t>(rc.y) | (kg.x << 16);
+    s_g[i] = kg.y;
+  }
+  __syncthreads();
+  // exclusive scan of the window items' entry counts (kPerThread consecutive items per thread)
+  uint32_t loc[kPerThread], sum = 0;
+#pragma unroll
+  for (int q = 0; q < kPerThread; ++q) {
+    const int i = threadIdx.x * kPerThread + q;
+    loc[q] = i < win ? (s_nk[i] & 0xffffu) : 0u;
+    sum += loc[q];
+  }
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t base = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kEmitThreads / 32; ++w) {
+      base += w < warp ? s_warp[w] : 0u;
+      total += s_warp[w];
+    }
+    base += incl - sum;
+#pragma unroll
+    for (int q = 0; q < kPerThread; ++q) {
+      const int i = threadIdx.x * kPerThread + q;
+      if (i < win) s_rbase[i] = base;
+      base += loc[q];
+    }
+    __syncthreads();
+    if (total <= static_cast<uint32_t>(kEmitRows)) {
+      for (int i = threadIdx.x; i < win; i += kEmitThreads) {
+        const uint32_t nr = s_nk[i] & 0xffffu, b = s_rbase[i], rt = s_rt[i];
+        for (uint32_t r = 0; r < nr; ++r) s_rows[b + r] = rowtab[rt + r];
+      }
+    } else if (threadIdx.x == 0) {
+      s_warp[0] = 0xffffffffu;  // marker: entries stay in global memory
+    }
+    __syncthreads();
+  }
+  const bool staged = s_warp[0] != 0xffffffffu;
   uint64_t* keys = at<uint64_t>(ws, L.keys[0]);
   uint32_t* vals = at<uint32_t>(ws, L.vals[0]);
   const uint64_t tiles_per_view = static_cast<uint64_t>(L.Tx) * L.Ty;
@@ -258,14 +320,14 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
       const int mid = (a + b) >> 1;
       if (s_off[mid] <= jj) a = mid; else b = mid;
     }
-    const int4 rc = rects[lo + a];  // (first row-table entry, entries)
-    const uint2 kg = kgs[lo + a];
+    const uint32_t nk = s_nk[a];
+    const int nrows = static_cast<int>(nk & 0xffffu);
     // the pair's tile: its row is the last entry whose earlier-row pair count is <= r
     const int r = static_cast<int>(jj - s_off[a]);
     int tx = 0, ty = 0;
-    if (rc.y > 0) {
-      const int2* tab = rowtab + rc.x;
-      int p = 0, q = rc.y;  // tab[p].x <= r, and r < tab[q].x or q = entries
+    if (nrows > 0) {
+      const int2* tab = staged ? s_rows + s_rbase[a] : rowtab + s_rt[a];
+      int p = 0, q = nrows;  // tab[p].x <= r, and r < tab[q].x or q = entries
       while (q - p > 1) {
         const int mid = (p + q) >> 1;
         if (tab[mid].x <= r) p = mid; else q = mid;
@@ -274,8 +336,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
       tx = (e.y & 0xffff) + (r - e.x);
       ty = static_cast<int>(static_cast<uint32_t>(e.y) >> 16);
     }
-    const uint64_t tid = static_cast<uint64_t>(kg.x) * tiles_per_view + static_cast<uint64_t>(ty) * L.Tx + tx;
-    keys[j] = (tid << 32) | kg.y;
+    const uint64_t tid = static_cast<uint64_t>(nk >> 16) * tiles_per_view + static_cast<uint64_t>(ty) * L.Tx + tx;
+    keys[j] = (tid << 32) | s_g[a];
     vals[j] = jj;
   }
 }

@@ -13,7 +13,7 @@ namespace gs {
 constexpr int kTile = 16;             // tile side (pixels)
 constexpr int kTilePixels = kTile * kTile;
 constexpr int kProjBlock = 256;       // (view, Gaussian) items per projection / scan block
-constexpr int kEmitPairs = 2048;      // pairs emitted per emission block
+constexpr int kEmitPairs = 1024;      // pairs emitted per emission block
 constexpr int kProjGridCells = 6144;  // largest (Tx+1)(Ty+1) difference grid kept in shared memory
 constexpr int kSortThreads = 256;     // onesweep block
 constexpr int kSortItems = 15;        // keys per thread per onesweep tile (default; 8 also built)

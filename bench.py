@@ -156,15 +156,14 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     cfg, ws = r.cfg, r.ws
     # kernels of ours per step: project; gs_bin_sort (item depth sort, counts, scan, item
-    # offsets, tile prefix, tile scan, emission, pair sort); raster fwd; loss (2); raster bwd;
-    # project bwd + pose reduction
-    n_launch = 1 + r.layout.bin_sort_launches + 1 + 2 + 1 + 2
+    # offsets, tile prefix, tile scan, emission, pair sort); raster fwd with the fused L1 loss;
+    # raster bwd; project bwd + pose reduction (gradients are stored, not accumulated: no zeroing)
+    n_launch = 1 + r.layout.bin_sort_launches + 1 + 1 + 2
 
     def zero_grads():
-        for v in grads.values():
-            v.zero_()
+        pass  # gs_project_bwd(overwrite=True) stores every gradient
 
-    stage_names = ["project", "bin_sort", "raster_fwd", "loss", "raster_bwd", "project_bwd"]
+    stage_names = ["project", "bin_sort", "raster_fwd_l1", "raster_bwd", "project_bwd"]
 
     def step(ev=None):
         def mark(i):
@@ -175,14 +174,13 @@ def run_ours(args, rank, world):
         mark(1)
         api.gs_bin_sort(cfg, ws, stream)
         mark(2)
-        api.gs_raster_fwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], stream)
+        api.gs_raster_fwd_l1(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], rgb_t, depth_t, g_rgb,
+                             g_depth, loss, stream)
         mark(3)
-        api.gs_loss_l1(cfg, out["rgb"], out["depth"], rgb_t, depth_t, g_rgb, g_depth, loss, ws, stream)
-        mark(4)
         api.gs_raster_bwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth, None, stream)
+        mark(4)
+        api.gs_project_bwd(cfg, g, cams, ws, grads, stream, overwrite=True)
         mark(5)
-        api.gs_project_bwd(cfg, g, cams, ws, grads, stream)
-        mark(6)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
@@ -206,7 +204,7 @@ def run_ours(args, rank, world):
 
     # ---- per-stage breakdown (eager launches, events between the entry points)
     n_stage = min(args.steps, 100)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(n_stage)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stage_names) + 1)] for _ in range(n_stage)]
     for i in range(n_stage):
         zero_grads()
         flush.fill_(float(i))
@@ -262,10 +260,10 @@ def run_ours(args, rank, world):
         zero_grads()
         api.gs_project(cfg, ge, cams, ws, stream)
         api.gs_bin_sort(cfg, ws, stream)
-        api.gs_raster_fwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], stream)
-        api.gs_loss_l1(cfg, out["rgb"], out["depth"], dev_tgt[0], dev_tgt[1], g_rgb, g_depth, loss, ws, stream)
+        api.gs_raster_fwd_l1(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], dev_tgt[0], dev_tgt[1], g_rgb,
+                             g_depth, loss, stream)
         api.gs_raster_bwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth, None, stream)
-        api.gs_project_bwd(cfg, ge, cams, ws, grads, stream)
+        api.gs_project_bwd(cfg, ge, cams, ws, grads, stream, overwrite=True)
         for k, v in grads.items():
             host_out[k].copy_(v, non_blocking=True)
         host_loss.copy_(loss, non_blocking=True)
@@ -428,8 +426,8 @@ def measure_window(dev, reps=10):
             pose = torch.zeros((1, 6), device=dev)
             api.gs_project(r1.cfg, g32, views[k], r1.ws)
             api.gs_bin_sort(r1.cfg, r1.ws)
-            api.gs_raster_fwd(r1.cfg, r1.ws, out["rgb"], out["depth"], out["T"], out["last"])
-            api.gs_loss_l1(r1.cfg, out["rgb"], out["depth"], tg[k][0], tg[k][1], g_rgb, g_depth, loss, r1.ws)
+            api.gs_raster_fwd_l1(r1.cfg, r1.ws, out["rgb"], out["depth"], out["T"], out["last"], tg[k][0], tg[k][1],
+                                 g_rgb, g_depth, loss)
             api.gs_raster_bwd(r1.cfg, r1.ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth)
             api.gs_project_bwd(r1.cfg, g32, views[k], r1.ws, {**grads, "pose": pose})
 
@@ -547,8 +545,8 @@ def roofline(stage, ms_list, counts, pairs, s, r):
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
     t = statistics.mean(ms_list) / 1e3
-    if stage in ("raster_fwd", "raster_bwd"):
-        if stage == "raster_fwd":
+    if stage in ("raster_fwd", "raster_fwd_l1", "raster_bwd"):
+        if stage != "raster_bwd":
             flop = FLOP_EVAL * counts["evals"] + FLOP_FWD_BLEND * counts["blended"]
         else:
             flop = FLOP_EVAL * counts["evals_bwd"] + FLOP_BWD_BLEND * counts["blended"]

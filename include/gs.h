@@ -106,7 +106,8 @@ typedef struct {
   gs_dtype_t means_dtype;
 } gs_gaussians_t;
 
-/* Gradient outputs of gs_project_bwd, FP32, accumulated (+=); any may be NULL (skipped). */
+/* Gradient outputs of gs_project_bwd, FP32, accumulated (+=) or stored (overwrite); any array
+ * may be NULL (skipped). */
 typedef struct {
   float* means;          /* [N,3] */
   float* log_scales;     /* [N,3] */
@@ -114,6 +115,8 @@ typedef struct {
   float* opacity_logits; /* [N] */
   float* rgb;            /* [N,3] */
   float* pose;           /* [K,6] (rho, phi): left perturbation T <- Exp(xi) T at xi = 0 */
+  int32_t overwrite;     /* 0: accumulate into the arrays (+=); 1: store the gradients (=), so the
+                            caller need not zero them first */
 } gs_grads_t;
 
 /* Byte offsets of the workspace sub-buffers (for inspection and tests). */
@@ -204,6 +207,14 @@ GS_API gs_status_t gs_raster_fwd(const gs_config_t* cfg, void* ws, size_t ws_byt
  * the counting costs time, so gs_raster_fwd does not count. */
 GS_API gs_status_t gs_raster_fwd_stats(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
                                 float* T_final, int32_t* last, void* stream);
+
+/* gs_raster_fwd with gs_loss_l1 fused into its epilogue: the same rgb, depth, T_final and
+ * last (bit for bit), the same dL/drgb and dL/ddepth images (bit for bit), and the loss L in
+ * d_loss[0] summed per tile then over tiles in tile order (equal to gs_loss_l1's value up to
+ * FP32 summation order). rgb and depth must not be NULL. */
+GS_API gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                             float* T_final, int32_t* last, const float* rgb_target, const float* depth_target,
+                             float* dL_drgb, float* dL_ddepth, float* d_loss, void* stream);
 
 /* Photometric loss of a mapping step: L = sum_k [ mean|R - R*| over 3HW + lambda
  * mean|D - D*| over HW ], sign(0) = 0. Writes dL/drgb [K,3,H,W], dL/ddepth [K,H,W] and

@@ -100,6 +100,12 @@ def gs_raster_fwd(cfg, ws, rgb, depth, T_final, last, stream=None):
          _s(stream))
 
 
+def gs_raster_fwd_l1(cfg, ws, rgb, depth, T_final, last, rgb_target, depth_target, dL_drgb, dL_ddepth, loss,
+                     stream=None):
+    call("gs_raster_fwd_l1", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
+         _p(rgb_target), _p(depth_target), _p(dL_drgb), _p(dL_ddepth), _p(loss), _s(stream))
+
+
 def gs_raster_fwd_stats(cfg, ws, rgb, depth, T_final, last, stream=None):
     call("gs_raster_fwd_stats", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
          _s(stream))
@@ -115,9 +121,11 @@ def gs_raster_bwd(cfg, ws, rgb, depth, T_final, last, dL_drgb, dL_ddepth, dL_dT=
          _p(dL_drgb), _p(dL_ddepth), _p(dL_dT), _s(stream))
 
 
-def gs_project_bwd(cfg, g: Gaussians, cams, ws, grads: dict, stream=None):
+def gs_project_bwd(cfg, g: Gaussians, cams, ws, grads: dict, stream=None, overwrite=False):
+    """Accumulates (+=) the gradients into ``grads`` or, with overwrite=True, stores them."""
     gs = g.struct()
-    gr = GsGrads(*(_p(grads.get(k)) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose")))
+    gr = GsGrads(*(_p(grads.get(k)) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose")),
+                 1 if overwrite else 0)
     call("gs_project_bwd", ctypes.byref(cfg), ctypes.byref(gs), _p(cams), _p(ws), ws.numel(), ctypes.byref(gr),
          _s(stream))
 

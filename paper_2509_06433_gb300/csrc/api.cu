@@ -67,6 +67,7 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->proj_rows = take(KN * 8);
   L->row_table = take(cap * 8);
   L->pair_valid = take((cap + 31) / 32 * 4);
+  L->tile_loss = take(static_cast<size_t>(L->n_tiles) * 4);
   L->color_opacity = take(N * 16);
   L->block_sums = take(static_cast<size_t>(L->n_proj_blocks) * 4);
   L->block_offsets = take(static_cast<size_t>(L->n_proj_blocks) * 8);
@@ -204,7 +205,7 @@ gs_status_t gs_raster_fwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, flo
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
-  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, false, static_cast<cudaStream_t>(stream)));
+  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, false, nullptr, static_cast<cudaStream_t>(stream)));
 }
 
 gs_status_t gs_raster_fwd_stats(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
@@ -212,7 +213,18 @@ gs_status_t gs_raster_fwd_stats(const gs_config_t* cfg, void* ws, size_t ws_byte
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
-  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, true, static_cast<cudaStream_t>(stream)));
+  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, true, nullptr, static_cast<cudaStream_t>(stream)));
+}
+
+gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                             float* T_final, int32_t* last, const float* rgb_target, const float* depth_target,
+                             float* dL_drgb, float* dL_ddepth, float* d_loss, void* stream) {
+  Layout L;
+  gs_status_t st = check(cfg, ws, ws_bytes, &L);
+  if (st != GS_OK) return st;
+  if (!rgb || !depth || !rgb_target || !depth_target || !dL_drgb || !dL_ddepth || !d_loss) return GS_ERR_INVALID_ARG;
+  const FusedLossArgs F{rgb_target, depth_target, dL_drgb, dL_ddepth, d_loss};
+  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, false, &F, static_cast<cudaStream_t>(stream)));
 }
 
 gs_status_t gs_loss_l1(const gs_config_t* cfg, const float* rgb, const float* depth, const float* rgb_target,

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* _
 constexpr int kEmitRows = 1024;  // row-span entries staged per block (else read from the table)
 
 __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* __restrict__ ws) {
-  pdl_begin();
+  pdl_wait();
   constexpr int kPerThread = (kEmitPairs + 1 + kEmitThreads - 1) / kEmitThreads;  // items per thread in the scan
   __shared__ uint32_t s_off[kEmitPairs + 2];
   __shared__ uint32_t s_rt[kEmitPairs + 1];    // first row-table entry of each window item
@@ -340,6 +340,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
     keys[j] = (tid << 32) | s_g[a];
     vals[j] = jj;
   }
+  pdl_trigger();
 }
 
 }  // namespace

@@ -34,7 +34,7 @@ struct Status {
   uint32_t tile_ctr[kMaxSortPasses];  // onesweep dynamic tile counters: [0,4) item sort, [4,8) pair sort
   uint64_t composited;      // evaluations of the last forward raster that blended a splat
   uint32_t row_ctr;         // entries of the row-span table handed out by the projection
-  uint32_t pad;
+  uint32_t loss_ctr;        // blocks of the loss-fused forward done (reset by the last one)
 };
 static_assert(sizeof(Status) <= 256, "status block");
 
@@ -71,6 +71,7 @@ struct Layout {
   // every pixel's last contributor of their tile); the other records are never written, their
   // gradient is zero. Cleared by the emission.
   size_t pair_valid;
+  size_t tile_loss;         // float [n_tiles]: per-tile loss partials of the loss-fused forward
   // per view a (Ty+1) x (Tx+1) grid: +1 / -1 at the first / one-past-last tile of every
   // emitted row span; its row-wise prefix sum is the number of pairs of each tile
   size_t tile_diff;
@@ -108,6 +109,11 @@ __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// For the long compositing kernels: wait at entry, but let the following grid launch only
+// once this block's main loop is done (pdl_trigger), so its blocks do not sit on the SMs for
+// the whole kernel.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
@@ -185,8 +191,15 @@ cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_item_sort(const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_sort_passes(const Layout& L, void* ws, cudaStream_t s);
 
+struct FusedLossArgs {
+  const float* rgb_t;
+  const float* depth_t;
+  float* g_rgb;
+  float* g_depth;
+  float* d_loss;
+};
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
-                              bool stats, cudaStream_t s);
+                              bool stats, const FusedLossArgs* loss, cudaStream_t s);
 cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const float* depth, const float* T_final,
                               const int32_t* last, const float* dL_drgb, const float* dL_ddepth, const float* dL_dT,
                               cudaStream_t s);

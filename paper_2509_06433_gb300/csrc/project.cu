@@ -107,7 +107,7 @@ __device__ __forceinline__ uint32_t pack16(int lo, int hi) {
 
 __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                        uint8_t* __restrict__ ws) {
-  pdl_begin();
+  pdl_wait();
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
   __shared__ uint32_t s_hist[4 * 256];
   // the block's rectangles are first added into a shared copy of its first view's difference
@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
   for (int p = 0; p < 4; ++p)
     for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kProjBlock + threadIdx.x; i < used; i += gsize)
       st[static_cast<uint64_t>(p) * used + i] = 0;
+  pdl_trigger();
 }
 
 }  // namespace

@@ -111,7 +111,7 @@ __device__ __forceinline__ Sum10 sum_pairs_warp(const float* __restrict__ pg, co
 __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                            const uint8_t* __restrict__ ws, gs_grads_t out,
                                                            float* __restrict__ pose_partials) {
-  pdl_begin();
+  pdl_wait();
   const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
   const bool valid = g < L.N;
   const int4* tiles = at<int4>(ws, L.proj_tiles);
@@ -284,19 +284,24 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
   const float qd = w * dqh[0] + x * dqh[1] + y * dqh[2] + z * dqh[3];
   const float qh[4] = {w, x, y, z};
   const float o = 1.0f / (1.0f + expf(-lg));
+  // accumulate (+=) or, with out.overwrite, store (=)
+  const float keep = out.overwrite ? 0.0f : 1.0f;
   if (out.means)
-    for (int j = 0; j < 3; ++j) out.means[3 * g + j] += d_mean[j];
+    for (int j = 0; j < 3; ++j) out.means[3 * g + j] = fmaf(keep, out.means[3 * g + j], d_mean[j]);
   if (out.log_scales)
-    for (int j = 0; j < 3; ++j) out.log_scales[3 * g + j] += dls[j];
+    for (int j = 0; j < 3; ++j) out.log_scales[3 * g + j] = fmaf(keep, out.log_scales[3 * g + j], dls[j]);
   if (out.quats)
-    for (int j = 0; j < 4; ++j) out.quats[4 * g + j] += (dqh[j] - qh[j] * qd) * iq;
-  if (out.opacity_logits) out.opacity_logits[g] += d_op * o * (1.0f - o);
+    for (int j = 0; j < 4; ++j)
+      out.quats[4 * g + j] = fmaf(keep, out.quats[4 * g + j], (dqh[j] - qh[j] * qd) * iq);
+  if (out.opacity_logits) out.opacity_logits[g] = fmaf(keep, out.opacity_logits[g], d_op * o * (1.0f - o));
   if (out.rgb)
-    for (int j = 0; j < 3; ++j) out.rgb[3 * g + j] += d_rgb[j];
+    for (int j = 0; j < 3; ++j) out.rgb[3 * g + j] = fmaf(keep, out.rgb[3 * g + j], d_rgb[j]);
+  pdl_trigger();
 }
 
-// pose[k][i] += sum over blocks of pose_partials[block][k][i], in block order.
-__global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_blocks, int K, float* __restrict__ pose) {
+// pose[k][i] += (or, with overwrite, =) the sum over blocks of pose_partials[block][k][i].
+__global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_blocks, int K, float* __restrict__ pose,
+                              int overwrite) {
   pdl_begin();
   const int k = blockIdx.x;
   const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -304,7 +309,7 @@ __global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_bloc
   for (int64_t b = lane; b < n_blocks; b += 32) v += partials[(b * K + k) * 6 + i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) pose[k * 6 + i] += v;
+  if (lane == 0) pose[k * 6 + i] = overwrite ? v : pose[k * 6 + i] + v;
 }
 
 __global__ void __launch_bounds__(kPoseBlock) k_screen_grads(Layout L, const uint8_t* __restrict__ ws, float* d_mean2d,
@@ -349,11 +354,14 @@ __global__ void __launch_bounds__(kPoseBlock) k_screen_grads(Layout L, const uin
 
 cudaError_t launch_project_bwd(const Layout& L, const GaussPtrs& g, const gs_camera_t* cams, void* ws,
                                const gs_grads_t& out, cudaStream_t s) {
-  if (L.N == 0) return cudaSuccess;
+  if (L.N == 0) {
+    if (out.overwrite && out.pose) cudaMemsetAsync(out.pose, 0, sizeof(float) * 6 * L.K, s);
+    return cudaGetLastError();
+  }
   float* partials = at<float>(ws, L.pose_partials);
   launch(k_project_bwd, static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s, L, g, cams, static_cast<uint8_t*>(ws),
                                                                               out, partials);
-  if (out.pose) launch(k_pose_reduce, L.K, 6 * 32, 0, s, partials, L.n_pose_blocks, L.K, out.pose);
+  if (out.pose) launch(k_pose_reduce, L.K, 6 * 32, 0, s, partials, L.n_pose_blocks, L.K, out.pose, out.overwrite);
   return cudaGetLastError();
 }
 

@@ -138,15 +138,30 @@ __device__ __forceinline__ TileCoord tile_coord(const Layout& L, int64_t tile_g)
 // bit unchanged when ae = 0, so the blend needs no selects. STATS = true also counts the
 // evaluations (list entries examined, including the one that stops a pixel) and the blended
 // ones; the decisions and outputs are the same.
-template <int PX, bool STATS>
+// L1 loss fused into the forward pass (LOSS = true): the targets, the gradient images it
+// writes, per-tile partial sums and the block counter that elects the last block to finish,
+// which sums the partials in tile order into *d_loss.
+struct FusedLoss {
+  const float* rgb_t;
+  const float* depth_t;
+  float* g_rgb;
+  float* g_depth;
+  float* partials;
+  uint32_t* counter;
+  float* d_loss;
+};
+
+__device__ __forceinline__ float sgn(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
+
+template <int PX, bool STATS, bool LOSS>
 __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
                                                                  float* __restrict__ out_rgb,
                                                                  float* __restrict__ out_depth,
                                                                  float* __restrict__ out_T,
                                                                  int32_t* __restrict__ out_last,
                                                                  uint64_t* __restrict__ evals_out,
-                                                                 uint64_t* __restrict__ blended_out) {
-  pdl_begin();
+                                                                 uint64_t* __restrict__ blended_out, FusedLoss F) {
+  pdl_wait();
   constexpr int kThreads = kTilePixels / PX;
   constexpr int kWarps = kThreads / 32;
   const float kInf = __int_as_float(0x7f800000);
@@ -223,23 +238,74 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
       }
     }
   }
+  pdl_trigger();
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
   const int len = static_cast<int>(rg.y - rg.x);
   uint32_t evals = 0;
+  float loss = 0.0f;
+  const float inv3 = 1.0f / (3.0f * static_cast<float>(HW));
+  const float invd = L.lambda_depth / static_cast<float>(HW);
 #pragma unroll
   for (int q = 0; q < PX; ++q) {
     const int y = py + q;
     if (px < L.W && y < L.H) {
       if (STATS) evals += static_cast<uint32_t>(stop_at[q] >= 0 ? stop_at[q] + 1 : len);
       const int64_t pix = static_cast<int64_t>(y) * L.W + px;
+      const int64_t c0 = static_cast<int64_t>(tc.k) * 3 * HW + pix;
       if (out_rgb) {
-        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 0) * HW + pix] = cr[q];
-        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 1) * HW + pix] = cg[q];
-        out_rgb[(static_cast<int64_t>(tc.k) * 3 + 2) * HW + pix] = cb[q];
+        out_rgb[c0] = cr[q];
+        out_rgb[c0 + HW] = cg[q];
+        out_rgb[c0 + 2 * HW] = cb[q];
       }
       if (out_depth) out_depth[tc.k * HW + pix] = cd[q];
       if (out_T) out_T[tc.k * HW + pix] = T[q];
       if (out_last) out_last[tc.k * HW + pix] = last[q];
+      if (LOSS) {
+        // L = sum_k [ mean_{3HW} |R - R*| + lambda mean_{HW} |D - D*| ], sign(0) = 0
+        const float c[3] = {cr[q], cg[q], cb[q]};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          const float d = c[ch] - F.rgb_t[c0 + ch * HW];
+          loss += fabsf(d) * inv3;
+          F.g_rgb[c0 + ch * HW] = sgn(d) * inv3;
+        }
+        const float d = cd[q] - F.depth_t[tc.k * HW + pix];
+        loss += fabsf(d) * invd;
+        F.g_depth[tc.k * HW + pix] = sgn(d) * invd;
+      }
+    }
+  }
+  if (LOSS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    __shared__ float s_loss[kWarps];
+    __shared__ bool s_last;
+    if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int w = 0; w < kWarps; ++w) t += s_loss[w];
+      F.partials[blockIdx.x] = t;
+      __threadfence();
+      s_last = atomicAdd(F.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+      // the last block sums every tile's partial in a fixed order
+      __threadfence();
+      float v = 0.0f;
+      for (uint32_t i = threadIdx.x; i < gridDim.x; i += kThreads) v += __ldcg(&F.partials[i]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < kWarps; ++w) t += s_loss[w];
+        F.d_loss[0] = t;
+        *F.counter = 0;
+      }
     }
   }
   if (STATS) {
@@ -328,7 +394,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
                                                                  const float* __restrict__ g_rgb,
                                                                  const float* __restrict__ g_depth,
                                                                  const float* __restrict__ g_T) {
-  pdl_begin();
+  pdl_wait();
   constexpr int kThreads = kTilePixels / PX;
   constexpr int kWarps = kThreads / 32;
   __shared__ Stage<kBwdChunk> S;
@@ -472,6 +538,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
     __syncthreads();
   }
   // pairs behind every pixel's last contributor get no record: their bit stays clear
+  pdl_trigger();
 }
 
 int pick_px(int requested, int fallback) { return (requested == 1 || requested == 2 || requested == 4) ? requested : fallback; }
@@ -479,30 +546,46 @@ int pick_px(int requested, int fallback) { return (requested == 1 || requested =
 }  // namespace
 
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
-                              bool stats, cudaStream_t s) {
+                              bool stats, const FusedLossArgs* loss, cudaStream_t s) {
   Status* st = at<Status>(ws, L.status);
   if (stats) {
     cudaMemsetAsync(&st->evals, 0, sizeof(uint64_t), s);
     cudaMemsetAsync(&st->composited, 0, sizeof(uint64_t), s);
   }
-  if (L.n_tiles == 0) return cudaGetLastError();
+  if (L.n_tiles == 0) {
+    if (loss) cudaMemsetAsync(loss->d_loss, 0, sizeof(float), s);
+    return cudaGetLastError();
+  }
   const unsigned grid = static_cast<unsigned>(L.n_tiles);
   const uint8_t* w = static_cast<const uint8_t*>(ws);
   uint64_t *ev = &st->evals, *cp = &st->composited;
+  FusedLoss F{};
+  if (loss)
+    F = FusedLoss{loss->rgb_t, loss->depth_t, loss->g_rgb, loss->g_depth, at<float>(ws, L.tile_loss), &st->loss_ctr,
+                  loss->d_loss};
   const int px = pick_px(L.fwd_px, kDefaultFwdPx);
-  if (stats) {
+#define GS_FWD(P, ST, LO) \
+  launch(k_raster_fwd<P, ST, LO>, grid, kTilePixels / P, 0, s, L, w, rgb, depth, T_final, last, ev, cp, F)
+  if (loss) {
     switch (px) {
-      case 1: launch(k_raster_fwd<1, true>, grid, kTilePixels, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
-      case 2: launch(k_raster_fwd<2, true>, grid, kTilePixels / 2, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
-      default: launch(k_raster_fwd<4, true>, grid, kTilePixels / 4, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
+      case 1: GS_FWD(1, false, true); break;
+      case 2: GS_FWD(2, false, true); break;
+      default: GS_FWD(4, false, true); break;
+    }
+  } else if (stats) {
+    switch (px) {
+      case 1: GS_FWD(1, true, false); break;
+      case 2: GS_FWD(2, true, false); break;
+      default: GS_FWD(4, true, false); break;
     }
   } else {
     switch (px) {
-      case 1: launch(k_raster_fwd<1, false>, grid, kTilePixels, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
-      case 2: launch(k_raster_fwd<2, false>, grid, kTilePixels / 2, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
-      default: launch(k_raster_fwd<4, false>, grid, kTilePixels / 4, 0, s, L, w, rgb, depth, T_final, last, ev, cp); break;
+      case 1: GS_FWD(1, false, false); break;
+      case 2: GS_FWD(2, false, false); break;
+      default: GS_FWD(4, false, false); break;
     }
   }
+#undef GS_FWD
   return cudaGetLastError();
 }
 

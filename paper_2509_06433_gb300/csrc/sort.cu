@@ -112,7 +112,7 @@ __device__ __forceinline__ uint32_t look_back(const uint32_t* status, uint32_t t
 // shared memory, look back for the tile's global digit offsets, write the keys out.
 template <class KeyT, int IT>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, int pass) {
-  pdl_begin();
+  pdl_wait();
   constexpr int kTileKeys = kSortThreads * IT;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   SortSmem<KeyT, IT>& S = *reinterpret_cast<SortSmem<KeyT, IT>*>(smem_raw);
@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, in
     }
     __syncthreads();
   }
+  pdl_trigger();
 }
 
 // Digit histograms of every pass, and clearing of the look-back status of the used tiles.

@@ -81,12 +81,11 @@ class Tracker(_Captured):
         r, o = self.r, self.out
         api.gs_project(r.cfg, self.g, self.cams, r.ws)
         api.gs_bin_sort(r.cfg, r.ws)
-        api.gs_raster_fwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"])
-        api.gs_loss_l1(r.cfg, o["rgb"], o["depth"], self.rgb_obs, self.depth_obs, self.g_rgb, self.g_depth,
-                       self.loss, r.ws)
+        api.gs_raster_fwd_l1(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.rgb_obs, self.depth_obs,
+                             self.g_rgb, self.g_depth, self.loss)
         api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
-        api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, {"pose": self.pose_grad})
-        api.gs_pose_adam_step(self.cams, self.pose_grad, self.state, self.lr[0], self.lr[1])
+        api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, {"pose": self.pose_grad}, overwrite=True)
+        api.gs_pose_adam_step(self.cams, self.pose_grad, self.state, self.lr[0], self.lr[1], zero_grad=False)
 
     def reset_optimizer(self):
         self.state.zero_()
@@ -102,8 +101,9 @@ class Tracker(_Captured):
 
 
 class MappingStep(_Captured):
-    """One mapping iteration (fixed poses): render, L1 against the key-frames, backward to
-    every Gaussian parameter and the poses; gradients are zeroed at the start of the step."""
+    """One mapping iteration (fixed poses): render with the L1 loss against the key-frames fused
+    into the forward pass, backward to every Gaussian parameter and the poses; the gradients
+    are stored (not accumulated), so nothing is zeroed."""
 
     def __init__(self, r: api.Rasterizer, g: api.Gaussians, cams: torch.Tensor, rgb_t: torch.Tensor,
                  depth_t: torch.Tensor, graph=True):
@@ -122,12 +122,9 @@ class MappingStep(_Captured):
 
     def _iteration(self):
         r, o = self.r, self.out
-        for v in self.grads.values():
-            v.zero_()
         api.gs_project(r.cfg, self.g, self.cams, r.ws)
         api.gs_bin_sort(r.cfg, r.ws)
-        api.gs_raster_fwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"])
-        api.gs_loss_l1(r.cfg, o["rgb"], o["depth"], self.rgb_t, self.depth_t, self.g_rgb, self.g_depth, self.loss,
-                       r.ws)
+        api.gs_raster_fwd_l1(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.rgb_t, self.depth_t,
+                             self.g_rgb, self.g_depth, self.loss)
         api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
-        api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, self.grads)
+        api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, self.grads, overwrite=True)

@@ -380,3 +380,46 @@ def test_large_item_and_pair_counts():
     np.testing.assert_array_equal(d["vals"], L.vals)
     np.testing.assert_array_equal(d["ranges"], L.ranges)
     check_images(to_np(out), orc)
+
+
+def test_loss_fused_forward_equals_forward_then_loss():
+    """gs_raster_fwd_l1 writes the forward outputs and the loss gradient images bit for bit
+    as gs_raster_fwd followed by gs_loss_l1, and the same loss up to summation order."""
+    torch, api = torch_mods()
+    s = scene("map100k")
+    r, g, ct, ref, d = gpu_fwd("map100k")
+    rgb_t = torch.as_tensor(random_image(21, (s.K, 3, s.H, s.W))).cuda()
+    depth_t = torch.as_tensor(random_image(22, (s.K, s.H, s.W)) * 5).cuda()
+    a = r.new_outputs()
+    api.gs_raster_fwd(r.cfg, r.ws, a["rgb"], a["depth"], a["T"], a["last"])
+    ga, gda, la = torch.empty_like(a["rgb"]), torch.empty_like(a["depth"]), torch.zeros(1, device="cuda")
+    api.gs_loss_l1(r.cfg, a["rgb"], a["depth"], rgb_t, depth_t, ga, gda, la, r.ws)
+    for px in (1, 2, 4):
+        r.cfg.fwd_px_per_thread = px
+        b = r.new_outputs()
+        gb, gdb, lb = torch.empty_like(b["rgb"]), torch.empty_like(b["depth"]), torch.zeros(1, device="cuda")
+        for _ in range(2):  # twice: the block counter resets itself
+            api.gs_raster_fwd_l1(r.cfg, r.ws, b["rgb"], b["depth"], b["T"], b["last"], rgb_t, depth_t, gb, gdb, lb)
+        torch.cuda.synchronize()
+        for k in a:
+            assert torch.equal(a[k], b[k]), (px, k)
+        assert torch.equal(ga, gb) and torch.equal(gda, gdb), px
+        assert abs(la.item() - lb.item()) <= 1e-5 * abs(la.item()), (px, la.item(), lb.item())
+    r.cfg.fwd_px_per_thread = 0
+
+
+def test_overwritten_gradients_equal_zeroed_accumulated_ones():
+    torch, api = torch_mods()
+    s = scene("window_k3")
+    r, g, ct, out, d = gpu_fwd("window_k3")
+    gr, gd, gt = (torch.as_tensor(x).cuda() for x in _upstream("window_k3", s))
+    api.gs_raster_bwd(r.cfg, r.ws, out["rgb"], out["depth"], out["T"], out["last"], gr, gd, gt)
+    shapes = {"means": (s.N, 3), "log_scales": (s.N, 3), "quats": (s.N, 4), "opacity_logits": (s.N,),
+              "rgb": (s.N, 3), "pose": (s.K, 6)}
+    acc = {k: torch.zeros(v, device="cuda") for k, v in shapes.items()}
+    ovr = {k: torch.full(v, 7.0, device="cuda") for k, v in shapes.items()}
+    api.gs_project_bwd(r.cfg, g, ct, r.ws, acc)
+    api.gs_project_bwd(r.cfg, g, ct, r.ws, ovr, overwrite=True)
+    torch.cuda.synchronize()
+    for k in shapes:
+        assert torch.equal(acc[k], ovr[k]), k

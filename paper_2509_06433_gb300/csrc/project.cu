@@ -105,7 +105,7 @@ __device__ __forceinline__ uint32_t pack16(int lo, int hi) {
   return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
 }
 
-__global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
+__global__ void __launch_bounds__(kProjBlock, 3) k_project(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                        uint8_t* __restrict__ ws) {
   pdl_wait();
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
@@ -124,8 +124,12 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
   uint32_t count = 0, item_key = 0xffffffffu;
   // what the row-span table needs once the warp has its entries
   Ellipse E_keep{};
-  int span_x0 = 0, span_x1 = 0, row_first = 0;
+  int span_x0 = 0, span_x1 = 0, span_y0 = 0, row_first = 0;
   uint32_t nrows = 0;
+  constexpr int kCachedRows = 4;  // spans of the rectangle's first rows, kept for the table
+  int2 spc[kCachedRows];
+#pragma unroll
+  for (int q = 0; q < kCachedRows; ++q) spc[q] = make_int2(1, 0);
   if (idx < L.KN) {
     const int k = static_cast<int>(idx / L.N);
     const int64_t g = idx - static_cast<int64_t>(k) * L.N;
@@ -251,19 +255,26 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
                             ? s_grid
                             : at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * gcells;
           int first = -1, last = -1;
-          for (int ty = y0; ty < y1; ++ty) {
-            const int2 sp = row_span(E, ty, x0, x1);
-            if (sp.x > sp.y) continue;
+          auto add_row = [&](int ty, int2 sp) {
+            if (sp.x > sp.y) return;
             count += static_cast<uint32_t>(sp.y - sp.x + 1);
             atomicAdd(&dg[ty * gstride + sp.x], 1);  // row-wise prefix sum: pairs per tile
             atomicAdd(&dg[ty * gstride + sp.y + 1], -1);
             if (first < 0) first = ty;
             last = ty;
-          }
+          };
+#pragma unroll
+          for (int q = 0; q < kCachedRows; ++q)
+            if (y0 + q < y1) {
+              spc[q] = row_span(E, y0 + q, x0, x1);
+              add_row(y0 + q, spc[q]);
+            }
+          for (int ty = y0 + kCachedRows; ty < y1; ++ty) add_row(ty, row_span(E, ty, x0, x1));
           if (count) {
             E_keep = E;
             span_x0 = x0;
             span_x1 = x1;
+            span_y0 = y0;
             row_first = first;
             nrows = static_cast<uint32_t>(last - first + 1);
           }
@@ -290,7 +301,8 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
     }
   }
   // row-span table entries for the item's rows first..last (one counter atomic per warp);
-  // the spans are recomputed bit for bit by the same function
+  // rows past the first kCachedRows of the rectangle are recomputed bit for bit by the same
+  // function
   {
     const int lane = threadIdx.x & 31;
     uint32_t incl = nrows;
@@ -305,13 +317,17 @@ __global__ void __launch_bounds__(kProjBlock) k_project(Layout L, GaussPtrs G, c
     if (nrows) {
       if (static_cast<uint64_t>(base) + nrows <= static_cast<uint64_t>(L.cap)) {
         int2* tab = at<int2>(ws, L.row_table) + base;
+        const int row_end = row_first + static_cast<int>(nrows);
         int cum = 0;
-        for (uint32_t q = 0; q < nrows; ++q) {
-          const int ty = row_first + static_cast<int>(q);
-          const int2 sp = row_span(E_keep, ty, span_x0, span_x1);
-          tab[q] = make_int2(cum, (sp.x & 0xffff) | (ty << 16));
+        auto put = [&](int ty, int2 sp) {
+          tab[ty - row_first] = make_int2(cum, (sp.x & 0xffff) | (ty << 16));
           if (sp.x <= sp.y) cum += sp.y - sp.x + 1;
-        }
+        };
+#pragma unroll
+        for (int q = 0; q < kCachedRows; ++q)
+          if (span_y0 + q >= row_first && span_y0 + q < row_end) put(span_y0 + q, spc[q]);
+        for (int ty = max(span_y0 + kCachedRows, row_first); ty < row_end; ++ty)
+          put(ty, row_span(E_keep, ty, span_x0, span_x1));
         at<uint2>(ws, L.proj_rows)[idx] = make_uint2(base, nrows);
       } else {
         atomicOr(&at<Status>(ws, L.status)->err, GS_DEVERR_PAIR_OVERFLOW);

@@ -44,8 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the tracking and mapping-window fields")
     ap.add_argument("--px", default=None,
-                    help="pixels per thread of the forward and backward compositing kernels, e.g. 2,4 "
-                         "(default: autotuned on the workload)")
+                    help="pixels per thread of the forward and backward compositing kernels, e.g. 2,4, "
+                         "with the default chunk depths (default: both autotuned on the workload)")
     return ap.parse_args()
 
 
@@ -143,7 +143,7 @@ def run_ours(args, rank, world):
     if args.px:
         fpx, bpx = (int(x) for x in args.px.split(","))
         r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = fpx, bpx
-        tuned = {"fwd": None, "bwd": None, "choice": (fpx, bpx)}
+        tuned = {"fwd": None, "bwd": None, "choice": (fpx, bpx), "chunks": (0, 0)}
     else:
         tuned = autotune.tune(r, g, cams)
     out = r.new_outputs()
@@ -311,7 +311,8 @@ def run_ours(args, rank, world):
         "gaussian_pixel_evals_per_s": evals * iters / (total_ms / 1e3),
         "stage_ms_median": {k: round(v, 5) for k, v in med.items()},
         "roofline": roof,
-        "autotune": {"fwd_ms": tuned["fwd"], "bwd_ms": tuned["bwd"], "px_per_thread": list(tuned["choice"])},
+        "autotune": {"fwd_ms": _keys(tuned["fwd"]), "bwd_ms": _keys(tuned["bwd"]),
+                     "px_per_thread": list(tuned["choice"]), "chunk": list(tuned.get("chunks", (0, 0)))},
         "clocks": clocks,
     }
     return line
@@ -519,6 +520,12 @@ def load_peaks():
 FLOP_EVAL = 10.0
 FLOP_FWD_BLEND = 11.0
 FLOP_BWD_BLEND = 44.0
+
+
+def _keys(d):
+    """{(px, chunk): ms} -> {"px,chunk": ms} for JSON."""
+    return None if d is None else {",".join(str(x) for x in k) if isinstance(k, tuple) else str(k): v
+                                   for k, v in d.items()}
 
 
 def measured_traffic(stage):

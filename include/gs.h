@@ -92,6 +92,10 @@ typedef struct {
   int32_t bwd_px_per_thread;  /* pixels per thread of gs_raster_bwd: 1, 2 or 4; 0 = library default.
                                  Every choice takes the same skip/stop decisions: forward outputs are
                                  bit-identical, gradients differ only in FP32 summation order. */
+  int32_t fwd_chunk;          /* splats staged in shared memory per step of gs_raster_fwd: 64, 128 or
+                                 256; 0 = library default (128). Outputs do not depend on it. */
+  int32_t bwd_chunk;          /* the same for gs_raster_bwd: 32, 64 or 128; 0 = default (64).
+                                 Gradients do not depend on it. */
 } gs_config_t;
 
 /* Gaussian attributes. means may be F32 or BF16/F16 (means_dtype); the other four

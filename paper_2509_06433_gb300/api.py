@@ -33,9 +33,9 @@ def _s(stream):
 
 
 def make_config(width, height, num_views, num_gaussians, pair_capacity, near_plane=0.2, lambda_depth=0.1,
-                fwd_px=0, bwd_px=0):
+                fwd_px=0, bwd_px=0, fwd_chunk=0, bwd_chunk=0):
     return GsConfig(int(width), int(height), TILE, int(num_views), int(num_gaussians), int(pair_capacity),
-                    float(near_plane), float(lambda_depth), int(fwd_px), int(bwd_px))
+                    float(near_plane), float(lambda_depth), int(fwd_px), int(bwd_px), int(fwd_chunk), int(bwd_chunk))
 
 
 def workspace_size(cfg: GsConfig) -> int:
@@ -202,7 +202,9 @@ class Rasterizer:
 
     def _configure(self, cap):
         self.cap = int(min(cap, (1 << 30) - 1))
-        self.cfg = make_config(self.W, self.H, self.K, self.N, self.cap, self.near_plane, self.lambda_depth)
+        old = getattr(self, "cfg", None)  # keep the tuned kernel variants across a capacity change
+        tuned = (old.fwd_px_per_thread, old.bwd_px_per_thread, old.fwd_chunk, old.bwd_chunk) if old else (0, 0, 0, 0)
+        self.cfg = make_config(self.W, self.H, self.K, self.N, self.cap, self.near_plane, self.lambda_depth, *tuned)
         self.ws = workspace(self.cfg, self.device)
         self.layout = workspace_layout(self.cfg)
 

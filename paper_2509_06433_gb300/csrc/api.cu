@@ -42,6 +42,10 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   if (cfg->bwd_px_per_thread < 0 || cfg->bwd_px_per_thread > 4 || cfg->bwd_px_per_thread == 3) return false;
   L->fwd_px = cfg->fwd_px_per_thread;
   L->bwd_px = cfg->bwd_px_per_thread;
+  if (cfg->fwd_chunk != 0 && cfg->fwd_chunk != 64 && cfg->fwd_chunk != 128 && cfg->fwd_chunk != 256) return false;
+  if (cfg->bwd_chunk != 0 && cfg->bwd_chunk != 32 && cfg->bwd_chunk != 64 && cfg->bwd_chunk != 128) return false;
+  L->fwd_chunk = cfg->fwd_chunk;
+  L->bwd_chunk = cfg->bwd_chunk;
   L->n_proj_blocks = L->KN > 0 ? (L->KN + kProjBlock - 1) / kProjBlock : 1;
   L->item_sort_items = pick_sort_items(L->KN);
   L->pair_sort_items = pick_sort_items(L->cap);

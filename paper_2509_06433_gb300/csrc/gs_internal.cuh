@@ -49,6 +49,7 @@ struct Layout {
   int64_t max_item_tiles;   // onesweep tiles of the per-item depth sort
   float near_plane, lambda_depth;
   int fwd_px, bwd_px;       // pixels per thread of the compositing kernels (0 = default)
+  int fwd_chunk, bwd_chunk; // splats staged per chunk of the compositing kernels (0 = default)
   int64_t n_proj_blocks;    // ceil(KN / kProjBlock)
   int64_t max_sort_tiles;   // onesweep tiles of the pair sort at capacity
   int64_t n_pose_blocks;    // ceil(N / kPoseBlock)

@@ -1,0 +1,264 @@
+// Forward compositing (gs_raster_fwd, gs_raster_fwd_stats, gs_raster_fwd_l1); see
+// raster_common.cuh for the staging and the opacity test both compositing kernels share.
+#include "raster_common.cuh"
+
+namespace gs {
+namespace {
+
+// ============================================================================ forward
+// Per pixel, amin is the opacity a splat must reach to be kept: 1/255 while the pixel is
+// open, +inf once it has stopped (or lies outside the image), so a stopped pixel skips every
+// later splat without a separate flag. A kept splat that does not stop the pixel is blended
+// through ae = alpha (else ae = 0): w = ae T and T <- T - ae T leave every accumulator bit for
+// bit unchanged when ae = 0, so the blend needs no selects. STATS = true also counts the
+// evaluations (list entries examined, including the one that stops a pixel) and the blended
+// ones; the decisions and outputs are the same.
+// L1 loss fused into the forward pass (LOSS = true): the targets, the gradient images it
+// writes, per-tile partial sums and the block counter that elects the last block to finish,
+// which sums the partials in tile order into *d_loss.
+struct FusedLoss {
+  const float* rgb_t;
+  const float* depth_t;
+  float* g_rgb;
+  float* g_depth;
+  float* partials;
+  uint32_t* counter;
+  float* d_loss;
+};
+
+__device__ __forceinline__ float sgn(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
+
+template <int PX, int CH, bool STATS, bool LOSS>
+__global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
+                                                                 float* __restrict__ out_rgb,
+                                                                 float* __restrict__ out_depth,
+                                                                 float* __restrict__ out_T,
+                                                                 int32_t* __restrict__ out_last,
+                                                                 uint64_t* __restrict__ evals_out,
+                                                                 uint64_t* __restrict__ blended_out, FusedLoss F) {
+  pdl_wait();
+  constexpr int kThreads = kTilePixels / PX;
+  constexpr int kWarps = kThreads / 32;
+  const float kInf = __int_as_float(0x7f800000);
+  __shared__ Stage<CH> S;
+  __shared__ uint32_t s_red[2][kWarps];
+  const TileCoord tc = tile_coord(L, blockIdx.x);
+  const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * PX;
+  const int px = tc.tx * kTile + lx, py = tc.ty * kTile + ly;
+  const uint64_t* keys = at<uint64_t>(ws, (L.passes & 1) ? L.keys[1] : L.keys[0]);
+  const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
+  const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
+  const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
+  // this warp's pixel rows: (2 * warp) * PX .. (2 * warp + 2) * PX - 1
+  const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
+  float T[PX], cr[PX], cg[PX], cb[PX], cd[PX], amin[PX];
+  int32_t last[PX], stop_at[PX];
+  uint32_t blended = 0;
+  bool all_done = true;
+#pragma unroll
+  for (int q = 0; q < PX; ++q) {
+    T[q] = 1.0f;
+    cr[q] = cg[q] = cb[q] = cd[q] = 0.0f;
+    last[q] = 0;
+    stop_at[q] = -1;
+    const bool outside = !(px < L.W && py + q < L.H);
+    amin[q] = outside ? kInf : kAlphaMin;
+    all_done = all_done && outside;
+  }
+  for (uint32_t base = rg.x; base < rg.y; base += CH) {
+    if (__syncthreads_count(!all_done) == 0) break;
+    for (int jj = threadIdx.x; jj < CH; jj += kThreads) {
+      const uint32_t i = base + jj;
+      if (i < rg.y) stage_splat(S, jj, L, ws, keys, i, tc.k, ox, oy);
+    }
+    __syncthreads();
+    const int n = min(CH, static_cast<int>(rg.y - base));
+    const int pos0 = static_cast<int>(base - rg.x);
+    for (int j = 0; j < n; ++j) {
+      if ((j & 7) == 0) {  // warp-uniform early exit, checked every 8 splats (extra ones are no-ops)
+        all_done = true;
+#pragma unroll
+        for (int q = 0; q < PX; ++q) all_done = all_done && (amin[q] == kInf);
+        if (__all_sync(0xffffffffu, all_done)) break;
+      }
+      if (!(S.rows[j] & wrows)) continue;
+      const float4 A = S.A[j], B = S.B[j], C = S.C[j];
+      const float dx = __fsub_rn(A.x, pxc);
+      const float qadx = __fmul_rn(A.z, dx);
+      const int pos = pos0 + j;
+#pragma unroll
+      for (int q = 0; q < PX; ++q) {
+        // pixel-centre offsets are formed the same way whatever PX is, so every variant
+        // takes bit-identical decisions
+        const float dy = __fsub_rn(A.y, pyc + static_cast<float>(q));
+        const float p = __fmaf_rn(dx, __fmaf_rn(A.w, dy, qadx), __fmul_rn(__fmul_rn(B.x, dy), dy));
+        const float alpha = fminf(__fmul_rn(B.y, ex2_approx(p)), kAlphaMax);
+        const bool keep = (p <= 0.0f) && (alpha >= amin[q]);
+        const float Tn = __fmaf_rn(-T[q], alpha, T[q]);
+        const bool stop = keep && (Tn < kTStop);
+        const bool blend = keep && !stop;
+        const float ae = blend ? alpha : 0.0f;
+        const float w = __fmul_rn(ae, T[q]);
+        cr[q] = __fmaf_rn(C.x, w, cr[q]);
+        cg[q] = __fmaf_rn(C.y, w, cg[q]);
+        cb[q] = __fmaf_rn(C.z, w, cb[q]);
+        cd[q] = __fmaf_rn(B.z, w, cd[q]);
+        T[q] = __fmaf_rn(-T[q], ae, T[q]);
+        last[q] = blend ? pos + 1 : last[q];
+        amin[q] = stop ? kInf : amin[q];
+        if (STATS) {
+          stop_at[q] = stop ? pos : stop_at[q];
+          blended += blend ? 1u : 0u;
+        }
+      }
+    }
+  }
+  pdl_trigger();
+  const int64_t HW = static_cast<int64_t>(L.H) * L.W;
+  const int len = static_cast<int>(rg.y - rg.x);
+  uint32_t evals = 0;
+  float loss = 0.0f;
+  const float inv3 = 1.0f / (3.0f * static_cast<float>(HW));
+  const float invd = L.lambda_depth / static_cast<float>(HW);
+#pragma unroll
+  for (int q = 0; q < PX; ++q) {
+    const int y = py + q;
+    if (px < L.W && y < L.H) {
+      if (STATS) evals += static_cast<uint32_t>(stop_at[q] >= 0 ? stop_at[q] + 1 : len);
+      const int64_t pix = static_cast<int64_t>(y) * L.W + px;
+      const int64_t c0 = static_cast<int64_t>(tc.k) * 3 * HW + pix;
+      if (out_rgb) {
+        out_rgb[c0] = cr[q];
+        out_rgb[c0 + HW] = cg[q];
+        out_rgb[c0 + 2 * HW] = cb[q];
+      }
+      if (out_depth) out_depth[tc.k * HW + pix] = cd[q];
+      if (out_T) out_T[tc.k * HW + pix] = T[q];
+      if (out_last) out_last[tc.k * HW + pix] = last[q];
+      if (LOSS) {
+        // L = sum_k [ mean_{3HW} |R - R*| + lambda mean_{HW} |D - D*| ], sign(0) = 0
+        const float c[3] = {cr[q], cg[q], cb[q]};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          const float d = c[ch] - F.rgb_t[c0 + ch * HW];
+          loss += fabsf(d) * inv3;
+          F.g_rgb[c0 + ch * HW] = sgn(d) * inv3;
+        }
+        const float d = cd[q] - F.depth_t[tc.k * HW + pix];
+        loss += fabsf(d) * invd;
+        F.g_depth[tc.k * HW + pix] = sgn(d) * invd;
+      }
+    }
+  }
+  if (LOSS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    __shared__ float s_loss[kWarps];
+    __shared__ bool s_last;
+    if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int w = 0; w < kWarps; ++w) t += s_loss[w];
+      F.partials[blockIdx.x] = t;
+      __threadfence();
+      s_last = atomicAdd(F.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+      // the last block sums every tile's partial in a fixed order
+      __threadfence();
+      float v = 0.0f;
+      for (uint32_t i = threadIdx.x; i < gridDim.x; i += kThreads) v += __ldcg(&F.partials[i]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < kWarps; ++w) t += s_loss[w];
+        F.d_loss[0] = t;
+        *F.counter = 0;
+      }
+    }
+  }
+  if (STATS) {
+    uint32_t e = evals, c = blended;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_red[0][threadIdx.x >> 5] = e;
+      s_red[1][threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t te = 0, tcn = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        te += s_red[0][w];
+        tcn += s_red[1][w];
+      }
+      if (te) atomicAdd(reinterpret_cast<unsigned long long*>(evals_out), static_cast<unsigned long long>(te));
+      if (tcn) atomicAdd(reinterpret_cast<unsigned long long*>(blended_out), static_cast<unsigned long long>(tcn));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
+                              bool stats, const FusedLossArgs* loss, cudaStream_t s) {
+  Status* st = at<Status>(ws, L.status);
+  if (stats) {
+    cudaMemsetAsync(&st->evals, 0, sizeof(uint64_t), s);
+    cudaMemsetAsync(&st->composited, 0, sizeof(uint64_t), s);
+  }
+  if (L.n_tiles == 0) {
+    if (loss) cudaMemsetAsync(loss->d_loss, 0, sizeof(float), s);
+    return cudaGetLastError();
+  }
+  const unsigned grid = static_cast<unsigned>(L.n_tiles);
+  const uint8_t* w = static_cast<const uint8_t*>(ws);
+  uint64_t *ev = &st->evals, *cp = &st->composited;
+  FusedLoss F{};
+  if (loss)
+    F = FusedLoss{loss->rgb_t, loss->depth_t, loss->g_rgb, loss->g_depth, at<float>(ws, L.tile_loss), &st->loss_ctr,
+                  loss->d_loss};
+  const int px = pick_px(L.fwd_px, kDefaultFwdPx);
+  const int ch = pick_chunk(L.fwd_chunk, 64, 256, kFwdChunk);
+#define GS_FWD(P, C, ST, LO) \
+  launch(k_raster_fwd<P, C, ST, LO>, grid, kTilePixels / P, 0, s, L, w, rgb, depth, T_final, last, ev, cp, F)
+#define GS_FWD_CH(P, ST, LO)              \
+  switch (ch) {                           \
+    case 64: GS_FWD(P, 64, ST, LO); break;   \
+    case 256: GS_FWD(P, 256, ST, LO); break; \
+    default: GS_FWD(P, 128, ST, LO); break;  \
+  }
+  if (stats) {  // the counting variant: one chunk depth (the chunking changes no decision)
+    switch (px) {
+      case 1: GS_FWD(1, kFwdChunk, true, false); break;
+      case 2: GS_FWD(2, kFwdChunk, true, false); break;
+      default: GS_FWD(4, kFwdChunk, true, false); break;
+    }
+  } else if (loss) {
+    switch (px) {
+      case 1: GS_FWD_CH(1, false, true); break;
+      case 2: GS_FWD_CH(2, false, true); break;
+      default: GS_FWD_CH(4, false, true); break;
+    }
+  } else {
+    switch (px) {
+      case 1: GS_FWD_CH(1, false, false); break;
+      case 2: GS_FWD_CH(2, false, false); break;
+      default: GS_FWD_CH(4, false, false); break;
+    }
+  }
+#undef GS_FWD_CH
+#undef GS_FWD
+  return cudaGetLastError();
+}
+
+}  // namespace gs

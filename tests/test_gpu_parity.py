@@ -286,7 +286,7 @@ def test_bf16_and_f16_storage_match_dequantised_oracle():
 
 @pytest.mark.parametrize("name", ["ragged_tiny", "map100k"])
 def test_pixels_per_thread_variants_agree(name):
-    """Every (forward, backward) pixels-per-thread variant takes the same decisions: the
+    """Every (forward, backward) pixels-per-thread and chunk-depth variant takes the same decisions: the
     forward outputs are bit-identical; the gradients differ only by the order in which
     pixels are summed in FP32 (relative L2 below 1e-5; the pose gradient, a sum over every
     pair with cancellation, is the most sensitive)."""
@@ -295,22 +295,25 @@ def test_pixels_per_thread_variants_agree(name):
     r, g, ct, _, _ = gpu_fwd(name)
     gr, gd, gt = (torch.as_tensor(a).cuda() for a in _upstream(name, s))
     ref = None
-    for fpx in (1, 2, 4):
-        for bpx in (1, 2, 4):
-            r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = fpx, bpx
-            out = r.render(g, ct)
-            grads = r.backward(g, ct, out, gr, gd, gt)
-            got = {**{k: v.clone() for k, v in out.items()}, **{"g_" + k: v for k, v in grads.items()}}
-            if ref is None:
-                ref = got
-            else:
-                for k in ref:
-                    if k.startswith("g_"):
-                        e = rel_l2(got[k].cpu().numpy(), ref[k].cpu().numpy())
-                        assert e < 1e-5, (fpx, bpx, k, e)
-                    else:
-                        assert torch.equal(ref[k], got[k]), (fpx, bpx, k)
+    combos = [(f, b, 0, 0) for f in (1, 2, 4) for b in (1, 2, 4)]
+    combos += [(2, 4, 64, 32), (4, 2, 256, 128), (1, 1, 256, 128), (2, 2, 64, 128)]  # chunk depths
+    for fpx, bpx, fch, bch in combos:
+        r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = fpx, bpx
+        r.cfg.fwd_chunk, r.cfg.bwd_chunk = fch, bch
+        out = r.render(g, ct)
+        grads = r.backward(g, ct, out, gr, gd, gt)
+        got = {**{k: v.clone() for k, v in out.items()}, **{"g_" + k: v for k, v in grads.items()}}
+        if ref is None:
+            ref = got
+        else:
+            for k in ref:
+                if k.startswith("g_"):
+                    e = rel_l2(got[k].cpu().numpy(), ref[k].cpu().numpy())
+                    assert e < 1e-5, (fpx, bpx, k, e)
+                else:
+                    assert torch.equal(ref[k], got[k]), (fpx, bpx, k)
     r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0
+    r.cfg.fwd_chunk, r.cfg.bwd_chunk = 0, 0
 
 
 def test_counting_forward_equals_plain_forward():
@@ -340,6 +343,8 @@ def test_autotuner_picks_a_variant():
     res = autotune.tune(r, g, ct, reps=3)
     assert res["choice"][0] in (1, 2, 4) and res["choice"][1] in (1, 2, 4)
     assert (r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread) == res["choice"]
+    assert res["chunks"][0] in (64, 128, 256) and res["chunks"][1] in (32, 64, 128)
+    assert (r.cfg.fwd_chunk, r.cfg.bwd_chunk) == res["chunks"]
     check_images(to_np(r.render(g, ct)), oracle_fwd("fwd10k"))
     r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0
 

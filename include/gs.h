@@ -284,6 +284,48 @@ GS_API gs_status_t gs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int3
 GS_API gs_status_t gs_sort_diag_withheld_tile(uint64_t* keys, uint32_t* vals, int64_t n, void* tmp, size_t tmp_bytes,
                                               uint32_t* d_err_word, void* stream);
 
+/* ---------------------------------------------------------------- the mapping loop */
+
+/* Learning rates per parameter group and Adam's constants. */
+typedef struct {
+  float lr_means, lr_log_scales, lr_quats, lr_opacity, lr_rgb;
+  float beta1, beta2, eps;
+} gs_adam_t;
+
+/* Floats of the Adam state of N Gaussians: m and v (14 values per Gaussian each, grouped as
+ * means [N,3], log-scales [N,3], quaternions [N,4], opacity logits [N], colours [N,3]) and the
+ * step count. The caller zeroes it before the first step. */
+GS_API gs_status_t gs_map_adam_state_size(int64_t N, int64_t* floats);
+
+/* One Adam step (Kingma & Ba; bias-corrected) of the mapping optimiser (Sec. II-B: the map is
+ * updated from the comparison of rendered images with the key-frames) on the FP32 master arrays
+ * of N Gaussians, from the gradients in `grads` (FP32, the five parameter arrays; pose is
+ * ignored). The step count lives in the state, so the call can be replayed from a CUDA graph.
+ * storage (optional, NULL = none): reduced-storage arrays (its dtype / means_dtype) that receive
+ * the updated values rounded to nearest, for the next render; an array equal to its master is
+ * skipped. */
+GS_API gs_status_t gs_map_adam_step(int64_t N, float* means, float* log_scales, float* quats, float* opacity_logits,
+                             float* rgb, const gs_grads_t* grads, float* state, const gs_adam_t* hp,
+                             const gs_gaussians_t* storage, void* stream);
+
+/* Scratch bytes of gs_keyframe_insert for a width x height frame sampled every `stride` pixels. */
+GS_API gs_status_t gs_keyframe_tmp_size(int32_t width, int32_t height, int32_t stride, size_t* bytes);
+
+/* New Gaussians from one RGB-D key-frame (the map grows from the key-frames, Sec. II-B; how is
+ * not in the paper, so this rule is proposed): every stride-th pixel in x and y whose depth is
+ * > near_plane and, when T (the current map's transmittance image, [H,W], may be NULL) is
+ * given, whose T is > t_min, becomes one Gaussian: the pixel centre back-projected to its
+ * depth through the camera *d_cam (device; world = R^T (p_c - t)), isotropic log-scale ln(scale_factor * stride *
+ * depth / ((fx + fy) / 2)), quaternion (1, 0, 0, 0), opacity logit logit0, colour = rgb
+ * ([3,H,W]) at the pixel. They are written in row-major pixel order to FP32 arrays at
+ * indices [first, first + count), count <= capacity - first (excess pixels are dropped), and
+ * count is stored to *d_count (device). tmp: gs_keyframe_tmp_size bytes of device scratch. */
+GS_API gs_status_t gs_keyframe_insert(const gs_camera_t* d_cam, const float* rgb, const float* depth, const float* T,
+                               int32_t width, int32_t height, int32_t stride, float near_plane, float t_min,
+                               float scale_factor, float logit0, float* means, float* log_scales, float* quats,
+                               float* opacity_logits, float* colours, int64_t first, int64_t capacity,
+                               uint32_t* d_count, void* tmp, size_t tmp_bytes, void* stream);
+
 /* Largest n accepted by gs_sort_pairs_noalloc. */
 #define GS_SORT_NOALLOC_MAX_PAIRS 1048576
 

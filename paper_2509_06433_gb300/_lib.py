@@ -27,7 +27,8 @@ GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 EXPORTS = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
            "gs_raster_fwd", "gs_raster_fwd_stats", "gs_raster_fwd_l1", "gs_loss_l1", "gs_raster_bwd", "gs_project_bwd", "gs_screen_grads",
            "gs_pose_adam_step", "gs_sort_pairs_tmp_size", "gs_sort_pairs", "gs_sort_diag_withheld_tile",
-           "gs_sort_pairs_noalloc")
+           "gs_sort_pairs_noalloc", "gs_map_adam_state_size", "gs_map_adam_step", "gs_keyframe_tmp_size",
+           "gs_keyframe_insert")
 
 
 class GsConfig(ctypes.Structure):
@@ -45,6 +46,11 @@ class GsGaussians(ctypes.Structure):
 class GsGrads(ctypes.Structure):
     _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p), ("opacity_logits", c_void_p),
                 ("rgb", c_void_p), ("pose", c_void_p), ("overwrite", c_int32)]
+
+
+class GsAdam(ctypes.Structure):
+    _fields_ = [("lr_means", c_float), ("lr_log_scales", c_float), ("lr_quats", c_float), ("lr_opacity", c_float),
+                ("lr_rgb", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
 
 
 class GsWsLayout(ctypes.Structure):
@@ -92,6 +98,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
                 "gs_sort_pairs_tmp_size": [c_int64, P],
                 "gs_sort_pairs": [P, P, c_int64, c_int32, P, c_size_t, P, P],
                 "gs_sort_pairs_noalloc": [P, P, c_int64, c_int32, P, P],
+                "gs_map_adam_state_size": [c_int64, P],
+                "gs_map_adam_step": [c_int64, P, P, P, P, P, P, P, P, P, P],
+                "gs_keyframe_tmp_size": [c_int32, c_int32, c_int32, P],
+                "gs_keyframe_insert": [P, P, P, P, c_int32, c_int32, c_int32, c_float, c_float, c_float, c_float,
+                                       P, P, P, P, P, c_int64, c_int64, P, P, c_size_t, P],
                 "gs_sort_diag_withheld_tile": [P, P, c_int64, P, c_size_t, P, P],
                 "gs_pose_adam_step": [P, P, P, c_int32, c_float, c_float, c_float, c_float, c_float, c_int32, P],
             }

@@ -14,7 +14,7 @@ import dataclasses
 import torch
 
 from . import _lib
-from ._lib import GsConfig, GsGaussians, GsGrads, GsWsLayout, call
+from ._lib import GsAdam, GsConfig, GsGaussians, GsGrads, GsWsLayout, call
 
 DTYPES = {torch.float32: _lib.GS_F32, torch.bfloat16: _lib.GS_BF16, torch.float16: _lib.GS_F16}
 TILE = 16
@@ -176,6 +176,65 @@ def gs_sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: int,
     assert vals.numel() == n and keys.dtype == torch.int64 and vals.dtype == torch.int32
     call("gs_sort_pairs_noalloc", _p(keys), _p(vals), ctypes.c_int64(n), ctypes.c_int32(key_bits), _p(err),
          _s(stream))
+
+
+# ----------------------------------------------------------------------------- the mapping loop
+
+def gs_map_adam_state_size(N: int) -> int:
+    n = ctypes.c_int64()
+    call("gs_map_adam_state_size", ctypes.c_int64(N), ctypes.byref(n))
+    return n.value
+
+
+def gs_map_adam_step(masters: "Gaussians", grads: dict, state: torch.Tensor, lr: dict, beta1=0.9, beta2=0.999,
+                     eps=1e-15, storage: "Gaussians" = None, stream=None):
+    """One Adam step of the FP32 master arrays from ``grads``; refreshes ``storage`` if given."""
+    hp = GsAdam(lr["means"], lr["log_scales"], lr["quats"], lr["opacity_logits"], lr["rgb"], beta1, beta2, eps)
+    gr = GsGrads(*(_p(grads.get(k)) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose")), 0)
+    st = storage.struct() if storage is not None else None
+    call("gs_map_adam_step", ctypes.c_int64(masters.N), _p(masters.means), _p(masters.log_scales), _p(masters.quats),
+         _p(masters.opacity_logits), _p(masters.rgb), ctypes.byref(gr), _p(state), ctypes.byref(hp),
+         ctypes.byref(st) if st is not None else None, _s(stream))
+
+
+def gs_keyframe_insert(cam: torch.Tensor, rgb, depth, T, out: "Gaussians", first: int, count: torch.Tensor,
+                       stride=4, near=0.2, t_min=0.5, scale_factor=0.5, logit0=0.0, tmp=None, stream=None):
+    """Appends one key-frame's new Gaussians to the FP32 arrays of ``out`` from index ``first``;
+    ``count`` (a 1-element int32 device tensor) receives how many were written."""
+    H, W = depth.shape[-2:]
+    if tmp is None:
+        b = ctypes.c_size_t()
+        call("gs_keyframe_tmp_size", ctypes.c_int32(W), ctypes.c_int32(H), ctypes.c_int32(stride), ctypes.byref(b))
+        tmp = torch.empty(b.value, dtype=torch.uint8, device=depth.device)
+    call("gs_keyframe_insert", _p(cam), _p(rgb), _p(depth), _p(T), ctypes.c_int32(W), ctypes.c_int32(H),
+         ctypes.c_int32(stride), ctypes.c_float(near), ctypes.c_float(t_min), ctypes.c_float(scale_factor),
+         ctypes.c_float(logit0), _p(out.means), _p(out.log_scales), _p(out.quats), _p(out.opacity_logits),
+         _p(out.rgb), ctypes.c_int64(first), ctypes.c_int64(out.N), _p(count), _p(tmp), tmp.numel(), _s(stream))
+
+
+class MapOptimizer:
+    """Adam over a map: FP32 master copies of the Gaussians (the render may read a reduced-storage
+    copy, refreshed by every step), the optimiser state, the learning rates per group."""
+
+    DEFAULT_LR = {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 5e-2, "rgb": 2.5e-3}
+
+    def __init__(self, g: "Gaussians", lr: dict = None, beta1=0.9, beta2=0.999, eps=1e-15):
+        f32 = lambda t: t.float().clone().contiguous()  # noqa: E731
+        self.masters = Gaussians(f32(g.means), f32(g.log_scales), f32(g.quats), f32(g.opacity_logits), f32(g.rgb))
+        all_f32 = all(t.dtype == torch.float32 for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb))
+        # an FP32 map is updated in place; a reduced-storage map is refreshed from the masters
+        if all_f32:
+            self.masters = g
+            self.storage = None
+        else:
+            self.storage = g
+        self.state = torch.zeros(gs_map_adam_state_size(g.N), device=g.means.device)
+        self.lr = dict(self.DEFAULT_LR, **(lr or {}))
+        self.beta1, self.beta2, self.eps = beta1, beta2, eps
+
+    def step(self, grads: dict, stream=None):
+        gs_map_adam_step(self.masters, grads, self.state, self.lr, self.beta1, self.beta2, self.eps, self.storage,
+                         stream)
 
 
 # ----------------------------------------------------------------------------- convenience

@@ -102,13 +102,15 @@ class Tracker(_Captured):
 
 class MappingStep(_Captured):
     """One mapping iteration (fixed poses): render with the L1 loss against the key-frames fused
-    into the forward pass, backward to every Gaussian parameter and the poses; the gradients
-    are stored (not accumulated), so nothing is zeroed."""
+    into the forward pass, backward to every Gaussian parameter and the poses (the gradients
+    are stored, not accumulated, so nothing is zeroed), and, with an ``optimizer``, its Adam
+    step of the map; the whole iteration is one CUDA graph."""
 
     def __init__(self, r: api.Rasterizer, g: api.Gaussians, cams: torch.Tensor, rgb_t: torch.Tensor,
-                 depth_t: torch.Tensor, graph=True):
+                 depth_t: torch.Tensor, graph=True, optimizer: "api.MapOptimizer" = None):
         super().__init__(graph)
         self.r, self.g, self.cams, self.rgb_t, self.depth_t = r, g, cams, rgb_t, depth_t
+        self.optimizer = optimizer
         d = cams.device
         N, K = g.N, cams.shape[0]
         self.out = r.new_outputs()
@@ -118,7 +120,25 @@ class MappingStep(_Captured):
         self.grads = {"means": torch.zeros((N, 3), device=d), "log_scales": torch.zeros((N, 3), device=d),
                       "quats": torch.zeros((N, 4), device=d), "opacity_logits": torch.zeros(N, device=d),
                       "rgb": torch.zeros((N, 3), device=d), "pose": torch.zeros((K, 6), device=d)}
+        saved = self._snapshot()
         self._capture(self._iteration)
+        self._restore(saved)  # the warm-up iterations stepped the optimiser: start from the given map
+
+    def _tensors(self):
+        if self.optimizer is None:
+            return []
+        o = self.optimizer
+        ts = [o.state] + [getattr(o.masters, k) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb")]
+        if o.storage is not None:
+            ts += [getattr(o.storage, k) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb")]
+        return ts
+
+    def _snapshot(self):
+        return [t.clone() for t in self._tensors()]
+
+    def _restore(self, saved):
+        for t, c in zip(self._tensors(), saved):
+            t.copy_(c)
 
     def _iteration(self):
         r, o = self.r, self.out
@@ -128,3 +148,5 @@ class MappingStep(_Captured):
                              self.g_rgb, self.g_depth, self.loss)
         api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
         api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, self.grads, overwrite=True)
+        if self.optimizer is not None:
+            self.optimizer.step(self.grads)

@@ -77,6 +77,9 @@ def _declare(L):
     L.orc_project_mirror.restype = None
     L.orc_project64.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P]
     L.orc_project64.restype = None
+    L.orc_render_occluded.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _D,
+                                      _P, _P, _P, _P, _P, _P, _P]
+    L.orc_render_occluded.restype = None
     L.orc_bin.argtypes = [_I64, _I, _I, _I, _I, _P, _P, _P, _P, _I64, _P, _P, _P]
     L.orc_bin.restype = _I64
     L.orc_render_fwd.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _D, _D, _D,
@@ -192,6 +195,25 @@ def render_fwd(params, cams, W, H, vals, ranges, tile=TILE, guard=(GUARD_ALPHA, 
                                  _ptr(o["near"]), _ptr(o["alt_rgb"]), _ptr(o["alt_depth"]), _ptr(o["alt_T"]),
                                  _ptr(o["alt_last"]))
     o["total_evals"] = int(total)
+    return o
+
+
+def render_occluded(params, cams, W, H, vals, ranges, ext_depth, ext_rgb=None, tile=TILE,
+                    guard=(GUARD_ALPHA, GUARD_T, GUARD_POWER)):
+    """FP64 render occluded by an external surface (depth [K,H,W], colour [K,3,H,W] or None)."""
+    means, ls, qs, lg, rgb = params64(*params)
+    cams = _c(np.asarray(cams, np.float64), np.float64).reshape(-1, 16)
+    N, K = means.shape[0], cams.shape[0]
+    ed = _c(ext_depth, np.float32)
+    er = _c(ext_rgb, np.float32) if ext_rgb is not None else None
+    o = {"rgb": np.empty((K, 3, H, W)), "depth": np.empty((K, H, W)), "T": np.empty((K, H, W)),
+         "near": np.empty((K, H, W), np.int32), "alt_rgb": np.empty((K, 3, H, W)), "alt_depth": np.empty((K, H, W)),
+         "alt_T": np.empty((K, H, W))}
+    lib().orc_render_occluded(N, _ptr(means), _ptr(ls), _ptr(qs), _ptr(lg), _ptr(rgb), K, _ptr(cams), W, H, tile,
+                              _ptr(_c(vals, np.uint32)), _ptr(_c(ranges, np.uint32)), _ptr(ed),
+                              _ptr(er) if er is not None else None, *guard, _ptr(o["rgb"]), _ptr(o["depth"]),
+                              _ptr(o["T"]), _ptr(o["near"]), _ptr(o["alt_rgb"]), _ptr(o["alt_depth"]),
+                              _ptr(o["alt_T"]))
     return o
 
 

@@ -374,8 +374,11 @@ struct Contrib {  // one composited Gaussian of a pixel, as the backward pass ne
 // Front-to-back compositing of one pixel over its tile's sorted list (Sec. II-A reading).
 // view: the FP64 projections of this view, indexed by Gaussian id.
 // flip_at >= 0 inverts the near-threshold decision taken at that list position.
+// zmax: depth of an external surface at the pixel (+inf: none). The list is in depth order, so
+// the first Gaussian at or behind it ends the pixel (it is not composited).
 PixelResult walk_pixel(const Proj64* view, const uint32_t* vals, uint32_t start, uint32_t end, double px,
-                       double py, const Guard& gd, int flip_at, std::vector<Contrib>* trace) {
+                       double py, const Guard& gd, int flip_at, std::vector<Contrib>* trace,
+                       double zmax = INFINITY) {
   PixelResult r{};
   r.first_near = -1;
   double T = 1.0;
@@ -391,11 +394,16 @@ PixelResult walk_pixel(const Proj64* view, const uint32_t* vals, uint32_t start,
     const int pos = static_cast<int>(i - start);
     const uint32_t g = vals[i];
     const Proj64& P = view[g];
+    bool flip_here = (pos == flip_at);
+    if (std::isfinite(zmax)) {
+      bool behind = P.pc[2] >= zmax;  // decision 0: the external surface occludes the rest
+      if (std::fabs(P.pc[2] / zmax - 1.0) <= 1e-6) near_decision(pos, behind, flip_here);
+      if (behind) break;
+    }
     ++r.evals;
     const double dx = P.u - px, dy = P.v - py;
     const double power = -0.5 * (P.A * dx * dx + P.C * dy * dy) - P.B * dx * dy;
     const double mag = 0.5 * (std::fabs(P.A) * dx * dx + std::fabs(P.C) * dy * dy) + std::fabs(P.B * dx * dy);
-    bool flip_here = (pos == flip_at);
     bool skip = power > 0.0;  // decision 1
     if (std::fabs(power) <= gd.power * mag) near_decision(pos, skip, flip_here);
     if (skip) continue;
@@ -598,6 +606,46 @@ int64_t orc_render_fwd(int64_t N, const double* means, const double* log_scales,
       }
     }
   return evals;
+}
+
+// FP64 forward render with occlusion by an external surface (a digital-twin depth buffer):
+// ext_depth [K,H,W] (float, > 0), ext_rgb [K,3,H,W] (may be NULL: black). Per pixel the list
+// is composited front to back until the first Gaussian at or behind ext_depth; the surface then
+// shows through the remaining transmittance: rgb += T ext_rgb, depth += T ext_depth.
+// Outputs as orc_render_fwd (primary and alternative for near-threshold pixels).
+void orc_render_occluded(int64_t N, const double* means, const double* log_scales, const double* quats,
+                         const double* logits, const double* rgb, int K, const double* cams, int W, int H, int tile,
+                         const uint32_t* vals, const uint32_t* ranges, const float* ext_depth, const float* ext_rgb,
+                         double guard_alpha, double guard_T, double guard_power, double* out_rgb, double* out_depth,
+                         double* out_T, int32_t* out_near, double* alt_rgb, double* alt_depth, double* alt_T) {
+  const std::vector<Proj64> pr = project_all(N, means, log_scales, quats, logits, rgb, K, cams, W, H);
+  const int Tx = tiles_x(W, tile), Ty = tiles_y(H, tile);
+  const Guard gd{guard_alpha, guard_T, guard_power};
+  const int64_t HW = static_cast<int64_t>(H) * W;
+#pragma omp parallel for collapse(2) schedule(dynamic, 2)
+  for (int k = 0; k < K; ++k)
+    for (int py = 0; py < H; ++py) {
+      const Proj64* view = pr.data() + static_cast<int64_t>(k) * N;
+      for (int px = 0; px < W; ++px) {
+        const int64_t t = static_cast<int64_t>(k) * Tx * Ty + (py / tile) * Tx + (px / tile);
+        const uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+        const int64_t pix = static_cast<int64_t>(py) * W + px, kp = static_cast<int64_t>(k) * HW + pix;
+        const double zmax = static_cast<double>(ext_depth[kp]);
+        const PixelResult r = walk_pixel(view, vals, s, e, px + 0.5, py + 0.5, gd, -1, nullptr, zmax);
+        const PixelResult a =
+            r.n_near ? walk_pixel(view, vals, s, e, px + 0.5, py + 0.5, gd, r.first_near, nullptr, zmax) : r;
+        for (int ch = 0; ch < 3; ++ch) {
+          const double bg = ext_rgb ? static_cast<double>(ext_rgb[(static_cast<int64_t>(k) * 3 + ch) * HW + pix]) : 0.0;
+          out_rgb[(static_cast<int64_t>(k) * 3 + ch) * HW + pix] = r.rgb[ch] + r.T * bg;
+          alt_rgb[(static_cast<int64_t>(k) * 3 + ch) * HW + pix] = a.rgb[ch] + a.T * bg;
+        }
+        out_depth[kp] = r.depth + r.T * zmax;
+        alt_depth[kp] = a.depth + a.T * zmax;
+        out_T[kp] = r.T;
+        alt_T[kp] = a.T;
+        out_near[kp] = r.n_near;
+      }
+    }
 }
 
 // Contributors of one pixel (test aid for the transmittance-product and weight pins).

@@ -584,3 +584,72 @@ def test_two_views_sum_single_view_gradients():
     for name in ("means", "log_scales", "quats", "opacity_logits", "rgb"):
         np.testing.assert_allclose(both[name], singles[0][name] + singles[1][name], rtol=1e-10, atol=1e-12)
     np.testing.assert_allclose(both["pose"], np.concatenate([s["pose"] for s in singles]), rtol=1e-10, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- occlusion
+
+def _brute_occluded(params, cam, W, H, ext_depth, ext_rgb):
+    """Per pixel: every Gaussian in front of the external surface, by depth, front to back; then
+    the surface through the remaining transmittance."""
+    means, ls, qs, lg, rgb = (np.asarray(a, np.float64) for a in params)
+    fx, fy, cx, cy = (float(c) for c in cam[:4])
+    recs = []
+    for g in range(means.shape[0]):
+        S2, pc = _fp64_sigma2(means[g], ls[g], qs[g] / np.linalg.norm(qs[g]), cam, W, H)
+        recs.append((pc[2], g, fx * pc[0] / pc[2] + cx, fy * pc[1] / pc[2] + cy, np.linalg.inv(S2),
+                     1 / (1 + math.exp(-lg[g])), rgb[g]))
+    recs.sort(key=lambda r: (r[0], r[1]))
+    img, dep, T = np.zeros((3, H, W)), np.zeros((H, W)), np.ones((H, W))
+    for py in range(H):
+        for px in range(W):
+            Tp, c, d = 1.0, np.zeros(3), 0.0
+            zmax = float(ext_depth[py, px])
+            for z, g, u, v, inv, o, col in recs:
+                if z >= zmax:
+                    break
+                dd = np.array([u - px - 0.5, v - py - 0.5])
+                pw = -0.5 * dd @ inv @ dd
+                if pw > 0:
+                    continue
+                a = min(ALPHA_MAX, o * math.exp(pw))
+                if a < ALPHA_MIN:
+                    continue
+                if Tp * (1 - a) < T_STOP:
+                    break
+                c += col * a * Tp
+                d += z * a * Tp
+                Tp *= 1 - a
+            img[:, py, px] = c + Tp * ext_rgb[:, py, px]
+            dep[py, px], T[py, px] = d + Tp * zmax, Tp
+    return img, dep, T
+
+
+def test_occluded_render_equals_per_pixel_brute_force():
+    rng = np.random.default_rng(9)
+    N, W, H, f = 9, 32, 32, 60.0
+    params = (rng.uniform((-0.2, -0.2, 3), (0.2, 0.2, 5), (N, 3)).astype(np.float32),
+              rng.normal(-0.3, 0.1, (N, 3)).astype(np.float32),
+              rng.normal(size=(N, 4)).astype(np.float32),
+              rng.normal(0.5, 1.0, N).astype(np.float32),
+              rng.uniform(0, 1, (N, 3)).astype(np.float32))
+    cam = identity_camera(W, H, f)
+    ext_depth = rng.uniform(2.5, 5.5, (1, H, W)).astype(np.float32)
+    ext_rgb = rng.uniform(0, 1, (1, 3, H, W)).astype(np.float32)
+    lists = oracle.discrete(params, cam, W, H)
+    o = oracle.render_occluded(params, cam, W, H, lists.vals, lists.ranges, ext_depth, ext_rgb)
+    img, dep, T = _brute_occluded(params, cam, W, H, ext_depth[0], ext_rgb[0].astype(np.float64))
+    ok = o["near"][0] == 0
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(o["rgb"][0][:, ok], img[:, ok], atol=1e-12)
+    np.testing.assert_allclose(o["depth"][0][ok], dep[ok], atol=1e-12)
+    np.testing.assert_allclose(o["T"][0][ok], T[ok], atol=1e-12)
+    # occluded pixels exist, and pixels whose surface is behind everything equal the plain render
+    plain = oracle.render_fwd(params, cam, W, H, lists.vals, lists.ranges)
+    far = oracle.render_occluded(params, cam, W, H, lists.vals, lists.ranges, np.full((1, H, W), 1e9, np.float32))
+    np.testing.assert_array_equal(far["T"], plain["T"])
+    np.testing.assert_array_equal(far["rgb"], plain["rgb"] + plain["T"][:, None] * 0.0)
+    assert np.abs(o["rgb"] - plain["rgb"]).max() > 0.05
+    near = oracle.render_occluded(params, cam, W, H, lists.vals, lists.ranges, np.full((1, H, W), 0.5, np.float32),
+                                  ext_rgb)
+    np.testing.assert_array_equal(near["rgb"], ext_rgb.astype(np.float64))
+    assert np.all(near["T"] == 1.0) and np.all(near["depth"] == 0.5)

@@ -220,6 +220,16 @@ GS_API gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_
                              float* T_final, int32_t* last, const float* rgb_target, const float* depth_target,
                              float* dL_drgb, float* dL_ddepth, float* d_loss, void* stream);
 
+/* gs_raster_fwd occluded by an external surface (the digital twin's virtual objects; the
+ * viewer composites the map against them): ext_depth [K,H,W] (camera depth of the surface per
+ * pixel, +inf or very large = none), ext_rgb [K,3,H,W] (its colour; NULL = black). Per pixel
+ * the depth-sorted list is composited until the first Gaussian at or behind the surface (not
+ * composited), then the surface shows through the remaining transmittance:
+ * rgb += T ext_rgb, depth += T ext_depth. T_final and last are those of the occluded pixel. */
+GS_API gs_status_t gs_raster_fwd_occluded(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                                   float* T_final, int32_t* last, const float* ext_depth, const float* ext_rgb,
+                                   void* stream);
+
 /* Photometric loss of a mapping step: L = sum_k [ mean|R - R*| over 3HW + lambda
  * mean|D - D*| over HW ], sign(0) = 0. Writes dL/drgb [K,3,H,W], dL/ddepth [K,H,W] and
  * the scalar L to d_loss[0] (device). rgb/depth are the forward outputs. */

@@ -106,6 +106,11 @@ def gs_raster_fwd_l1(cfg, ws, rgb, depth, T_final, last, rgb_target, depth_targe
          _p(rgb_target), _p(depth_target), _p(dL_drgb), _p(dL_ddepth), _p(loss), _s(stream))
 
 
+def gs_raster_fwd_occluded(cfg, ws, rgb, depth, T_final, last, ext_depth, ext_rgb=None, stream=None):
+    call("gs_raster_fwd_occluded", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
+         _p(ext_depth), _p(ext_rgb), _s(stream))
+
+
 def gs_raster_fwd_stats(cfg, ws, rgb, depth, T_final, last, stream=None):
     call("gs_raster_fwd_stats", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
          _s(stream))

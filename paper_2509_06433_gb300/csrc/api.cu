@@ -220,6 +220,17 @@ gs_status_t gs_raster_fwd_stats(const gs_config_t* cfg, void* ws, size_t ws_byte
   return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, true, nullptr, static_cast<cudaStream_t>(stream)));
 }
 
+gs_status_t gs_raster_fwd_occluded(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                                   float* T_final, int32_t* last, const float* ext_depth, const float* ext_rgb,
+                                   void* stream) {
+  Layout L;
+  gs_status_t st = check(cfg, ws, ws_bytes, &L);
+  if (st != GS_OK) return st;
+  if (!ext_depth) return GS_ERR_INVALID_ARG;
+  return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, false, nullptr, static_cast<cudaStream_t>(stream),
+                                    ext_depth, ext_rgb));
+}
+
 gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
                              float* T_final, int32_t* last, const float* rgb_target, const float* depth_target,
                              float* dL_drgb, float* dL_ddepth, float* d_loss, void* stream) {

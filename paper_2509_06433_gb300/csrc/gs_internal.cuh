@@ -200,7 +200,8 @@ struct FusedLossArgs {
   float* d_loss;
 };
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
-                              bool stats, const FusedLossArgs* loss, cudaStream_t s);
+                              bool stats, const FusedLossArgs* loss, cudaStream_t s, const float* ext_depth = nullptr,
+                              const float* ext_rgb = nullptr);
 cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const float* depth, const float* T_final,
                               const int32_t* last, const float* dL_drgb, const float* dL_ddepth, const float* dL_dT,
                               cudaStream_t s);

@@ -28,14 +28,24 @@ struct FusedLoss {
 
 __device__ __forceinline__ float sgn(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
 
-template <int PX, int CH, bool STATS, bool LOSS>
+// Occlusion by an external surface (OCC = true): per pixel its depth and, optionally, colour
+// ([K,H,W], [K,3,H,W]). The list is in depth order, so the first splat at or behind the surface
+// ends the pixel (it is not composited); the surface then shows through the remaining
+// transmittance: rgb += T ext_rgb, depth += T ext_depth.
+struct Occlusion {
+  const float* depth;
+  const float* rgb;
+};
+
+template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false>
 __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
                                                                  float* __restrict__ out_rgb,
                                                                  float* __restrict__ out_depth,
                                                                  float* __restrict__ out_T,
                                                                  int32_t* __restrict__ out_last,
                                                                  uint64_t* __restrict__ evals_out,
-                                                                 uint64_t* __restrict__ blended_out, FusedLoss F) {
+                                                                 uint64_t* __restrict__ blended_out, FusedLoss F,
+                                                                 Occlusion O) {
   pdl_wait();
   constexpr int kThreads = kTilePixels / PX;
   constexpr int kWarps = kThreads / 32;
@@ -53,6 +63,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
   const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
   float T[PX], cr[PX], cg[PX], cb[PX], cd[PX], amin[PX];
   int32_t last[PX], stop_at[PX];
+  float zmax[PX];
   uint32_t blended = 0;
   bool all_done = true;
 #pragma unroll
@@ -63,6 +74,8 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
     stop_at[q] = -1;
     const bool outside = !(px < L.W && py + q < L.H);
     amin[q] = outside ? kInf : kAlphaMin;
+    zmax[q] = kInf;
+    if (OCC && !outside) zmax[q] = O.depth[tc.k * static_cast<int64_t>(L.H) * L.W + static_cast<int64_t>(py + q) * L.W + px];
     all_done = all_done && outside;
   }
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
@@ -93,7 +106,12 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
         const float dy = __fsub_rn(A.y, pyc + static_cast<float>(q));
         const float p = __fmaf_rn(dx, __fmaf_rn(A.w, dy, qadx), __fmul_rn(__fmul_rn(B.x, dy), dy));
         const float alpha = fminf(__fmul_rn(B.y, ex2_approx(p)), kAlphaMax);
-        const bool keep = (p <= 0.0f) && (alpha >= amin[q]);
+        bool keep = (p <= 0.0f) && (alpha >= amin[q]);
+        bool behind = false;
+        if (OCC) {
+          behind = B.z >= zmax[q];  // B.z: the splat's camera depth
+          keep = keep && !behind;
+        }
         const float Tn = __fmaf_rn(-T[q], alpha, T[q]);
         const bool stop = keep && (Tn < kTStop);
         const bool blend = keep && !stop;
@@ -105,7 +123,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
         cd[q] = __fmaf_rn(B.z, w, cd[q]);
         T[q] = __fmaf_rn(-T[q], ae, T[q]);
         last[q] = blend ? pos + 1 : last[q];
-        amin[q] = stop ? kInf : amin[q];
+        amin[q] = (stop || behind) ? kInf : amin[q];
         if (STATS) {
           stop_at[q] = stop ? pos : stop_at[q];
           blended += blend ? 1u : 0u;
@@ -127,6 +145,14 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
       if (STATS) evals += static_cast<uint32_t>(stop_at[q] >= 0 ? stop_at[q] + 1 : len);
       const int64_t pix = static_cast<int64_t>(y) * L.W + px;
       const int64_t c0 = static_cast<int64_t>(tc.k) * 3 * HW + pix;
+      if (OCC) {  // the external surface through the remaining transmittance
+        if (O.rgb) {
+          cr[q] = __fmaf_rn(T[q], O.rgb[c0], cr[q]);
+          cg[q] = __fmaf_rn(T[q], O.rgb[c0 + HW], cg[q]);
+          cb[q] = __fmaf_rn(T[q], O.rgb[c0 + 2 * HW], cb[q]);
+        }
+        cd[q] = __fmaf_rn(T[q], zmax[q], cd[q]);
+      }
       if (out_rgb) {
         out_rgb[c0] = cr[q];
         out_rgb[c0 + HW] = cg[q];
@@ -210,7 +236,8 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
 }  // namespace
 
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
-                              bool stats, const FusedLossArgs* loss, cudaStream_t s) {
+                              bool stats, const FusedLossArgs* loss, cudaStream_t s, const float* ext_depth,
+                              const float* ext_rgb) {
   Status* st = at<Status>(ws, L.status);
   if (stats) {
     cudaMemsetAsync(&st->evals, 0, sizeof(uint64_t), s);
@@ -230,14 +257,25 @@ cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* dept
   const int px = pick_px(L.fwd_px, kDefaultFwdPx);
   const int ch = pick_chunk(L.fwd_chunk, 64, 256, kFwdChunk);
 #define GS_FWD(P, C, ST, LO) \
-  launch(k_raster_fwd<P, C, ST, LO>, grid, kTilePixels / P, 0, s, L, w, rgb, depth, T_final, last, ev, cp, F)
+  launch(k_raster_fwd<P, C, ST, LO>, grid, kTilePixels / P, 0, s, L, w, rgb, depth, T_final, last, ev, cp, F, \
+         Occlusion{})
 #define GS_FWD_CH(P, ST, LO)              \
   switch (ch) {                           \
     case 64: GS_FWD(P, 64, ST, LO); break;   \
     case 256: GS_FWD(P, 256, ST, LO); break; \
     default: GS_FWD(P, 128, ST, LO); break;  \
   }
-  if (stats) {  // the counting variant: one chunk depth (the chunking changes no decision)
+  if (ext_depth) {  // occlusion by an external surface: one chunk depth
+    const Occlusion O{ext_depth, ext_rgb};
+    switch (px) {
+      case 1: launch(k_raster_fwd<1, kFwdChunk, false, false, true>, grid, kTilePixels, 0, s, L, w, rgb, depth, T_final,
+                     last, ev, cp, F, O); break;
+      case 2: launch(k_raster_fwd<2, kFwdChunk, false, false, true>, grid, kTilePixels / 2, 0, s, L, w, rgb, depth,
+                     T_final, last, ev, cp, F, O); break;
+      default: launch(k_raster_fwd<4, kFwdChunk, false, false, true>, grid, kTilePixels / 4, 0, s, L, w, rgb, depth,
+                      T_final, last, ev, cp, F, O); break;
+    }
+  } else if (stats) {  // the counting variant: one chunk depth (the chunking changes no decision)
     switch (px) {
       case 1: GS_FWD(1, kFwdChunk, true, false); break;
       case 2: GS_FWD(2, kFwdChunk, true, false); break;

@@ -428,3 +428,42 @@ def test_overwritten_gradients_equal_zeroed_accumulated_ones():
     torch.cuda.synchronize()
     for k in shapes:
         assert torch.equal(acc[k], ovr[k]), k
+
+
+@pytest.mark.parametrize("with_rgb", [True, False])
+def test_occluded_render_matches_the_oracle(with_rgb):
+    """gs_raster_fwd_occluded against the oracle's occluded render (external surface at random
+    depths inside the scene's depth range): images within the parity tolerance, and a surface
+    behind everything gives the plain render bit for bit."""
+    torch, api = torch_mods()
+    s = scene("window_k3")
+    r, g, ct, plain, d = gpu_fwd("window_k3")
+    rng = np.random.default_rng(17)
+    ext_depth = rng.uniform(1.0, 6.0, (s.K, s.H, s.W)).astype(np.float32)
+    ext_rgb = rng.uniform(0, 1, (s.K, 3, s.H, s.W)).astype(np.float32) if with_rgb else None
+    out = r.new_outputs()
+    api.gs_raster_fwd_occluded(r.cfg, r.ws, out["rgb"], out["depth"], out["T"], out["last"],
+                               torch.as_tensor(ext_depth).cuda(),
+                               torch.as_tensor(ext_rgb).cuda() if with_rgb else None)
+    torch.cuda.synchronize()
+    L = oracle_fwd("window_k3")["lists"]
+    o = oracle.render_occluded(s.params(), s.cams, s.W, s.H, L.vals, L.ranges, ext_depth, ext_rgb)
+    got = to_np(out)
+    near = o["near"]
+    excluded = near >= 2
+    assert excluded.mean() <= 1e-3
+    for key in ("rgb", "depth", "T"):
+        a = got[key].astype(np.float64)
+        p, q = np.abs(a - o[key]), np.abs(a - o["alt_" + key])
+        nb = np.broadcast_to(near[:, None], p.shape) if key == "rgb" else near
+        ex = np.broadcast_to(excluded[:, None], p.shape) if key == "rgb" else excluded
+        tol = 1e-4 * (10.0 if key == "depth" else 1.0)  # depth adds T x ext_depth (up to 6)
+        ok = (p <= tol) | ((nb == 1) & (q <= tol)) | ex
+        assert ok.all(), (key, int((~ok).sum()))
+    assert np.abs(got["rgb"] - to_np(plain)["rgb"]).max() > 0.05  # the surface occludes something
+    far = r.new_outputs()
+    api.gs_raster_fwd_occluded(r.cfg, r.ws, far["rgb"], far["depth"], far["T"], far["last"],
+                               torch.full((s.K, s.H, s.W), float("inf"), device="cuda"), None)
+    torch.cuda.synchronize()
+    for k in ("rgb", "T", "last"):
+        assert torch.equal(far[k], plain[k]), k

@@ -72,6 +72,16 @@ typedef enum {
 
 typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype_t;
 
+/* How a Gaussian's `rgb` array is read (gs_config_t.color_mode).
+ * GS_COLOR_RGB: rgb is [N,3], the colour itself, used as is (degree-0 appearance).
+ * GS_COLOR_SH:  rgb is [N,(D+1)^2,3], D = gs_config_t.sh_degree in 0..3: RGB coefficient
+ *   triples of the real spherical harmonics (Condon-Shortley phase; band l, then m = -l..l),
+ *   evaluated per view at the unit direction from the camera centre -R^T t to the mean
+ *   (Sec. II-A: view-dependent colour). colour = max(sum_i Y_i f_i + 1/2, 0); at D = 0 this is
+ *   the SH0 mapping f_0 / (2 sqrt(pi)) + 1/2. Gradients: zero where the clamp is active; the
+ *   direction's gradient reaches the means and the pose translation (rho). */
+typedef enum { GS_COLOR_RGB = 0, GS_COLOR_SH = 1 } gs_color_mode_t;
+
 /* One pinhole camera, 64 bytes. R, t map world to camera: p_c = R p + t, with the
  * camera looking along +z, x right and y down. Pixel u = fx x/z + cx, v = fy y/z + cy. */
 typedef struct {
@@ -96,6 +106,8 @@ typedef struct {
                                  256; 0 = library default (128). Outputs do not depend on it. */
   int32_t bwd_chunk;          /* the same for gs_raster_bwd: 32, 64 or 128; 0 = default (64).
                                  Gradients do not depend on it. */
+  int32_t color_mode;         /* gs_color_mode_t; 0 = GS_COLOR_RGB */
+  int32_t sh_degree;          /* 0..3 with GS_COLOR_SH (ignored with GS_COLOR_RGB) */
 } gs_config_t;
 
 /* Gaussian attributes. means may be F32 or BF16/F16 (means_dtype); the other four
@@ -105,7 +117,8 @@ typedef struct {
   const void* log_scales;     /* [N,3] log of the per-axis standard deviation */
   const void* quats;          /* [N,4] (w,x,y,z), any non-zero length */
   const void* opacity_logits; /* [N]   opacity = sigmoid(logit) */
-  const void* rgb;            /* [N,3] colour (degree-0 appearance, used as is) */
+  const void* rgb;            /* [N,3] colour (GS_COLOR_RGB), or [N,(D+1)^2,3] spherical-harmonic
+                                 coefficients (GS_COLOR_SH, see gs_color_mode_t) */
   gs_dtype_t dtype;
   gs_dtype_t means_dtype;
 } gs_gaussians_t;
@@ -117,7 +130,7 @@ typedef struct {
   float* log_scales;     /* [N,3] */
   float* quats;          /* [N,4] w.r.t. the stored (unnormalised) quaternion */
   float* opacity_logits; /* [N] */
-  float* rgb;            /* [N,3] */
+  float* rgb;            /* [N,3], or [N,(D+1)^2,3] with GS_COLOR_SH (the shape of the rgb input) */
   float* pose;           /* [K,6] (rho, phi): left perturbation T <- Exp(xi) T at xi = 0 */
   int32_t overwrite;     /* 0: accumulate into the arrays (+=); 1: store the gradients (=), so the
                             caller need not zero them first */
@@ -133,7 +146,8 @@ typedef struct {
   size_t proj_tiles;     /* int4 [K*N]: pair offset, x0 | x1 << 16, y0 | y1 << 16, tiles emitted */
   size_t proj_depth_key; /* u32 [K*N]: binary32 bits of the camera depth (sort key low word) */
   size_t proj_radius;    /* i32 [K*N]: pixel radius (0 when culled) */
-  size_t color_opacity;  /* float4 [N]: r, g, b, opacity */
+  size_t color_opacity;  /* float4 [N]: r, g, b, opacity; [K*N] (view-major) with GS_COLOR_SH of
+                            degree >= 1, whose colours depend on the view */
   size_t keys_sorted;    /* u64 [pair_capacity], valid prefix num_pairs, after gs_bin_sort:
                             (global tile id << 32) | Gaussian id */
   size_t vals_sorted;    /* u32 [pair_capacity]: emission index of each sorted pair (pairs of an
@@ -335,6 +349,32 @@ GS_API gs_status_t gs_keyframe_insert(const gs_camera_t* d_cam, const float* rgb
                                float scale_factor, float logit0, float* means, float* log_scales, float* quats,
                                float* opacity_logits, float* colours, int64_t first, int64_t capacity,
                                uint32_t* d_count, void* tmp, size_t tmp_bytes, void* stream);
+
+/* ---------------------------------------------------------------- map-accuracy metrics
+ *
+ * Sec. IV judges a map by the PSNR and SSIM of its rendered views against the key-frames (and
+ * its generation speed by the time a new frame takes to reach its final PSNR / SSIM). The
+ * paper gives no formula; these are the standard definitions of the splatting literature:
+ *   PSNR of an image = 10 log10(R^2 / MSE) over its C*H*W values (+inf when MSE = 0);
+ *   SSIM (Wang et al. 2004) per pixel and channel under an 11 x 11 Gaussian window (sigma 1.5,
+ *   taps normalised to sum 1) over zero-padded planes, C1 = (0.01 R)^2, C2 = (0.03 R)^2; an
+ *   image's SSIM is the mean of its map.
+ * x, y: device FP32 images [images, channels, height, width], contiguous. R = data_range > 0.
+ * Results are deterministic (fixed-order reductions). images <= 65535, images * channels <=
+ * 65535, height and width <= 65536, else GS_ERR_INVALID_ARG. */
+
+/* Device scratch bytes of gs_psnr / gs_ssim for these dimensions. */
+GS_API gs_status_t gs_metrics_tmp_size(int32_t images, int32_t channels, int32_t height, int32_t width, size_t* bytes);
+
+/* psnr: device float [images]. tmp: gs_metrics_tmp_size bytes of device scratch. */
+GS_API gs_status_t gs_psnr(const float* x, const float* y, int32_t images, int32_t channels, int32_t height,
+                           int32_t width, float data_range, float* psnr, void* tmp, size_t tmp_bytes, void* stream);
+
+/* ssim: device float [images] (mean SSIM); ssim_map: device float [images, channels, height,
+ * width] or NULL (not written). tmp: gs_metrics_tmp_size bytes of device scratch. */
+GS_API gs_status_t gs_ssim(const float* x, const float* y, int32_t images, int32_t channels, int32_t height,
+                           int32_t width, float data_range, float* ssim, float* ssim_map, void* tmp, size_t tmp_bytes,
+                           void* stream);
 
 /* Largest n accepted by gs_sort_pairs_noalloc. */
 #define GS_SORT_NOALLOC_MAX_PAIRS 1048576

@@ -28,14 +28,14 @@ EXPORTS = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_pro
            "gs_raster_fwd", "gs_raster_fwd_stats", "gs_raster_fwd_l1", "gs_raster_fwd_occluded", "gs_loss_l1", "gs_raster_bwd", "gs_project_bwd", "gs_screen_grads",
            "gs_pose_adam_step", "gs_sort_pairs_tmp_size", "gs_sort_pairs", "gs_sort_diag_withheld_tile",
            "gs_sort_pairs_noalloc", "gs_map_adam_state_size", "gs_map_adam_step", "gs_keyframe_tmp_size",
-           "gs_keyframe_insert")
+           "gs_keyframe_insert", "gs_metrics_tmp_size", "gs_psnr", "gs_ssim")
 
 
 class GsConfig(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("tile", c_int32), ("num_views", c_int32),
                 ("num_gaussians", c_int64), ("pair_capacity", c_int64), ("near_plane", c_float),
                 ("lambda_depth", c_float), ("fwd_px_per_thread", c_int32), ("bwd_px_per_thread", c_int32),
-                ("fwd_chunk", c_int32), ("bwd_chunk", c_int32)]
+                ("fwd_chunk", c_int32), ("bwd_chunk", c_int32), ("color_mode", c_int32), ("sh_degree", c_int32)]
 
 
 class GsGaussians(ctypes.Structure):
@@ -104,6 +104,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
                 "gs_keyframe_tmp_size": [c_int32, c_int32, c_int32, P],
                 "gs_keyframe_insert": [P, P, P, P, c_int32, c_int32, c_int32, c_float, c_float, c_float, c_float,
                                        P, P, P, P, P, c_int64, c_int64, P, P, c_size_t, P],
+                "gs_metrics_tmp_size": [c_int32, c_int32, c_int32, c_int32, P],
+                "gs_psnr": [P, P, c_int32, c_int32, c_int32, c_int32, c_float, P, P, c_size_t, P],
+                "gs_ssim": [P, P, c_int32, c_int32, c_int32, c_int32, c_float, P, P, P, c_size_t, P],
                 "gs_sort_diag_withheld_tile": [P, P, c_int64, P, c_size_t, P, P],
                 "gs_pose_adam_step": [P, P, P, c_int32, c_float, c_float, c_float, c_float, c_float, c_int32, P],
             }

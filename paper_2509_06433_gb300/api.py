@@ -32,10 +32,17 @@ def _s(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+COLOR_RGB, COLOR_SH = 0, 1
+
+
 def make_config(width, height, num_views, num_gaussians, pair_capacity, near_plane=0.2, lambda_depth=0.1,
-                fwd_px=0, bwd_px=0, fwd_chunk=0, bwd_chunk=0):
+                fwd_px=0, bwd_px=0, fwd_chunk=0, bwd_chunk=0, sh_degree=None):
+    """sh_degree None: the rgb array is the colour [N,3]; 0..3: it holds spherical-harmonic
+    coefficients [N,(sh_degree+1)^2,3] evaluated per view."""
+    mode = COLOR_RGB if sh_degree is None else COLOR_SH
     return GsConfig(int(width), int(height), TILE, int(num_views), int(num_gaussians), int(pair_capacity),
-                    float(near_plane), float(lambda_depth), int(fwd_px), int(bwd_px), int(fwd_chunk), int(bwd_chunk))
+                    float(near_plane), float(lambda_depth), int(fwd_px), int(bwd_px), int(fwd_chunk), int(bwd_chunk),
+                    mode, int(sh_degree or 0))
 
 
 def workspace_size(cfg: GsConfig) -> int:
@@ -217,6 +224,46 @@ def gs_keyframe_insert(cam: torch.Tensor, rgb, depth, T, out: "Gaussians", first
          _p(out.rgb), ctypes.c_int64(first), ctypes.c_int64(out.N), _p(count), _p(tmp), tmp.numel(), _s(stream))
 
 
+def _image_dims(x: torch.Tensor):
+    if x.dim() == 3:
+        x = x.unsqueeze(0)
+    if x.dim() != 4 or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("images must be contiguous float32 [B, C, H, W] or [C, H, W]")
+    return x.shape
+
+
+def gs_metrics_tmp_size(images: int, channels: int, height: int, width: int) -> int:
+    b = ctypes.c_size_t()
+    call("gs_metrics_tmp_size", ctypes.c_int32(images), ctypes.c_int32(channels), ctypes.c_int32(height),
+         ctypes.c_int32(width), ctypes.byref(b))
+    return b.value
+
+
+def gs_psnr(x: torch.Tensor, y: torch.Tensor, data_range=1.0, out=None, tmp=None, stream=None) -> torch.Tensor:
+    """PSNR of each image of x against y ([B, C, H, W] or [C, H, W]); returns a device [B] tensor."""
+    B, C, H, W = _image_dims(x)
+    if tuple(y.shape[-3:]) != (C, H, W) or y.numel() != x.numel():
+        raise ValueError("x and y must have the same shape")
+    out = torch.empty(B, device=x.device) if out is None else out
+    tmp = torch.empty(gs_metrics_tmp_size(B, C, H, W), dtype=torch.uint8, device=x.device) if tmp is None else tmp
+    call("gs_psnr", _p(x), _p(y.contiguous()), ctypes.c_int32(B), ctypes.c_int32(C), ctypes.c_int32(H),
+         ctypes.c_int32(W), ctypes.c_float(data_range), _p(out), _p(tmp), tmp.numel(), _s(stream))
+    return out
+
+
+def gs_ssim(x: torch.Tensor, y: torch.Tensor, data_range=1.0, out=None, ssim_map=None, tmp=None, stream=None):
+    """Mean SSIM of each image of x against y; returns a device [B] tensor (and fills ssim_map,
+    a [B, C, H, W] float32 tensor, when given)."""
+    B, C, H, W = _image_dims(x)
+    if tuple(y.shape[-3:]) != (C, H, W) or y.numel() != x.numel():
+        raise ValueError("x and y must have the same shape")
+    out = torch.empty(B, device=x.device) if out is None else out
+    tmp = torch.empty(gs_metrics_tmp_size(B, C, H, W), dtype=torch.uint8, device=x.device) if tmp is None else tmp
+    call("gs_ssim", _p(x), _p(y.contiguous()), ctypes.c_int32(B), ctypes.c_int32(C), ctypes.c_int32(H),
+         ctypes.c_int32(W), ctypes.c_float(data_range), _p(out), _p(ssim_map), _p(tmp), tmp.numel(), _s(stream))
+    return out
+
+
 class MapOptimizer:
     """Adam over a map: FP32 master copies of the Gaussians (the render may read a reduced-storage
     copy, refreshed by every step), the optimiser state, the learning rates per group."""
@@ -256,10 +303,11 @@ class Rasterizer:
     """
 
     def __init__(self, width, height, num_views, num_gaussians, pair_capacity=None, device="cuda",
-                 near_plane=0.2, lambda_depth=0.1):
+                 near_plane=0.2, lambda_depth=0.1, sh_degree=None):
         self.W, self.H, self.K, self.N = int(width), int(height), int(num_views), int(num_gaussians)
         self.device = torch.device(device)
         self.near_plane, self.lambda_depth = near_plane, lambda_depth
+        self.sh_degree = sh_degree  # None: rgb [N,3] is the colour; 0..3: SH coefficients [N,(D+1)^2,3]
         if pair_capacity is None:
             pair_capacity = max(1 << 16, 8 * self.N * self.K)
         self._configure(pair_capacity)
@@ -268,9 +316,14 @@ class Rasterizer:
         self.cap = int(min(cap, (1 << 30) - 1))
         old = getattr(self, "cfg", None)  # keep the tuned kernel variants across a capacity change
         tuned = (old.fwd_px_per_thread, old.bwd_px_per_thread, old.fwd_chunk, old.bwd_chunk) if old else (0, 0, 0, 0)
-        self.cfg = make_config(self.W, self.H, self.K, self.N, self.cap, self.near_plane, self.lambda_depth, *tuned)
+        self.cfg = make_config(self.W, self.H, self.K, self.N, self.cap, self.near_plane, self.lambda_depth, *tuned,
+                               sh_degree=self.sh_degree)
         self.ws = workspace(self.cfg, self.device)
         self.layout = workspace_layout(self.cfg)
+
+    def color_shape(self):
+        """Shape of the Gaussians' rgb array (and of its gradient) for this rasterizer."""
+        return (self.N, 3) if self.sh_degree is None else (self.N, (self.sh_degree + 1) ** 2, 3)
 
     def status(self, stream=None):
         return gs_read_status(self.cfg, self.ws, stream)
@@ -313,7 +366,7 @@ class Rasterizer:
             d = self.device
             grads = {"means": torch.zeros((self.N, 3), device=d), "log_scales": torch.zeros((self.N, 3), device=d),
                      "quats": torch.zeros((self.N, 4), device=d), "opacity_logits": torch.zeros(self.N, device=d),
-                     "rgb": torch.zeros((self.N, 3), device=d), "pose": torch.zeros((self.K, 6), device=d)}
+                     "rgb": torch.zeros(self.color_shape(), device=d), "pose": torch.zeros((self.K, 6), device=d)}
         gs_raster_bwd(self.cfg, self.ws, out["rgb"], out["depth"], out["T"], out["last"], dL_drgb, dL_ddepth, dL_dT,
                       stream)
         gs_project_bwd(self.cfg, g, cams, self.ws, grads, stream)

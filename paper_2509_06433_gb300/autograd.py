@@ -62,7 +62,7 @@ class _Render(torch.autograd.Function):
             return None, None, None, None, None, None, None, pose, None
         grads = {"means": torch.empty((N, 3), device=d), "log_scales": torch.empty((N, 3), device=d),
                  "quats": torch.empty((N, 4), device=d), "opacity_logits": torch.empty(N, device=d),
-                 "rgb": torch.empty((N, 3), device=d), "pose": pose}
+                 "rgb": torch.empty(r.color_shape(), device=d), "pose": pose}
         api.gs_project_bwd(r.cfg, ctx.g, cams, r.ws, grads, overwrite=True)
         cast = lambda t, like: t.to(like.dtype) if like.dtype != t.dtype else t  # noqa: E731
         g = ctx.g

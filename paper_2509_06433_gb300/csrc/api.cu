@@ -46,6 +46,13 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   if (cfg->bwd_chunk != 0 && cfg->bwd_chunk != 32 && cfg->bwd_chunk != 64 && cfg->bwd_chunk != 128) return false;
   L->fwd_chunk = cfg->fwd_chunk;
   L->bwd_chunk = cfg->bwd_chunk;
+  if (cfg->color_mode != GS_COLOR_RGB && cfg->color_mode != GS_COLOR_SH) return false;
+  if (cfg->color_mode == GS_COLOR_SH && (cfg->sh_degree < 0 || cfg->sh_degree > 3)) return false;
+  L->color_mode = cfg->color_mode;
+  L->sh_degree = cfg->color_mode == GS_COLOR_SH ? cfg->sh_degree : 0;
+  L->sh_coeffs = (L->sh_degree + 1) * (L->sh_degree + 1);
+  // colours depend on the view only through spherical harmonics of degree >= 1
+  L->color_stride = (cfg->color_mode == GS_COLOR_SH && cfg->sh_degree > 0) ? L->N : 0;
   L->n_proj_blocks = L->KN > 0 ? (L->KN + kProjBlock - 1) / kProjBlock : 1;
   L->item_sort_items = pick_sort_items(L->KN);
   L->pair_sort_items = pick_sort_items(L->cap);
@@ -72,7 +79,7 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->row_table = take(cap * 8);
   L->pair_valid = take((cap + 31) / 32 * 4);
   L->tile_loss = take(static_cast<size_t>(L->n_tiles) * 4);
-  L->color_opacity = take(N * 16);
+  L->color_opacity = take((L->color_stride ? KN : N) * 16);
   L->block_sums = take(static_cast<size_t>(L->n_proj_blocks) * 4);
   L->block_offsets = take(static_cast<size_t>(L->n_proj_blocks) * 8);
   L->keys[0] = take(cap * 8);

@@ -50,6 +50,8 @@ struct Layout {
   float near_plane, lambda_depth;
   int fwd_px, bwd_px;       // pixels per thread of the compositing kernels (0 = default)
   int fwd_chunk, bwd_chunk; // splats staged per chunk of the compositing kernels (0 = default)
+  int color_mode, sh_degree, sh_coeffs;  // gs_color_mode_t; SH degree and (degree + 1)^2
+  int64_t color_stride;     // index of (view k, Gaussian g) in color_opacity = k * color_stride + g
   int64_t n_proj_blocks;    // ceil(KN / kProjBlock)
   int64_t max_sort_tiles;   // onesweep tiles of the pair sort at capacity
   int64_t n_pose_blocks;    // ceil(N / kPoseBlock)

@@ -10,6 +10,7 @@
 //    float pairs (hi + lo, Dot2-style compensated arithmetic), so the 2D mean that the
 //    compositing uses is accurate to ~1e-12 px instead of ~4e-5 px at 640 px.
 #include "gs_internal.cuh"
+#include "sh.cuh"
 
 namespace gs {
 namespace {
@@ -143,16 +144,28 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project(Layout L, GaussPtrs G
     const float* R = cam.R;
     const float* t = cam.t;
     const float lg = load_attr(G.logits, g, G.dtype);
-    if (k == 0) {
-      const float c0 = load_attr(G.rgb, 3 * g + 0, G.dtype);
-      const float c1 = load_attr(G.rgb, 3 * g + 1, G.dtype);
-      const float c2 = load_attr(G.rgb, 3 * g + 2, G.dtype);
+    // colour and opacity: once per Gaussian, or per item when the colour depends on the view
+    if (k == 0 || L.color_stride != 0) {
+      float c0, c1, c2;
+      bool finite_c = true;
+      if (L.color_mode == GS_COLOR_SH) {
+        const ShDir u = sh_dir(p0, p1, p2, cam);
+        float Y[kShMaxCoeffs];
+        sh_basis(u.x, u.y, u.z, Y);
+        const float3 raw = sh_raw(G.rgb, G.dtype, g, L.sh_coeffs, Y, finite_c);
+        c0 = fmaxf(raw.x, 0.0f), c1 = fmaxf(raw.y, 0.0f), c2 = fmaxf(raw.z, 0.0f);
+      } else {
+        c0 = load_attr(G.rgb, 3 * g + 0, G.dtype);
+        c1 = load_attr(G.rgb, 3 * g + 1, G.dtype);
+        c2 = load_attr(G.rgb, 3 * g + 2, G.dtype);
+        finite_c = isfinite(c0) && isfinite(c1) && isfinite(c2);
+      }
       const float o = 1.0f / (1.0f + expf(-lg));
-      at<float4>(ws, L.color_opacity)[g] = make_float4(c0, c1, c2, o);
+      at<float4>(ws, L.color_opacity)[k * L.color_stride + g] = make_float4(c0, c1, c2, o);
       const bool finite = isfinite(p0) && isfinite(p1) && isfinite(p2) && isfinite(ls[0]) && isfinite(ls[1]) &&
                           isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]) &&
-                          isfinite(lg) && isfinite(c0) && isfinite(c1) && isfinite(c2);
-      if (!finite) atomicOr(&at<Status>(ws, L.status)->err, GS_DEVERR_NONFINITE);
+                          isfinite(lg) && finite_c;
+      if (k == 0 && !finite) atomicOr(&at<Status>(ws, L.status)->err, GS_DEVERR_NONFINITE);
     }
 
     // ---------------- discrete path: fixed binary32 operation order -----------------

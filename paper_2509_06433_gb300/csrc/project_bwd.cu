@@ -11,9 +11,13 @@
 // dQ = dM diag(s), ds = diag(Q^T dM), dq through the normalisation; dp_c from J, (u, v), z;
 // pose (left perturbation): drho = dp_c, dphi = p_c x dp_c + vee(Nm dNm^T - dNm Nm^T).
 #include "gs_internal.cuh"
+#include "sh.cuh"
 
 namespace gs {
 namespace {
+
+// *p += v, or with `store` *p = v (the old value is not read: it may be uninitialised)
+__device__ __forceinline__ void put(float* p, bool store, float v) { *p = store ? v : *p + v; }
 
 struct Sum10 {
   float v[10];
@@ -142,6 +146,7 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
 
   float d_mean[3] = {0, 0, 0}, dM_acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   float d_op = 0.0f, d_rgb[3] = {0, 0, 0};
+  bool sh_touched = false;  // spherical-harmonic gradients already written for this Gaussian
 
   for (int k = 0; k < L.K; ++k) {
     float pose[6] = {0, 0, 0, 0, 0, 0};
@@ -243,6 +248,53 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
       pose[3] = pc[1] * dpc[2] - pc[2] * dpc[1] + Am[1][2] - Am[2][1];
       pose[4] = pc[2] * dpc[0] - pc[0] * dpc[2] + Am[2][0] - Am[0][2];
       pose[5] = pc[0] * dpc[1] - pc[1] * dpc[0] + Am[0][1] - Am[1][0];
+      if (L.color_mode == GS_COLOR_SH) {
+        // view-dependent colour: this view's colour gradient through the clamp (raw < 0: zero)
+        // into the coefficients, dL/df_i = Y_i g, written per view (accumulated in the output,
+        // so no per-coefficient registers), and into the unit direction u = (p - C) / |p - C|:
+        // dL/dp = (I - u u^T) (sum_i (f_i . g) grad Y_i) / |p - C|; the camera centre moves by
+        // -R^T rho under the pose perturbation, so dL/drho = R dL/dp.
+        const ShDir u = sh_dir(p[0], p[1], p[2], cam);
+        float Y[kShMaxCoeffs];
+        sh_basis(u.x, u.y, u.z, Y);
+        bool fin = true;
+        const float3 raw = sh_raw(G.rgb, G.dtype, g, L.sh_coeffs, Y, fin);
+        const float gc0 = raw.x >= 0.0f ? s.v[7] : 0.0f, gc1 = raw.y >= 0.0f ? s.v[8] : 0.0f,
+                    gc2 = raw.z >= 0.0f ? s.v[9] : 0.0f;
+        const int64_t base = g * L.sh_coeffs * 3;
+        const bool store_c = out.overwrite && !sh_touched;
+        float sv[kShMaxCoeffs];
+#pragma unroll
+        for (int i = 0; i < kShMaxCoeffs; ++i) {
+          sv[i] = 0.0f;
+          if (i < L.sh_coeffs) {
+            const float f0 = load_attr(G.rgb, base + 3 * i + 0, G.dtype);
+            const float f1 = load_attr(G.rgb, base + 3 * i + 1, G.dtype);
+            const float f2 = load_attr(G.rgb, base + 3 * i + 2, G.dtype);
+            sv[i] = gc0 * f0 + gc1 * f1 + gc2 * f2;
+            if (out.rgb) {
+              float* o3 = out.rgb + base + 3 * i;
+              put(o3 + 0, store_c, Y[i] * gc0);
+              put(o3 + 1, store_c, Y[i] * gc1);
+              put(o3 + 2, store_c, Y[i] * gc2);
+            }
+          }
+        }
+        sh_touched = true;
+        if (L.sh_degree > 0) {
+          float gx, gy, gz;
+          sh_basis_vjp(u.x, u.y, u.z, sv, gx, gy, gz);
+          const float ud = gx * u.x + gy * u.y + gz * u.z;
+          const float dd0 = (gx - u.x * ud) * u.inv_r, dd1 = (gy - u.y * ud) * u.inv_r,
+                      dd2 = (gz - u.z * ud) * u.inv_r;
+          d_mean[0] += dd0;
+          d_mean[1] += dd1;
+          d_mean[2] += dd2;
+          pose[0] += R[0] * dd0 + R[1] * dd1 + R[2] * dd2;
+          pose[1] += R[3] * dd0 + R[4] * dd1 + R[5] * dd2;
+          pose[2] += R[6] * dd0 + R[7] * dd1 + R[8] * dd2;
+        }
+      }
     }
     // block reduction of this view's pose gradient
 #pragma unroll
@@ -285,17 +337,22 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
   const float qh[4] = {w, x, y, z};
   const float o = 1.0f / (1.0f + expf(-lg));
   // accumulate (+=) or, with out.overwrite, store (=)
-  const float keep = out.overwrite ? 0.0f : 1.0f;
+  const bool store = out.overwrite != 0;
   if (out.means)
-    for (int j = 0; j < 3; ++j) out.means[3 * g + j] = fmaf(keep, out.means[3 * g + j], d_mean[j]);
+    for (int j = 0; j < 3; ++j) put(out.means + 3 * g + j, store, d_mean[j]);
   if (out.log_scales)
-    for (int j = 0; j < 3; ++j) out.log_scales[3 * g + j] = fmaf(keep, out.log_scales[3 * g + j], dls[j]);
+    for (int j = 0; j < 3; ++j) put(out.log_scales + 3 * g + j, store, dls[j]);
   if (out.quats)
     for (int j = 0; j < 4; ++j)
-      out.quats[4 * g + j] = fmaf(keep, out.quats[4 * g + j], (dqh[j] - qh[j] * qd) * iq);
-  if (out.opacity_logits) out.opacity_logits[g] = fmaf(keep, out.opacity_logits[g], d_op * o * (1.0f - o));
-  if (out.rgb)
-    for (int j = 0; j < 3; ++j) out.rgb[3 * g + j] = fmaf(keep, out.rgb[3 * g + j], d_rgb[j]);
+      put(out.quats + 4 * g + j, store, (dqh[j] - qh[j] * qd) * iq);
+  if (out.opacity_logits) put(out.opacity_logits + g, store, d_op * o * (1.0f - o));
+  if (out.rgb) {
+    if (L.color_mode != GS_COLOR_SH) {
+      for (int j = 0; j < 3; ++j) put(out.rgb + 3 * g + j, store, d_rgb[j]);
+    } else if (out.overwrite && !sh_touched) {  // seen by no view: zero gradient
+      for (int j = 0; j < 3 * L.sh_coeffs; ++j) out.rgb[g * 3 * L.sh_coeffs + j] = 0.0f;
+    }
+  }
   pdl_trigger();
 }
 

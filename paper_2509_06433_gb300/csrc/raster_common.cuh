@@ -95,7 +95,7 @@ __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layou
   const int64_t kg = static_cast<int64_t>(k) * L.N + gid;
   const float4 uv = at<float4>(ws, L.proj_uv)[kg];
   const float4 cn = at<float4>(ws, L.proj_conic)[kg];
-  const float4 co = at<float4>(ws, L.color_opacity)[gid];
+  const float4 co = at<float4>(ws, L.color_opacity)[k * L.color_stride + gid];
   const float x = __fadd_rn(__fsub_rn(uv.x, ox), uv.y), y = __fadd_rn(__fsub_rn(uv.z, oy), uv.w);
   const float qa = __fmul_rn(cn.x, -0.5f * kLog2e), qb = __fmul_rn(cn.y, -kLog2e), qc = __fmul_rn(cn.z, -0.5f * kLog2e);
   S.A[j] = make_float4(x, y, qa, qb);

@@ -12,5 +12,6 @@ from .generate import (  # noqa: F401
     make_scene,
     perturb_pose,
     random_image,
+    sh_coefficients,
     SCENE_CONFIGS,
 )

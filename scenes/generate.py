@@ -330,3 +330,12 @@ def make_scene(name: str, seed: int | None = None, n: int | None = None, K: int 
 def random_image(seed: int, shape, lo=-1.0, hi=1.0) -> np.ndarray:
     """Seeded uniform float32 array, e.g. an upstream gradient dL/dimage."""
     return np.random.default_rng(seed).uniform(lo, hi, size=shape).astype(np.float32)
+
+
+def sh_coefficients(seed: int, n: int, degree: int, dc_range=1.0, rest_sd=0.15) -> np.ndarray:
+    """Seeded float32 spherical-harmonic colour coefficients [n, (degree + 1)^2, 3]: the first
+    (constant) triple uniform in [-dc_range, dc_range], the others normal with sd rest_sd."""
+    rng = np.random.default_rng(seed)
+    f = rng.normal(0.0, rest_sd, (n, (degree + 1) ** 2, 3))
+    f[:, 0] = rng.uniform(-dc_range, dc_range, (n, 3))
+    return f.astype(np.float32)

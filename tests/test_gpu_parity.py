@@ -422,7 +422,8 @@ def test_overwritten_gradients_equal_zeroed_accumulated_ones():
     shapes = {"means": (s.N, 3), "log_scales": (s.N, 3), "quats": (s.N, 4), "opacity_logits": (s.N,),
               "rgb": (s.N, 3), "pose": (s.K, 6)}
     acc = {k: torch.zeros(v, device="cuda") for k, v in shapes.items()}
-    ovr = {k: torch.full(v, 7.0, device="cuda") for k, v in shapes.items()}
+    # NaN in the outputs: overwrite must not read them (uninitialised memory may hold NaN)
+    ovr = {k: torch.full(v, float("nan"), device="cuda") for k, v in shapes.items()}
     api.gs_project_bwd(r.cfg, g, ct, r.ws, acc)
     api.gs_project_bwd(r.cfg, g, ct, r.ws, ovr, overwrite=True)
     torch.cuda.synchronize()

@@ -525,6 +525,82 @@ def measure_aerial(dev, reps=3, track_iters=50):
             "px_per_thread": [r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread]}
 
 
+def measure_time_to_psnr(dev, iters=100, every=5):
+    """Map-generation speed (Sec. IV: the time each incoming frame takes to reach its final
+    PSNR / SSIM): online mapping of a robot's 90-degree turn (turn_room: 10 key-frames at
+    672x376 rendered from a 500k-Gaussian textured room). Each key-frame is inserted
+    (uncovered pixels become Gaussians) and mapped for `iters` iterations over a window of the
+    4 latest key-frames (one CUDA graph per iteration: render, fused L1, backward, Adam); its
+    view's PSNR / SSIM is evaluated on the GPU every `every` iterations, outside the timed
+    mapping work."""
+    import torch
+    from paper_2509_06433_gb300 import api, online
+    from scenes import make_scene
+    s = make_scene("turn_room")
+    g = api.Gaussians.from_numpy(s.params(), device=dev)
+    cams = torch.as_tensor(s.cams.reshape(-1, 16)).to(dev).contiguous()
+    r = api.Rasterizer(s.W, s.H, s.K, s.N, device=dev)
+    r.plan(g, cams)
+    kf = r.render(g, cams)
+    cover = 1.0 - kf["T"]
+    depth = torch.where(cover > 0.5, kf["depth"] / cover.clamp_min(1e-6), torch.zeros_like(cover))
+    frames = [(kf["rgb"][k].contiguous(), depth[k].contiguous(), cams[k].contiguous()) for k in range(s.K)]
+    del r
+    m = online.OnlineMapper(s.W, s.H, capacity=300_000, window=4, device=dev)
+    rec = online.map_sequence(m, frames, iters_per_frame=iters, eval_every=every, thresholds=(20.0, 21.0))
+    t_map = sum(rc["curve"][-1][0] for rc in rec)
+    rnd = lambda x: None if x is None else round(x, 5)  # noqa: E731
+    return {"workload": "turn_room: 10 key-frames 672x376 (f = 260) over a 90-degree turn in an 8x6x3 m room "
+                        "of 500k textured Gaussians; window of 4 key-frames; insertion stride 4",
+            "iters_per_frame": iters, "eval_every": every,
+            "seconds_to_psnr20": [rnd(rc["t_reach"][20.0]) for rc in rec],
+            "seconds_to_psnr21": [rnd(rc["t_reach"][21.0]) for rc in rec],
+            "psnr_after_insertion": [round(rc["curve"][0][2], 2) for rc in rec],
+            "psnr_final": [round(rc["curve"][-1][2], 2) for rc in rec],
+            "ssim_final": [round(rc["curve"][-1][3], 4) for rc in rec],
+            "gaussians_added": [rc["added"] for rc in rec], "gaussians_total": m.count,
+            "mapping_seconds_total": round(t_map, 4), "pair_overflow": m.overflowed()}
+
+
+def measure_sh(dev, reps=20):
+    """Cost of view-dependent colour: the map100k mapping iteration (render + fused L1 +
+    backward, one graph) with the stored RGB colour and with spherical harmonics of degree
+    0-3 (the colour evaluated per view in the projection, its gradient per view in the
+    projection's backward)."""
+    import torch
+    from paper_2509_06433_gb300 import api
+    from paper_2509_06433_gb300.tracking import MappingStep
+    from scenes import make_scene, sh_coefficients
+    s = make_scene("map100k")
+    cams = torch.as_tensor(s.cams).to(dev)
+    tgt = api.Rasterizer(s.W, s.H, s.K, s.N, device=dev)
+    t = s.target
+    gt = api.Gaussians.from_numpy(t.params(), device=dev)
+    tgt.plan(gt, cams)
+    o = tgt.render(gt, cams)
+    rgb_t, depth_t = o["rgb"].clone(), o["depth"].clone()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    res = {}
+    for deg in (None, 0, 1, 2, 3):
+        colour = s.rgb if deg is None else sh_coefficients(200 + deg, s.N, deg)
+        g = api.Gaussians.from_numpy((s.means, s.log_scales, s.quats, s.opacity_logits, colour), device=dev)
+        r = api.Rasterizer(s.W, s.H, s.K, s.N, device=dev, sh_degree=deg)
+        r.plan(g, cams)
+        m = MappingStep(r, g, cams, rgb_t, depth_t, graph=True)
+        ms = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            m.replay()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        res["rgb" if deg is None else f"sh{deg}"] = round(1e3 / statistics.median(ms), 1)
+    return {"workload": "map100k mapping iteration (fwd + fused L1 + bwd, no optimiser step), L2 flushed",
+            "iters_per_s": res}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -641,6 +717,8 @@ def main():
             line["tracking"] = measure_tracking(dev)
             line["mapping_window"] = measure_window(dev)
             line["aerial"] = measure_aerial(dev)
+            line["time_to_psnr"] = measure_time_to_psnr(dev)
+            line["view_dependent_colour"] = measure_sh(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = oracle_step_rate(args.cpu_seconds)
         print(json.dumps(line))

@@ -314,12 +314,15 @@ GS_API gs_status_t gs_sort_diag_withheld_tile(uint64_t* keys, uint32_t* vals, in
 typedef struct {
   float lr_means, lr_log_scales, lr_quats, lr_opacity, lr_rgb;
   float beta1, beta2, eps;
+  int32_t color_width;  /* colour scalars per Gaussian: 3 for GS_COLOR_RGB, 3 (D+1)^2 for SH
+                           coefficients of degree D; 0 = 3 */
 } gs_adam_t;
 
-/* Floats of the Adam state of N Gaussians: m and v (14 values per Gaussian each, grouped as
- * means [N,3], log-scales [N,3], quaternions [N,4], opacity logits [N], colours [N,3]) and the
- * step count. The caller zeroes it before the first step. */
-GS_API gs_status_t gs_map_adam_state_size(int64_t N, int64_t* floats);
+/* Floats of the Adam state of N Gaussians whose colour has color_width scalars (0 = 3): m and v
+ * (11 + color_width values per Gaussian each, grouped as means [N,3], log-scales [N,3],
+ * quaternions [N,4], opacity logits [N], colours [N,color_width]) and the step count. The
+ * caller zeroes it before the first step. */
+GS_API gs_status_t gs_map_adam_state_size(int64_t N, int32_t color_width, int64_t* floats);
 
 /* One Adam step (Kingma & Ba; bias-corrected) of the mapping optimiser (Sec. II-B: the map is
  * updated from the comparison of rendered images with the key-frames) on the FP32 master arrays
@@ -329,8 +332,8 @@ GS_API gs_status_t gs_map_adam_state_size(int64_t N, int64_t* floats);
  * the updated values rounded to nearest, for the next render; an array equal to its master is
  * skipped. */
 GS_API gs_status_t gs_map_adam_step(int64_t N, float* means, float* log_scales, float* quats, float* opacity_logits,
-                             float* rgb, const gs_grads_t* grads, float* state, const gs_adam_t* hp,
-                             const gs_gaussians_t* storage, void* stream);
+                             float* rgb /* [N, hp->color_width] */, const gs_grads_t* grads, float* state,
+                             const gs_adam_t* hp, const gs_gaussians_t* storage, void* stream);
 
 /* Scratch bytes of gs_keyframe_insert for a width x height frame sampled every `stride` pixels. */
 GS_API gs_status_t gs_keyframe_tmp_size(int32_t width, int32_t height, int32_t stride, size_t* bytes);

@@ -50,7 +50,8 @@ class GsGrads(ctypes.Structure):
 
 class GsAdam(ctypes.Structure):
     _fields_ = [("lr_means", c_float), ("lr_log_scales", c_float), ("lr_quats", c_float), ("lr_opacity", c_float),
-                ("lr_rgb", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
+                ("lr_rgb", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
+                ("color_width", c_int32)]
 
 
 class GsWsLayout(ctypes.Structure):
@@ -99,7 +100,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                 "gs_sort_pairs_tmp_size": [c_int64, P],
                 "gs_sort_pairs": [P, P, c_int64, c_int32, P, c_size_t, P, P],
                 "gs_sort_pairs_noalloc": [P, P, c_int64, c_int32, P, P],
-                "gs_map_adam_state_size": [c_int64, P],
+                "gs_map_adam_state_size": [c_int64, c_int32, P],
                 "gs_map_adam_step": [c_int64, P, P, P, P, P, P, P, P, P, P],
                 "gs_keyframe_tmp_size": [c_int32, c_int32, c_int32, P],
                 "gs_keyframe_insert": [P, P, P, P, c_int32, c_int32, c_int32, c_float, c_float, c_float, c_float,

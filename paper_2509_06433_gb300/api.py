@@ -192,16 +192,18 @@ def gs_sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: int,
 
 # ----------------------------------------------------------------------------- the mapping loop
 
-def gs_map_adam_state_size(N: int) -> int:
+def gs_map_adam_state_size(N: int, color_width: int = 3) -> int:
     n = ctypes.c_int64()
-    call("gs_map_adam_state_size", ctypes.c_int64(N), ctypes.byref(n))
+    call("gs_map_adam_state_size", ctypes.c_int64(N), ctypes.c_int32(color_width), ctypes.byref(n))
     return n.value
 
 
 def gs_map_adam_step(masters: "Gaussians", grads: dict, state: torch.Tensor, lr: dict, beta1=0.9, beta2=0.999,
                      eps=1e-15, storage: "Gaussians" = None, stream=None):
     """One Adam step of the FP32 master arrays from ``grads``; refreshes ``storage`` if given."""
-    hp = GsAdam(lr["means"], lr["log_scales"], lr["quats"], lr["opacity_logits"], lr["rgb"], beta1, beta2, eps)
+    width = masters.rgb[0].numel() if masters.N else 3  # 3, or the SH coefficients' 3 (D+1)^2
+    hp = GsAdam(lr["means"], lr["log_scales"], lr["quats"], lr["opacity_logits"], lr["rgb"], beta1, beta2, eps,
+                width)
     gr = GsGrads(*(_p(grads.get(k)) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose")), 0)
     st = storage.struct() if storage is not None else None
     call("gs_map_adam_step", ctypes.c_int64(masters.N), _p(masters.means), _p(masters.log_scales), _p(masters.quats),
@@ -280,7 +282,8 @@ class MapOptimizer:
             self.storage = None
         else:
             self.storage = g
-        self.state = torch.zeros(gs_map_adam_state_size(g.N), device=g.means.device)
+        width = g.rgb[0].numel() if g.N else 3
+        self.state = torch.zeros(gs_map_adam_state_size(g.N, width), device=g.means.device)
         self.lr = dict(self.DEFAULT_LR, **(lr or {}))
         self.beta1, self.beta2, self.eps = beta1, beta2, eps
 

@@ -2,9 +2,10 @@
 // comparing rendered images with the key-frames): an Adam step of every Gaussian parameter on
 // FP32 master values, and the insertion of a key-frame's pixels as new Gaussians.
 //
-// Adam: one thread per scalar over the 14 values of every Gaussian (means 3, log-scales 3,
-// quaternion 4, opacity logit 1, colour 3), group by group, so every access is coalesced. The
-// state holds m and v in the same group layout (2 x 14 N floats) and, after them, the step
+// Adam: one thread per scalar over the 11 + w values of every Gaussian (means 3, log-scales 3,
+// quaternion 4, opacity logit 1, colour w: 3, or the spherical-harmonic coefficients), group by
+// group, so every access is coalesced. The state holds m and v in the same group layout
+// (2 x (11 + w) N floats) and, after them, the step
 // count as a float; a one-thread kernel advances the count after the update, so the step can
 // be replayed from a CUDA graph.
 //
@@ -193,7 +194,8 @@ extern "C" gs_status_t gs_map_adam_step(int64_t N, float* means, float* log_scal
   float* p[kGroups] = {means, log_scales, quats, opacity_logits, rgb};
   const float* g[kGroups] = {grads->means, grads->log_scales, grads->quats, grads->opacity_logits, grads->rgb};
   const float lr[kGroups] = {hp->lr_means, hp->lr_log_scales, hp->lr_quats, hp->lr_opacity, hp->lr_rgb};
-  const int width[kGroups] = {3, 3, 4, 1, 3};
+  if (hp->color_width < 0) return GS_ERR_INVALID_ARG;
+  const int width[kGroups] = {3, 3, 4, 1, hp->color_width > 0 ? hp->color_width : 3};
   const void* st[kGroups] = {storage ? storage->means : nullptr, storage ? storage->log_scales : nullptr,
                              storage ? storage->quats : nullptr, storage ? storage->opacity_logits : nullptr,
                              storage ? storage->rgb : nullptr};
@@ -227,9 +229,9 @@ extern "C" gs_status_t gs_map_adam_step(int64_t N, float* means, float* log_scal
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
-extern "C" gs_status_t gs_map_adam_state_size(int64_t N, int64_t* floats) {
-  if (N < 0 || !floats) return GS_ERR_INVALID_ARG;
-  *floats = 2 * 14 * N + 1;
+extern "C" gs_status_t gs_map_adam_state_size(int64_t N, int32_t color_width, int64_t* floats) {
+  if (N < 0 || color_width < 0 || !floats) return GS_ERR_INVALID_ARG;
+  *floats = 2 * (11 + static_cast<int64_t>(color_width > 0 ? color_width : 3)) * N + 1;
   return GS_OK;
 }
 

@@ -119,7 +119,7 @@ class MappingStep(_Captured):
         self.loss = torch.zeros(1, device=d)
         self.grads = {"means": torch.zeros((N, 3), device=d), "log_scales": torch.zeros((N, 3), device=d),
                       "quats": torch.zeros((N, 4), device=d), "opacity_logits": torch.zeros(N, device=d),
-                      "rgb": torch.zeros((N, 3), device=d), "pose": torch.zeros((K, 6), device=d)}
+                      "rgb": torch.zeros(r.color_shape(), device=d), "pose": torch.zeros((K, 6), device=d)}
         saved = self._snapshot()
         self._capture(self._iteration)
         self._restore(saved)  # the warm-up iterations stepped the optimiser: start from the given map

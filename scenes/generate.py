@@ -223,6 +223,34 @@ def _room_walk(rng, K, W, H, f):
     return cams
 
 
+def _smooth_texture(rng, means, waves=6, amp=0.1, cycles=(0.3, 2.5), noise=0.02):
+    """Colour as a smooth function of the position: 0.5 + a sum of plane waves per channel
+    (random directions, 0.3 to 2.5 cycles per metre) + a little per-Gaussian noise, clipped to
+    [0, 1]. Neighbouring Gaussians then have similar colours, like a photographed surface, so
+    views of the map agree with one another whatever the compositing order of close splats."""
+    p = np.asarray(means, np.float64)
+    out = np.full((len(p), 3), 0.5)
+    for c in range(3):
+        for _ in range(waves):
+            d = rng.normal(size=3)
+            k = d / np.linalg.norm(d) * rng.uniform(*cycles) * 2 * math.pi
+            out[:, c] += amp * np.sin(p @ k + rng.uniform(0, 2 * math.pi))
+    out += rng.normal(0, noise, out.shape)
+    return np.clip(out, 0.0, 1.0)
+
+
+def _turn(rng, K, W, H, f, degrees=90.0):
+    """K views from the middle of the room turning by `degrees` of yaw in equal steps."""
+    pos = np.array([4.0, 3.0, 1.5])
+    yaw0 = rng.uniform(0, 2 * math.pi)
+    cams = []
+    for i in range(K):
+        yaw = yaw0 + math.radians(degrees) * i / max(K - 1, 1)
+        R, t = look_at(pos, np.array([math.cos(yaw), math.sin(yaw), 0.0]))
+        cams.append(camera_array(f, f, W / 2.0, H / 2.0, R, t))
+    return cams
+
+
 def _aerial(rng, n):
     """Ground plane plus 40 boxes; 20% large semi-transparent Gaussians."""
     n_large = n // 5
@@ -278,6 +306,7 @@ SCENE_CONFIGS = {
     "track300k": (1002, 300_000, 1, 640, 480, 525.0, "f32"),
     "window500k": (1003, 500_000, 8, 640, 480, 525.0, "bf16"),
     "aerial2m": (1004, 2_000_000, 16, 1280, 720, 900.0, "f16"),
+    "turn_room": (1005, 500_000, 10, 672, 376, 260.0, "f32"),
 }
 
 
@@ -291,6 +320,9 @@ def make_scene(name: str, seed: int | None = None, n: int | None = None, K: int 
     track300k  : the map100k mixture; ``track_cams`` = pose perturbed by 2 deg / 5 cm.
     window500k : 6 walls of a room + 10% free; K views on a 0.3 m / +-10 deg yaw walk.
     aerial2m   : ground + 40 boxes + 20% large translucent; K views at 3-10 m, 20 deg tilt.
+    turn_room  : the window500k room with a smooth colour texture; K views (672 x 376) from its
+                 middle turning by 90 deg of yaw: the key-frame sequence of a robot's turn,
+                 rendered from this map.
     """
     dseed, dn, dK, dW, dH, df, _ = SCENE_CONFIGS[name]
     seed = dseed if seed is None else seed
@@ -318,6 +350,10 @@ def make_scene(name: str, seed: int | None = None, n: int | None = None, K: int 
         s = _to_scene(d, _room_walk(rng, K, W, H, f), W, H, name)
         s.target = _perturbed_copy(rng, s)
         return s
+    if name == "turn_room":
+        d = _room(rng, n)
+        d["rgb"] = _smooth_texture(rng, d["means"])
+        return _to_scene(d, _turn(rng, K, W, H, f), W, H, name)
     if name == "aerial2m":
         d = _aerial(rng, n)
         s = _to_scene(d, _aerial_path(rng, K, W, H, f), W, H, name)

@@ -14,17 +14,20 @@ pytestmark = pytest.mark.gpu
 LR = {"means": 1e-3, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 5e-2, "rgb": 2.5e-3}
 
 
-def test_adam_steps_match_the_oracle():
+@pytest.mark.parametrize("color_width", [3, 48])  # RGB, or SH coefficients of degree 3
+def test_adam_steps_match_the_oracle(color_width):
     torch, api = torch_mods()
     rng = np.random.default_rng(0)
     N = 3001
+    widths = om.WIDTHS[:-1] + (color_width,)
     p0 = {k: rng.normal(size=(N, w)).astype(np.float32).reshape((N,) if w == 1 else (N, w))
-          for k, w in zip(om.GROUPS, om.WIDTHS)}
+          for k, w in zip(om.GROUPS, widths)}
     masters = api.Gaussians(*(torch.as_tensor(p0[k]).cuda() for k in om.GROUPS))
     store = api.Gaussians(masters.means.clone(), *(masters_t.to(torch.bfloat16) for masters_t in
                                                     (masters.log_scales, masters.quats, masters.opacity_logits,
                                                      masters.rgb)))
-    state = torch.zeros(api.gs_map_adam_state_size(N), device="cuda")
+    state = torch.zeros(api.gs_map_adam_state_size(N, color_width), device="cuda")
+    assert state.numel() == 2 * (11 + color_width) * N + 1
     ref = {k: p0[k].astype(np.float64) for k in om.GROUPS}
     m = {k: np.zeros_like(v) for k, v in ref.items()}
     v = {k: np.zeros_like(x) for k, x in ref.items()}

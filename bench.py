@@ -601,6 +601,97 @@ def measure_sh(dev, reps=20):
             "iters_per_s": res}
 
 
+def measure_viewer(dev, frames=300, views=2):
+    """Viewer concurrency (Sec. III-IV: two processes on one GPU share the map over CUDA IPC; the
+    viewer reaches 30 FPS without slowing map generation). The map100k mapping iteration with
+    its Adam step (one graph; the map lives in an IPC-shared buffer and is published after every
+    iteration) runs alone, then while a second process renders the shared map from `views`
+    viewpoints (a stereo pair) at 672x376 and synchronises every frame. The viewer is also run
+    with the mapper idle. Rates are wall-clock over blocks of 20 iterations with a device
+    synchronisation after each block."""
+    import tempfile
+
+    import torch
+    from paper_2509_06433_gb300 import api, ipc
+    from paper_2509_06433_gb300.tracking import MappingStep
+    from scenes import make_scene
+    s = make_scene("map100k")
+    shared = ipc.SharedMap(s.N, device=dev)
+    shared.load(api.Gaussians.from_numpy(s.params(), device=dev))
+    cams = torch.as_tensor(s.cams).to(dev)
+    r = api.Rasterizer(s.W, s.H, 1, s.N, device=dev)
+    gt = api.Gaussians.from_numpy(s.target.params(), device=dev)
+    r.plan(gt, cams)
+    tgt = r.render(gt, cams)
+    rgb_t, depth_t = tgt["rgb"].clone(), tgt["depth"].clone()
+    r.plan(shared.g, cams, headroom=1.5)
+    step = MappingStep(r, shared.g, cams, rgb_t, depth_t, graph=True, optimizer=api.MapOptimizer(shared.g))
+
+    def block(n=20):
+        for _ in range(n):
+            step.replay()
+            shared.publish()
+
+    def mapping_rate(stop):
+        it, t0 = 0, time.perf_counter()
+        while True:
+            block()
+            torch.cuda.synchronize(dev)
+            it += 20
+            if stop(it):
+                return it / (time.perf_counter() - t0)
+
+    block()
+    torch.cuda.synchronize(dev)
+    alone = mapping_rate(lambda it: it >= 600)
+    tmp = tempfile.mkdtemp(prefix="gs_viewer_")
+    desc = os.path.join(tmp, "map.json")
+    with open(desc, "w") as fh:
+        json.dump(shared.descriptor(), fh)
+    here = os.path.dirname(os.path.abspath(__file__))
+
+    def viewer(tag):
+        out, ready = os.path.join(tmp, tag + ".json"), os.path.join(tmp, tag + ".ready")
+        cmd = [sys.executable, "-m", "paper_2509_06433_gb300.viewer", "--desc", desc, "--out", out, "--ready", ready,
+               "--frames", str(frames), "--views", str(views)]
+        env = dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", str(dev.index or 0)))
+        return subprocess.Popen(cmd, cwd=here, env=env, stdout=subprocess.DEVNULL, stderr=subprocess.PIPE), out, ready
+
+    def wait_for(path, proc, limit=240.0):
+        t0 = time.time()
+        while not os.path.exists(path):
+            if proc.poll() is not None and not os.path.exists(path):
+                raise RuntimeError("viewer failed: " + proc.stderr.read().decode(errors="replace")[-1500:])
+            if time.time() - t0 > limit:
+                proc.kill()  # our own child
+                raise RuntimeError("viewer timed out")
+            time.sleep(0.02)
+
+    try:
+        proc, out, ready = viewer("idle")  # viewer alone (mapper idle)
+        wait_for(out, proc)
+        proc.wait(timeout=60)
+        with open(out) as fh:
+            v_alone = json.load(fh)
+        proc, out, ready = viewer("busy")  # viewer while the mapper runs
+        wait_for(ready, proc)
+        during = mapping_rate(lambda it: os.path.exists(out))
+        proc.wait(timeout=60)
+        with open(out) as fh:
+            v_busy = json.load(fh)
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line instead of failing the bench
+        shared.close()
+        return {"error": str(e)[-500:]}
+    shared.close()
+    return {"workload": f"map100k mapping iteration with Adam (one graph) in one process; a viewer process "
+                        f"rendering the IPC-shared map from {views} viewpoints at 672x376 every frame",
+            "mapping_iters_per_s_alone": round(alone, 1), "mapping_iters_per_s_with_viewer": round(during, 1),
+            "mapping_slowdown": round(alone / during, 3) if during else None,
+            "viewer_fps_alone": round(v_alone["fps"], 1), "viewer_fps_during_mapping": round(v_busy["fps"], 1),
+            "viewer_frame_ms_median": round(v_busy["frame_ms_median"], 3), "viewer_frames": frames,
+            "viewer_device_error": v_busy["device_error_word"]}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -719,6 +810,7 @@ def main():
             line["aerial"] = measure_aerial(dev)
             line["time_to_psnr"] = measure_time_to_psnr(dev)
             line["view_dependent_colour"] = measure_sh(dev)
+            line["viewer_ipc"] = measure_viewer(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = oracle_step_rate(args.cpu_seconds)
         print(json.dumps(line))

@@ -379,6 +379,53 @@ GS_API gs_status_t gs_ssim(const float* x, const float* y, int32_t images, int32
                            int32_t width, float data_range, float* ssim, float* ssim_map, void* tmp, size_t tmp_bytes,
                            void* stream);
 
+/* ---------------------------------------------------------------- shared map over CUDA IPC
+ *
+ * Sec. III (Fig. 5) runs the map optimiser and the interactive viewer as two processes on one
+ * GPU, each with its own renderer, both reading the Gaussian map where it lives in GPU memory
+ * through CUDA IPC. The exporting process shares a device range (e.g. one buffer holding the
+ * five Gaussian arrays) and an interprocess event; the importing process maps the range and
+ * orders its reads after the exporter's updates with the event.
+ *
+ * Ordering rule: the exporter records the event on its stream after an update of the map
+ * (gs_ipc_event_record); the importer enqueues gs_ipc_stream_wait before a render, which then
+ * starts after the last update recorded before that wait was enqueued. The exporter is never
+ * held back: an update enqueued after that record may run while the importer reads, so a
+ * render can mix two consecutive updates (the paper does not say how its processes
+ * synchronise; this is the non-blocking reading). Both processes must use the same GPU. */
+
+typedef struct { uint8_t bytes[128]; } gs_ipc_mem_handle_t;  /* opaque; plain bytes, may be sent
+                                                                between processes as is */
+typedef struct { uint8_t bytes[64]; } gs_ipc_event_handle_t; /* opaque; plain bytes */
+
+/* Shares bytes [d_ptr, d_ptr + bytes) of a device allocation made with cudaMalloc (d_ptr may
+ * point inside it). GS_ERR_INVALID_ARG if the range leaves the allocation; GS_ERR_CUDA if CUDA
+ * refuses (e.g. memory from a virtual-memory or managed allocator). The exporter keeps the
+ * allocation alive while importers use it. */
+GS_API gs_status_t gs_ipc_export(const void* d_ptr, size_t bytes, gs_ipc_mem_handle_t* out);
+
+/* In another process: maps the shared range; *d_ptr receives its address in this process and
+ * *bytes (may be NULL) its size. A handle cannot be imported by the process that exported it. */
+GS_API gs_status_t gs_ipc_import(const gs_ipc_mem_handle_t* handle, void** d_ptr, size_t* bytes);
+
+/* Unmaps a range from gs_ipc_import (d_ptr as returned by it). */
+GS_API gs_status_t gs_ipc_release(void* d_ptr);
+
+/* Creates an interprocess event (cudaEvent_t, timing disabled) in *event and its handle. */
+GS_API gs_status_t gs_ipc_event_create(void** event, gs_ipc_event_handle_t* out);
+
+/* In another process: opens the event of a handle; *event is a cudaEvent_t of this process. */
+GS_API gs_status_t gs_ipc_event_open(const gs_ipc_event_handle_t* handle, void** event);
+
+/* Records the event on `stream` (exporter: after an update of the map). */
+GS_API gs_status_t gs_ipc_event_record(void* event, void* stream);
+
+/* Makes `stream` wait for the event's last record (importer: before a render). */
+GS_API gs_status_t gs_ipc_stream_wait(void* stream, void* event);
+
+/* Destroys an event from gs_ipc_event_create or gs_ipc_event_open. */
+GS_API gs_status_t gs_ipc_event_destroy(void* event);
+
 /* Largest n accepted by gs_sort_pairs_noalloc. */
 #define GS_SORT_NOALLOC_MAX_PAIRS 1048576
 

@@ -28,7 +28,9 @@ EXPORTS = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_pro
            "gs_raster_fwd", "gs_raster_fwd_stats", "gs_raster_fwd_l1", "gs_raster_fwd_occluded", "gs_loss_l1", "gs_raster_bwd", "gs_project_bwd", "gs_screen_grads",
            "gs_pose_adam_step", "gs_sort_pairs_tmp_size", "gs_sort_pairs", "gs_sort_diag_withheld_tile",
            "gs_sort_pairs_noalloc", "gs_map_adam_state_size", "gs_map_adam_step", "gs_keyframe_tmp_size",
-           "gs_keyframe_insert", "gs_metrics_tmp_size", "gs_psnr", "gs_ssim")
+           "gs_keyframe_insert", "gs_metrics_tmp_size", "gs_psnr", "gs_ssim",
+           "gs_ipc_export", "gs_ipc_import", "gs_ipc_release", "gs_ipc_event_create", "gs_ipc_event_open",
+           "gs_ipc_event_record", "gs_ipc_stream_wait", "gs_ipc_event_destroy")
 
 
 class GsConfig(ctypes.Structure):
@@ -108,6 +110,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
                 "gs_metrics_tmp_size": [c_int32, c_int32, c_int32, c_int32, P],
                 "gs_psnr": [P, P, c_int32, c_int32, c_int32, c_int32, c_float, P, P, c_size_t, P],
                 "gs_ssim": [P, P, c_int32, c_int32, c_int32, c_int32, c_float, P, P, P, c_size_t, P],
+                "gs_ipc_export": [P, c_size_t, P],
+                "gs_ipc_import": [P, P, P],
+                "gs_ipc_release": [P],
+                "gs_ipc_event_create": [P, P],
+                "gs_ipc_event_open": [P, P],
+                "gs_ipc_event_record": [P, P],
+                "gs_ipc_stream_wait": [P, P],
+                "gs_ipc_event_destroy": [P],
                 "gs_sort_diag_withheld_tile": [P, P, c_int64, P, c_size_t, P, P],
                 "gs_pose_adam_step": [P, P, P, c_int32, c_float, c_float, c_float, c_float, c_float, c_int32, P],
             }

@@ -717,19 +717,28 @@ def _keys(d):
 
 
 def measured_traffic(stage):
-    """DRAM bytes per launch of `stage` from the committed ncu summary, or None when the
-    kernel's source has changed since the capture."""
-    import hashlib
+    """DRAM bytes per launch of `stage` from the committed ncu summary, or None when one of the
+    kernel's source files has changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic_map100k.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         f = line.split()
         if len(f) == 4 and not line.startswith("#") and f[0] == stage:
-            src = os.path.join(ROOT, f[1])
-            if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == f[2]:
+            srcs = [os.path.join(ROOT, x) for x in f[1].split(",")]
+            if all(os.path.exists(x) for x in srcs) and sources_sha256(srcs) == f[2]:
                 return int(f[3])
     return None
+
+
+def sources_sha256(paths):
+    """sha256 of the concatenated bytes of the files a kernel is built from, in the given order."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def roofline(stage, ms_list, counts, pairs, s, r):

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
       if (!(S.rows[j] & wrows)) continue;
       const float4 A = S.A[j], B = S.B[j];
       const float dx = __fsub_rn(A.x, pxc);
-      const float qadx = __fmul_rn(A.z, dx);
+      const Column col = splat_column(A, B, dx);
       const int pos = pos0 + j;
       // phase 1: opacity and keep/skip decision for the thread's pixels
       Alpha a[PX];
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
 #pragma unroll
       for (int q = 0; q < PX; ++q) {
         dy[q] = __fsub_rn(A.y, pyc + static_cast<float>(q));
-        a[q] = splat_alpha(A, B, qadx, dx, dy[q]);
+        a[q] = splat_alpha(B, col, dy[q]);
         okq[q] = a[q].keep && (pos < last[q]);
         contrib = contrib || okq[q];
       }

@@ -40,7 +40,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Staged splat: A = (x, y, qa, qb), B = (qc, opacity, depth, -), C = (r, g, b, -) where
+// Staged splat: A = (x, y, qa, qb), B = (qc, opacity, depth, log2 opacity), C = (r, g, b, -) where
 // (x, y) is the 2D mean relative to the tile origin and power * log2(e) = qa dx^2 + qb dx dy + qc dy^2.
 // rows: bit r is set when the splat's ellipse {opacity * 2^power >= 1/255}, widened by a safety
 // margin, meets the pixel-centre row y = r + 0.5 of the tile within the columns [0.5, 15.5].
@@ -99,25 +99,38 @@ __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layou
   const float x = __fadd_rn(__fsub_rn(uv.x, ox), uv.y), y = __fadd_rn(__fsub_rn(uv.z, oy), uv.w);
   const float qa = __fmul_rn(cn.x, -0.5f * kLog2e), qb = __fmul_rn(cn.y, -kLog2e), qc = __fmul_rn(cn.z, -0.5f * kLog2e);
   S.A[j] = make_float4(x, y, qa, qb);
-  S.B[j] = make_float4(qc, co.w, cn.w, 0.0f);
+  S.B[j] = make_float4(qc, co.w, cn.w, __log2f(co.w));
   S.C[j] = make_float4(co.x, co.y, co.z, 0.0f);
   S.rows[j] = splat_rows(x, y, -qa, -qb, -qc, co.w);
   return gid;
 }
 
-// Opacity of a splat at pixel offset (dx, dy) with qadx = qa * dx. keep: the splat is not
-// skipped (power <= 0 and alpha >= 1/255). G = exp(power); raw = opacity * G before the clamp.
+// Opacity of a splat at a pixel, in one form shared by every compositing kernel, so that they
+// all take the same decisions. For the pixel column at offset dx from the splat's mean, a lane
+// forms once per splat (splat_column)
+//   c1 = qb dx,   c0 = qa dx^2 + log2(opacity),
+// and per pixel row at offset dy the exponent  e = (qc dy + c1) dy + c0 = power log2(e) + log2(o),
+// so raw = 2^e = opacity * exp(power) costs two FMAs and one ex2. keep: the splat is not skipped
+// (power <= 0, i.e. e <= log2(o), and alpha >= 1/255); raw is the opacity before the 0.99 clamp.
+struct Column {
+  float c0, c1;
+};
+__device__ __forceinline__ Column splat_column(const float4& A, const float4& B, float dx) {
+  return {__fmaf_rn(__fmul_rn(A.z, dx), dx, B.w), __fmul_rn(A.w, dx)};
+}
+__device__ __forceinline__ float splat_exponent(const float4& B, Column c, float dy) {
+  return __fmaf_rn(__fmaf_rn(B.x, dy, c.c1), dy, c.c0);
+}
 struct Alpha {
-  float alpha, G, raw;
+  float alpha, raw;
   bool keep;
 };
-__device__ __forceinline__ Alpha splat_alpha(const float4& A, const float4& B, float qadx, float dx, float dy) {
+__device__ __forceinline__ Alpha splat_alpha(const float4& B, Column c, float dy) {
   Alpha r;
-  const float p = __fmaf_rn(dx, __fmaf_rn(A.w, dy, qadx), __fmul_rn(__fmul_rn(B.x, dy), dy));
-  r.G = ex2_approx(p);
-  r.raw = __fmul_rn(B.y, r.G);
+  const float e = splat_exponent(B, c, dy);
+  r.raw = ex2_approx(e);
   r.alpha = fminf(r.raw, kAlphaMax);
-  r.keep = (p <= 0.0f) && (r.alpha >= kAlphaMin);
+  r.keep = (e <= B.w) && (r.alpha >= kAlphaMin);
   return r;
 }
 

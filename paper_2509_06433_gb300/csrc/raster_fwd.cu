@@ -78,6 +78,23 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
     if (OCC && !outside) zmax[q] = O.depth[tc.k * static_cast<int64_t>(L.H) * L.W + static_cast<int64_t>(py + q) * L.W + px];
     all_done = all_done && outside;
   }
+  // the loss targets of the thread's pixels, loaded now so that the loads overlap the compositing
+  float tgt[LOSS ? PX : 1][4];
+  if (LOSS) {
+    const int64_t HW = static_cast<int64_t>(L.H) * L.W;
+#pragma unroll
+    for (int q = 0; q < PX; ++q) {
+      tgt[q][0] = tgt[q][1] = tgt[q][2] = tgt[q][3] = 0.0f;
+      if (px < L.W && py + q < L.H) {
+        const int64_t pix = static_cast<int64_t>(py + q) * L.W + px;
+        const int64_t c0 = static_cast<int64_t>(tc.k) * 3 * HW + pix;
+        tgt[q][0] = __ldg(F.rgb_t + c0);
+        tgt[q][1] = __ldg(F.rgb_t + c0 + HW);
+        tgt[q][2] = __ldg(F.rgb_t + c0 + 2 * HW);
+        tgt[q][3] = __ldg(F.depth_t + tc.k * HW + pix);
+      }
+    }
+  }
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     if (__syncthreads_count(!all_done) == 0) break;
     for (int jj = threadIdx.x; jj < CH; jj += kThreads) {
@@ -97,16 +114,16 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
       if (!(S.rows[j] & wrows)) continue;
       const float4 A = S.A[j], B = S.B[j], C = S.C[j];
       const float dx = __fsub_rn(A.x, pxc);
-      const float qadx = __fmul_rn(A.z, dx);
+      const Column col = splat_column(A, B, dx);
       const int pos = pos0 + j;
 #pragma unroll
       for (int q = 0; q < PX; ++q) {
         // pixel-centre offsets are formed the same way whatever PX is, so every variant
         // takes bit-identical decisions
         const float dy = __fsub_rn(A.y, pyc + static_cast<float>(q));
-        const float p = __fmaf_rn(dx, __fmaf_rn(A.w, dy, qadx), __fmul_rn(__fmul_rn(B.x, dy), dy));
-        const float alpha = fminf(__fmul_rn(B.y, ex2_approx(p)), kAlphaMax);
-        bool keep = (p <= 0.0f) && (alpha >= amin[q]);
+        const float e = splat_exponent(B, col, dy);
+        const float alpha = fminf(ex2_approx(e), kAlphaMax);
+        bool keep = (e <= B.w) && (alpha >= amin[q]);
         bool behind = false;
         if (OCC) {
           behind = B.z >= zmax[q];  // B.z: the splat's camera depth
@@ -166,11 +183,11 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
         const float c[3] = {cr[q], cg[q], cb[q]};
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-          const float d = c[ch] - F.rgb_t[c0 + ch * HW];
+          const float d = c[ch] - tgt[LOSS ? q : 0][ch];
           loss += fabsf(d) * inv3;
           F.g_rgb[c0 + ch * HW] = sgn(d) * inv3;
         }
-        const float d = cd[q] - F.depth_t[tc.k * HW + pix];
+        const float d = cd[q] - tgt[LOSS ? q : 0][3];
         loss += fabsf(d) * invd;
         F.g_depth[tc.k * HW + pix] = sgn(d) * invd;
       }

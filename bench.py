@@ -7,9 +7,9 @@ gs_project_bwd, gradients for every Gaussian parameter and the camera pose.
 
 Prints one JSON line. `value` is mapping iterations/s with inputs resident in HBM, timed
 with CUDA events per step, L2 flushed (256 MB write) between steps outside the timed
-region. `e2e` is the same metric through the same C ABI calls with the step's inputs
-copied from pinned host memory and the gradients and loss copied back inside the timed
-region. `--impl reference` times the FP64 CPU oracle on the same workload instead.
+region. `e2e` is the same metric through the public API with host buffers
+(tracking.HostMappingStep): every step copies the Gaussians, camera and targets from pinned
+host memory and the gradients and loss back, inside the timed region. `--impl reference` times the FP64 CPU oracle on the same workload instead.
 
 Multi-GPU (torchrun, N ranks): the path is replicated, one independent mapping step per
 rank ("replicas only", weak scaling); value = steps over all ranks / max rank time.
@@ -65,7 +65,7 @@ def workload_config():
     return {"workload": f"{WORKLOAD}: {n} Gaussians (50% free in [-2,2]^2x[2,8] m, 50% on 3 planes), "
                         f"{K} view {W}x{H} f={f:g}, fwd+bwd with L1(RGB)+0.1 L1(depth) vs perturbed-scene target",
             "N": n, "K": K, "width": W, "height": H, "seed": seed, "storage": "f32", "tile": 16,
-            "l2": "flushed between timed steps (256 MB write)"}
+            "l2": "flushed between timed steps (256 MB write), for value and e2e"}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -243,42 +243,27 @@ def run_ours(args, rank, world):
         if not torch.equal(grads[k], mstep.grads[k]):
             raise RuntimeError(f"graph replay and eager step disagree on {k}")
 
-    # ---- end to end through the C ABI: pinned host inputs in, gradients + loss out
-    host_in = [torch.as_tensor(a).pin_memory() for a in s.params()]
-    host_tgt = [rgb_t.cpu().pin_memory(), depth_t.cpu().pin_memory()]
-    dev_in = [x.to(dev) for x in host_in]
-    dev_tgt = [x.to(dev) for x in host_tgt]
-    host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in grads.items()}
-    host_loss = torch.empty(1, pin_memory=True)
-    ge = api.Gaussians(*dev_in)
-    h2d = sum(x.numel() * x.element_size() for x in host_in + host_tgt)
-    d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 4
-
-    def e2e_step():
-        for d, h in zip(dev_in + dev_tgt, host_in + host_tgt):
-            d.copy_(h, non_blocking=True)
-        zero_grads()
-        api.gs_project(cfg, ge, cams, ws, stream)
-        api.gs_bin_sort(cfg, ws, stream)
-        api.gs_raster_fwd_l1(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], dev_tgt[0], dev_tgt[1], g_rgb,
-                             g_depth, loss, stream)
-        api.gs_raster_bwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth, None, stream)
-        api.gs_project_bwd(cfg, ge, cams, ws, grads, stream, overwrite=True)
-        for k, v in grads.items():
-            host_out[k].copy_(v, non_blocking=True)
-        host_loss.copy_(loss, non_blocking=True)
-
+    # ---- end to end through the public API: pinned host inputs in, gradients + loss out, every
+    # step (tracking.HostMappingStep: the copies and the iteration replay as one CUDA graph)
+    from paper_2509_06433_gb300.tracking import HostMappingStep
+    host_g = api.Gaussians(*(torch.as_tensor(a) for a in s.params()))
+    hstep = HostMappingStep(r, host_g, cams.cpu(), rgb_t.cpu(), depth_t.cpu(), graph=True)
+    h2d, d2h = hstep.transfer_bytes()
     for _ in range(max(3, args.warmup)):
-        e2e_step()
+        hstep.replay()
+    torch.cuda.synchronize(dev)
+    e2e_loss = hstep.host_out["loss"].item()
+    assert abs(e2e_loss - mstep.loss.item()) <= 1e-6 * max(1.0, abs(e2e_loss)), (e2e_loss, mstep.loss.item())
     e2e_steps = max(10, args.steps // 2)
+    eb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
+    for i in range(e2e_steps):
+        flush.fill_(float(i))  # L2 flushed between steps, outside the events, as for `value`
+        eb[i][0].record(stream)
+        hstep.replay()
+        eb[i][1].record(stream)
     barrier()
-    e2e_ms = replicas.max_over_ranks(e0.elapsed_time(e1), dev)
+    e2e_ms = replicas.max_over_ranks(float(sum(a.elapsed_time(b) for a, b in eb)), dev)
 
     # ---- the full mapping iteration with the optimiser (Adam step of the map inside the graph)
     adam = None

@@ -116,13 +116,17 @@ class MappingStep(_Captured):
         self.out = r.new_outputs()
         self.g_rgb = torch.empty_like(self.out["rgb"])
         self.g_depth = torch.empty_like(self.out["depth"])
-        self.loss = torch.zeros(1, device=d)
-        self.grads = {"means": torch.zeros((N, 3), device=d), "log_scales": torch.zeros((N, 3), device=d),
-                      "quats": torch.zeros((N, 4), device=d), "opacity_logits": torch.zeros(N, device=d),
-                      "rgb": torch.zeros(r.color_shape(), device=d), "pose": torch.zeros((K, 6), device=d)}
+        self.grads, self.loss = self._alloc_grads(r, N, K, d)
         saved = self._snapshot()
         self._capture(self._iteration)
         self._restore(saved)  # the warm-up iterations stepped the optimiser: start from the given map
+
+    @staticmethod
+    def _alloc_grads(r, N, K, d):
+        grads = {"means": torch.zeros((N, 3), device=d), "log_scales": torch.zeros((N, 3), device=d),
+                 "quats": torch.zeros((N, 4), device=d), "opacity_logits": torch.zeros(N, device=d),
+                 "rgb": torch.zeros(r.color_shape(), device=d), "pose": torch.zeros((K, 6), device=d)}
+        return grads, torch.zeros(1, device=d)
 
     def _tensors(self):
         if self.optimizer is None:
@@ -150,3 +154,87 @@ class MappingStep(_Captured):
         api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, self.grads, overwrite=True)
         if self.optimizer is not None:
             self.optimizer.step(self.grads)
+
+
+class HostMappingStep(MappingStep):
+    """A mapping iteration fed from host memory, for callers whose map and key-frames live on
+    the host: every replay copies the Gaussians, the cameras and the key-frame targets from
+    pinned host buffers to the device, runs the iteration (render with the fused L1 loss,
+    backward to every parameter and the poses) and copies the gradients and the loss back to
+    pinned host buffers; copies and kernels are one CUDA graph.
+
+    The Gaussians and cameras travel as one packed buffer each way and the gradients with the
+    loss as one, so a replay makes three host-to-device copies (the targets on a side stream,
+    overlapping the projection and binning) and one device-to-host copy.
+
+    Fill the tensors of ``host_in`` (views of the pinned buffers: the five Gaussian arrays,
+    ``cams``, ``rgb_t``, ``depth_t``) before ``replay()``; ``host_out`` (the gradients and
+    ``loss``) is valid once the stream has synchronised."""
+
+    _IN = ("means", "log_scales", "quats", "opacity_logits", "rgb", "cams")
+
+    def __init__(self, r: api.Rasterizer, host_gaussians: api.Gaussians, host_cams: torch.Tensor,
+                 host_rgb_t: torch.Tensor, host_depth_t: torch.Tensor, graph=True):
+        d = torch.device("cuda", torch.cuda.current_device()) if r.device.index is None else r.device
+        src = {k: getattr(host_gaussians, k) for k in self._IN[:5]}
+        src["cams"] = host_cams
+        shapes = {k: tuple(v.shape) for k, v in src.items()}
+        sizes = {k: int(torch.Size(v).numel()) for k, v in shapes.items()}
+        total = sum(sizes.values())
+        self._h_pack = torch.empty(total, dtype=torch.float32, pin_memory=True)
+        self._d_pack = torch.empty(total, dtype=torch.float32, device=d)
+        self.host_in, self.dev_in, off = {}, {}, 0
+        for k in self._IN:
+            self.host_in[k] = self._h_pack[off:off + sizes[k]].view(shapes[k])
+            self.dev_in[k] = self._d_pack[off:off + sizes[k]].view(shapes[k])
+            self.host_in[k].copy_(src[k].reshape(shapes[k]))
+            off += sizes[k]
+        for k, v in (("rgb_t", host_rgb_t), ("depth_t", host_depth_t)):
+            self.host_in[k] = v.contiguous().float().pin_memory()
+            self.dev_in[k] = torch.empty_like(self.host_in[k], device=d)
+        self._d_pack.copy_(self._h_pack)
+        for k in ("rgb_t", "depth_t"):
+            self.dev_in[k].copy_(self.host_in[k])
+        self._side = torch.cuda.Stream(device=d)
+        g = api.Gaussians(*(self.dev_in[k] for k in self._IN[:5]))
+        super().__init__(r, g, self.dev_in["cams"], self.dev_in["rgb_t"], self.dev_in["depth_t"], graph=graph)
+
+    def _alloc_grads(self, r, N, K, d):
+        # gradients and loss as views of one device buffer, mirrored by one pinned host buffer
+        shapes = {"means": (N, 3), "log_scales": (N, 3), "quats": (N, 4), "opacity_logits": (N,),
+                  "rgb": tuple(r.color_shape()), "pose": (K, 6), "loss": (1,)}
+        total = sum(int(torch.Size(v).numel()) for v in shapes.values())
+        self._d_out = torch.zeros(total, device=d)
+        self._h_out = torch.zeros(total, pin_memory=True)
+        views, self.host_out, off = {}, {}, 0
+        for k, shp in shapes.items():
+            n = int(torch.Size(shp).numel())
+            views[k] = self._d_out[off:off + n].view(shp)
+            self.host_out[k] = self._h_out[off:off + n].view(shp)
+            off += n
+        loss = views.pop("loss")
+        return views, loss
+
+    def _iteration(self):
+        r, o = self.r, self.out
+        main = torch.cuda.current_stream()
+        # the key-frame targets are needed only by the forward: they are copied on a side stream
+        # while the Gaussians and cameras go first and the projection and binning run
+        self._side.wait_stream(main)
+        with torch.cuda.stream(self._side):
+            for k in ("rgb_t", "depth_t"):
+                self.dev_in[k].copy_(self.host_in[k], non_blocking=True)
+        self._d_pack.copy_(self._h_pack, non_blocking=True)
+        api.gs_project(r.cfg, self.g, self.cams, r.ws)
+        api.gs_bin_sort(r.cfg, r.ws)
+        main.wait_stream(self._side)
+        api.gs_raster_fwd_l1(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.rgb_t, self.depth_t,
+                             self.g_rgb, self.g_depth, self.loss)
+        api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
+        api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, self.grads, overwrite=True)
+        self._h_out.copy_(self._d_out, non_blocking=True)
+
+    def transfer_bytes(self):
+        """(host-to-device, device-to-host) bytes per replay."""
+        h2d = 4 * (self._h_pack.numel() + self.host_in["rgb_t"].numel() + self.host_in["depth_t"].numel())
+        return h2d, 4 * self._h_out.numel()

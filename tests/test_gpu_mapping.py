@@ -111,3 +111,36 @@ def test_keyframe_insertion_matches_the_oracle():
                            cap - 5, count, stride=3)
     torch.cuda.synchronize()
     assert int(count.item()) == 5
+
+
+def test_host_mapping_step_equals_device_step():
+    """HostMappingStep (copies from pinned host buffers, the iteration, copies back; one graph)
+    returns the device MappingStep's gradients and loss bit for bit, and follows new host inputs."""
+    torch, api = torch_mods()
+    from paper_2509_06433_gb300.tracking import HostMappingStep, MappingStep
+    s = make_scene("map100k", n=20_000, W=160, H=120, f=130.0)
+    t = s.target
+    cams = torch.as_tensor(s.cams).cuda()
+    r = api.Rasterizer(s.W, s.H, 1, s.N)
+    gt = api.Gaussians.from_numpy(t.params())
+    r.plan(gt, cams)
+    tgt = r.render(gt, cams)
+    rgb_t, depth_t = tgt["rgb"].clone(), tgt["depth"].clone()
+    g = api.Gaussians.from_numpy(s.params())
+    r.plan(g, cams)
+    dev = MappingStep(r, g, cams, rgb_t, depth_t, graph=True)
+    dev.replay()
+    host = HostMappingStep(r, api.Gaussians(*(torch.as_tensor(a) for a in s.params())), cams.cpu(), rgb_t.cpu(),
+                           depth_t.cpu(), graph=True)
+    host.replay()
+    torch.cuda.synchronize()
+    for k, v in dev.grads.items():
+        assert torch.equal(host.host_out[k], v.cpu()), k
+    assert host.host_out["loss"].item() == dev.loss.item()
+    # new host inputs are picked up by the next replay
+    host.host_in["rgb"].mul_(0.5)
+    host.replay()
+    torch.cuda.synchronize()
+    assert host.host_out["loss"].item() != dev.loss.item()
+    h2d, d2h = host.transfer_bytes()
+    assert h2d == 4 * (s.N * 14 + 16 + 4 * s.W * s.H) and d2h == 4 * (s.N * 14 + 6 + 1)

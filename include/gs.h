@@ -152,7 +152,7 @@ typedef struct {
                             (global tile id << 32) | Gaussian id */
   size_t vals_sorted;    /* u32 [pair_capacity]: emission index of each sorted pair (pairs of an
                             item occupy [pair offset, pair offset + tiles emitted)) */
-  size_t ranges;         /* u32 [K*Tx*Ty][2]: [start, end) of each global tile */
+  size_t ranges;         /* u32 [K*Tx*Ty][2]: [start, end) of each global tile ([0, 0) when empty) */
   size_t pair_grads;     /* float [pair_capacity][12]: per-pair gradients of gs_raster_bwd, valid
                             where the pair's bit in pair_valid is set (other pairs: zero) */
   int32_t sort_passes;   /* 8-bit LSD passes of the pair sort over the tile bits: ceil(ceil(log2(K*Tx*Ty)) / 8) */

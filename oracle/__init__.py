@@ -80,6 +80,9 @@ def _declare(L):
     L.orc_render_occluded.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _D,
                                       _P, _P, _P, _P, _P, _P, _P]
     L.orc_render_occluded.restype = None
+    L.orc_render_tiles.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P, _D, _D, _D,
+                                   _P, _P, _P, _P, _P, _P, _P, _P, _P]
+    L.orc_render_tiles.restype = None
     L.orc_bin.argtypes = [_I64, _I, _I, _I, _I, _P, _P, _P, _P, _I64, _P, _P, _P]
     L.orc_bin.restype = _I64
     L.orc_render_fwd.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _D, _D, _D,
@@ -215,6 +218,26 @@ def render_occluded(params, cams, W, H, vals, ranges, ext_depth, ext_rgb=None, t
                               _ptr(o["T"]), _ptr(o["near"]), _ptr(o["alt_rgb"]), _ptr(o["alt_depth"]),
                               _ptr(o["alt_T"]))
     return o
+
+
+def render_tiles(params, cams, W, H, vals, ranges, tiles, tile=TILE,
+                 guard=(GUARD_ALPHA, GUARD_T, GUARD_POWER)):
+    """FP64 render of the listed global tiles only (every pixel of each), with the same
+    compositing and guard-band outputs as render_fwd. Returns arrays [n, 16, 16] (rgb
+    [n, 3, 16, 16]); near = -1 marks pixels outside the image."""
+    means, ls, qs, lg, rgb = params64(*params)
+    cams = _c(np.asarray(cams, np.float64), np.float64).reshape(-1, 16)
+    N = means.shape[0]
+    tl = _c(np.asarray(tiles, np.int64), np.int64)
+    n, P = len(tl), tile * tile
+    o = {"rgb": np.empty((n, 3, P)), "depth": np.empty((n, P)), "T": np.empty((n, P)),
+         "last": np.empty((n, P), np.int32), "near": np.empty((n, P), np.int32), "alt_rgb": np.empty((n, 3, P)),
+         "alt_depth": np.empty((n, P)), "alt_T": np.empty((n, P)), "alt_last": np.empty((n, P), np.int32)}
+    lib().orc_render_tiles(N, _ptr(means), _ptr(ls), _ptr(qs), _ptr(lg), _ptr(rgb), cams.shape[0], _ptr(cams), W, H,
+                           tile, _ptr(_c(vals, np.uint32)), _ptr(_c(ranges, np.uint32)), n, _ptr(tl), *guard,
+                           _ptr(o["rgb"]), _ptr(o["depth"]), _ptr(o["T"]), _ptr(o["last"]), _ptr(o["near"]),
+                           _ptr(o["alt_rgb"]), _ptr(o["alt_depth"]), _ptr(o["alt_T"]), _ptr(o["alt_last"]))
+    return {k: (v.reshape(n, 3, tile, tile) if v.ndim == 3 else v.reshape(n, tile, tile)) for k, v in o.items()}
 
 
 def pixel_trace(params, cam, W, H, vals, ranges, k, px, py, tile=TILE, max_n=4096):

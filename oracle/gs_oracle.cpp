@@ -648,6 +648,61 @@ void orc_render_occluded(int64_t N, const double* means, const double* log_scale
     }
 }
 
+// FP64 render of selected tiles only (full-size parity on sampled outputs): the same per-pixel
+// compositing as orc_render_fwd, for every pixel of each listed global tile id, projecting only
+// the Gaussians of that tile's list. Outputs are [n_tiles, 16*16] per pixel of the tile in
+// row-major order (rgb: [n_tiles, 3, 256]); pixels outside the image get near = -1.
+void orc_render_tiles(int64_t N, const double* means, const double* log_scales, const double* quats,
+                      const double* logits, const double* rgb, int K, const double* cams, int W, int H, int tile,
+                      const uint32_t* vals, const uint32_t* ranges, int n_tiles, const int64_t* tiles,
+                      double guard_alpha, double guard_T, double guard_power, double* out_rgb, double* out_depth,
+                      double* out_T, int32_t* out_last, int32_t* out_near, double* alt_rgb, double* alt_depth,
+                      double* alt_T, int32_t* alt_last) {
+  const int Tx = tiles_x(W, tile), Ty = tiles_y(H, tile);
+  const Guard gd{guard_alpha, guard_T, guard_power};
+  const int P = tile * tile;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < n_tiles; ++i) {
+    const int64_t t = tiles[i];
+    const int k = static_cast<int>(t / (static_cast<int64_t>(Tx) * Ty));
+    const int r = static_cast<int>(t - static_cast<int64_t>(k) * Tx * Ty);
+    const int ty = r / Tx, tx = r - ty * Tx;
+    const uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+    const double* cam = cams + 16 * k;
+    // the tile's list, projected, indexed by list position
+    std::vector<Proj64> local(e - s);
+    std::vector<uint32_t> idx(e - s);
+    for (uint32_t j = s; j < e; ++j) {
+      const int64_t g = vals[j];
+      local[j - s] = project64(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], rgb + 3 * g, cam, W, H);
+      idx[j - s] = j - s;
+    }
+    for (int q = 0; q < P; ++q) {
+      const int px = tx * tile + q % tile, py = ty * tile + q / tile;
+      const int64_t o = static_cast<int64_t>(i) * P + q;
+      if (px >= W || py >= H) {
+        out_near[o] = -1;
+        continue;
+      }
+      const PixelResult pr = walk_pixel(local.data(), idx.data(), 0, e - s, px + 0.5, py + 0.5, gd, -1, nullptr);
+      const PixelResult a =
+          pr.n_near ? walk_pixel(local.data(), idx.data(), 0, e - s, px + 0.5, py + 0.5, gd, pr.first_near, nullptr)
+                    : pr;
+      for (int ch = 0; ch < 3; ++ch) {
+        out_rgb[(static_cast<int64_t>(i) * 3 + ch) * P + q] = pr.rgb[ch];
+        alt_rgb[(static_cast<int64_t>(i) * 3 + ch) * P + q] = a.rgb[ch];
+      }
+      out_depth[o] = pr.depth;
+      out_T[o] = pr.T;
+      out_last[o] = pr.last;
+      out_near[o] = pr.n_near;
+      alt_depth[o] = a.depth;
+      alt_T[o] = a.T;
+      alt_last[o] = a.last;
+    }
+  }
+}
+
 // Contributors of one pixel (test aid for the transmittance-product and weight pins).
 // Returns the number of composited Gaussians (at most max_n are written).
 int orc_pixel_trace(int64_t N, const double* means, const double* log_scales, const double* quats,

@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* _
     uint64_t tot;
     const uint64_t incl = block_inclusive_scan1024(c, tmp, &tot);
     if (t < L.n_tiles) {
-      const uint64_t start = carry + incl - c, end = carry + incl;
+      // an empty tile's range is [0, 0)
+      const uint64_t start = c ? carry + incl - c : 0, end = c ? carry + incl : 0;
       ranges[2 * t] = static_cast<uint32_t>(start < n ? start : n);
       ranges[2 * t + 1] = static_cast<uint32_t>(end < n ? end : n);
       if (c)

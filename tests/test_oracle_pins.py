@@ -14,6 +14,7 @@ import pytest
 from scipy.spatial.transform import Rotation
 
 import oracle
+from scenes import make_scene
 from scenes.generate import camera_array, identity_camera
 
 ALPHA_MAX, ALPHA_MIN, T_STOP, DIL = 0.99, 1.0 / 255.0, 1e-4, 0.3
@@ -653,3 +654,22 @@ def test_occluded_render_equals_per_pixel_brute_force():
                                   ext_rgb)
     np.testing.assert_array_equal(near["rgb"], ext_rgb.astype(np.float64))
     assert np.all(near["T"] == 1.0) and np.all(near["depth"] == 0.5)
+
+
+def test_render_tiles_equals_full_render():
+    # the tile-sampled FP64 render (full-size parity on sampled outputs) is the full render
+    # restricted to those tiles, element for element
+    s = make_scene("map100k", n=3000, W=72, H=50, f=60.0)
+    o = oracle.forward(s.params(), s.cams, s.W, s.H)
+    L = o["lists"]
+    Tx, Ty = (s.W + 15) // 16, (s.H + 15) // 16
+    tiles = np.array([0, 3, Tx + 2, Tx * Ty - 1])  # includes ragged edge tiles
+    t = oracle.render_tiles(s.params(), s.cams, s.W, s.H, L.vals, L.ranges, tiles)
+    for i, tg in enumerate(tiles):
+        ty, tx = divmod(int(tg), Tx)
+        ys, xs = slice(ty * 16, min(ty * 16 + 16, s.H)), slice(tx * 16, min(tx * 16 + 16, s.W))
+        h, w = ys.stop - ys.start, xs.stop - xs.start
+        assert np.array_equal(t["rgb"][i][:, :h, :w], o["rgb"][0][:, ys, xs])
+        for k in ("depth", "T", "last", "near", "alt_T", "alt_depth", "alt_last"):
+            assert np.array_equal(t[k][i][:h, :w], o[k][0][ys, xs]), k
+        assert np.all(t["near"][i][h:, :] == -1) and np.all(t["near"][i][:, w:] == -1)

@@ -69,6 +69,8 @@ typedef enum {
 #define GS_DEVERR_PAIR_OVERFLOW 0x1u /* more (Gaussian, tile) pairs than pair_capacity */
 #define GS_DEVERR_TIMEOUT 0x2u       /* a decoupled look-back spin hit its iteration cap */
 #define GS_DEVERR_NONFINITE 0x4u     /* a mean, scale, quaternion, logit or colour was NaN/Inf */
+#define GS_DEVERR_BOUNDS 0x8u        /* debug builds only (GS_DEBUG): a data-dependent index failed its
+                                        bounds check; the access was skipped */
 
 typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype_t;
 

@@ -11,7 +11,7 @@ import ctypes
 import os
 import threading
 
-from .build import LIB
+from .build import LIB, LIB_DEBUG
 
 c_int32, c_int64, c_float, c_void_p, c_size_t, c_uint32 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
                                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32)
@@ -80,7 +80,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            p = path or LIB
+            p = path or (LIB_DEBUG if os.environ.get("GS_DEBUG") == "1" else LIB)
             if not os.path.exists(p):
                 raise RuntimeError(f"CUDA library not built ({p}); run paper_2509_06433_gb300.build.build()")
             L = ctypes.CDLL(p)

@@ -1,4 +1,5 @@
 // C ABI entry points (include/gs.h): argument checks, workspace layout, launches.
+#include <nvtx3/nvToolsExt.h>
 #include <string.h>
 
 #include "gs_internal.cuh"
@@ -7,6 +8,12 @@ namespace gs {
 
 namespace {
 constexpr size_t kAlign = 256;
+// An NVTX range around each entry point that enqueues work (visible to nsys / ncu timelines;
+// a no-op when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+};
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 int ceil_log2(int64_t x) {  // smallest b with 2^b >= x (x >= 1)
   int b = 0;
@@ -186,6 +193,7 @@ gs_status_t gs_read_status(const gs_config_t* cfg, const void* ws, size_t ws_byt
 
 gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, const gs_camera_t* d_cams, void* ws,
                        size_t ws_bytes, void* stream) {
+  const TraceRange trace_("gs_project");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -201,6 +209,7 @@ gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, 
 }
 
 gs_status_t gs_bin_sort(const gs_config_t* cfg, void* ws, size_t ws_bytes, void* stream) {
+  const TraceRange trace_("gs_bin_sort");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -213,6 +222,7 @@ gs_status_t gs_bin_sort(const gs_config_t* cfg, void* ws, size_t ws_bytes, void*
 
 gs_status_t gs_raster_fwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
                           float* T_final, int32_t* last, void* stream) {
+  const TraceRange trace_("gs_raster_fwd");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -221,6 +231,7 @@ gs_status_t gs_raster_fwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, flo
 
 gs_status_t gs_raster_fwd_stats(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
                                 float* T_final, int32_t* last, void* stream) {
+  const TraceRange trace_("gs_raster_fwd_stats");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -230,6 +241,7 @@ gs_status_t gs_raster_fwd_stats(const gs_config_t* cfg, void* ws, size_t ws_byte
 gs_status_t gs_raster_fwd_occluded(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
                                    float* T_final, int32_t* last, const float* ext_depth, const float* ext_rgb,
                                    void* stream) {
+  const TraceRange trace_("gs_raster_fwd_occluded");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -241,6 +253,7 @@ gs_status_t gs_raster_fwd_occluded(const gs_config_t* cfg, void* ws, size_t ws_b
 gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
                              float* T_final, int32_t* last, const float* rgb_target, const float* depth_target,
                              float* dL_drgb, float* dL_ddepth, float* d_loss, void* stream) {
+  const TraceRange trace_("gs_raster_fwd_l1");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -252,6 +265,7 @@ gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_bytes, 
 gs_status_t gs_loss_l1(const gs_config_t* cfg, const float* rgb, const float* depth, const float* rgb_target,
                        const float* depth_target, float* dL_drgb, float* dL_ddepth, float* d_loss, void* ws,
                        size_t ws_bytes, void* stream) {
+  const TraceRange trace_("gs_loss_l1");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -263,6 +277,7 @@ gs_status_t gs_loss_l1(const gs_config_t* cfg, const float* rgb, const float* de
 gs_status_t gs_raster_bwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, const float* rgb, const float* depth,
                           const float* T_final, const int32_t* last, const float* dL_drgb, const float* dL_ddepth,
                           const float* dL_dT, void* stream) {
+  const TraceRange trace_("gs_raster_bwd");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -273,6 +288,7 @@ gs_status_t gs_raster_bwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, con
 
 gs_status_t gs_project_bwd(const gs_config_t* cfg, const gs_gaussians_t* gaussians, const gs_camera_t* d_cams,
                            void* ws, size_t ws_bytes, const gs_grads_t* grads, void* stream) {
+  const TraceRange trace_("gs_project_bwd");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -283,6 +299,7 @@ gs_status_t gs_project_bwd(const gs_config_t* cfg, const gs_gaussians_t* gaussia
 
 gs_status_t gs_screen_grads(const gs_config_t* cfg, const void* ws, size_t ws_bytes, float* d_mean2d, float* d_conic,
                             float* d_depth, float* d_opacity, float* d_rgb, void* stream) {
+  const TraceRange trace_("gs_screen_grads");
   Layout L;
   gs_status_t st = check(cfg, ws, ws_bytes, &L);
   if (st != GS_OK) return st;
@@ -326,6 +343,7 @@ gs_status_t gs_sort_pairs_tmp_size(int64_t n, size_t* bytes) {
 
 gs_status_t gs_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int32_t key_bits, void* tmp, size_t tmp_bytes,
                           uint32_t* d_err_word, void* stream) {
+  const TraceRange trace_("gs_sort_pairs");
   if (n < 0 || n > (1LL << 30) - 1 || key_bits < 1 || key_bits > 64) return GS_ERR_INVALID_ARG;
   if (n == 0) return GS_OK;
   if (!keys || !vals || !tmp || (reinterpret_cast<uintptr_t>(tmp) % kAlign) != 0) return GS_ERR_INVALID_ARG;

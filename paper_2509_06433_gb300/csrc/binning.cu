@@ -338,6 +338,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
       ty = static_cast<int>(static_cast<uint32_t>(e.y) >> 16);
     }
     const uint64_t tid = static_cast<uint64_t>(nk >> 16) * tiles_per_view + static_cast<uint64_t>(ty) * L.Tx + tx;
+    if (!GS_INDEX_OK(tid < static_cast<uint64_t>(L.n_tiles) && tx < L.Tx && ty < L.Ty && j < static_cast<uint64_t>(L.cap),
+                     &at<Status>(ws, L.status)->err))
+      continue;
     keys[j] = (tid << 32) | s_g[a];
     vals[j] = jj;
   }

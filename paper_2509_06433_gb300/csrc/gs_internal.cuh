@@ -102,6 +102,15 @@ struct GaussPtrs {
   int dtype, means_dtype;
 };
 
+// Debug builds (-DGS_DEBUG) check the data-dependent indices of gathers and scatters: a failed
+// check sets GS_DEVERR_BOUNDS in the error word and the access is skipped (no trap). Release
+// builds compile the checks away.
+#ifdef GS_DEBUG
+#define GS_INDEX_OK(cond, err) ((cond) ? true : (atomicOr((err), GS_DEVERR_BOUNDS), false))
+#else
+#define GS_INDEX_OK(cond, err) true
+#endif
+
 // ---------------------------------------------------------------------------- launches
 // Programmatic dependent launch: every kernel of the library begins with pdl_begin(), which
 // waits until the preceding grid of the stream has completed (its writes are then visible)

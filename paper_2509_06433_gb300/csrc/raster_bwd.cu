@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
       const float dv = kLn2 * (2.0f * B.x * R[1] + A.w * R[0]);
       const float dop = R[6] != 0.0f ? R[6] / B.y : 0.0f;
       const uint32_t slot = s_slot[jj];
+      if (!GS_INDEX_OK(static_cast<int64_t>(slot) < L.cap, &at<Status>(ws, L.status)->err)) continue;
       float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(slot) * kPairGradStride);
       dst[0] = make_float4(du, dv, -0.5f * R[2], -R[3]);
       dst[1] = make_float4(-0.5f * R[4], R[5], dop, R[7]);

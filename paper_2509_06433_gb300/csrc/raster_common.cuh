@@ -91,7 +91,8 @@ __device__ __forceinline__ uint32_t splat_rows(float mx, float my, float Qa, flo
 template <int CH>
 __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layout& L, const uint8_t* ws,
                                                 const uint64_t* keys, uint32_t i, int k, float ox, float oy) {
-  const uint32_t gid = static_cast<uint32_t>(keys[i]);  // sorted key = (tile << 32) | Gaussian id
+  uint32_t gid = static_cast<uint32_t>(keys[i]);  // sorted key = (tile << 32) | Gaussian id
+  if (!GS_INDEX_OK(static_cast<int64_t>(gid) < L.N, &at<Status>(const_cast<uint8_t*>(ws), L.status)->err)) gid = 0;
   const int64_t kg = static_cast<int64_t>(k) * L.N + gid;
   const float4 uv = at<float4>(ws, L.proj_uv)[kg];
   const float4 cn = at<float4>(ws, L.proj_conic)[kg];

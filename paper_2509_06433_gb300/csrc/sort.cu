@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgsT<KeyT> a, in
       const KeyT key = S.keys[j];
       const uint32_t d = static_cast<uint32_t>(key >> shift) & dmask;
       const uint32_t dst = S.global_base[d] + (j - S.local_start[d]);
+      if (!GS_INDEX_OK(dst < n, a.err)) continue;
       kout[dst] = key;
       vout[dst] = S.vals[j];
     }

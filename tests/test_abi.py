@@ -37,6 +37,15 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_debug_build_exports_the_same_entry_points():
+    # the index-checking build (GS_DEBUG) is a drop-in replacement of the release library
+    from paper_2509_06433_gb300.build import build
+    path = build(debug=True)
+    dbg = ctypes.CDLL(path)
+    for n in declared_entry_points():
+        assert hasattr(dbg, n), n
+
+
 def _cfg(W=640, H=480, K=1, N=100_000, cap=1 << 20, tile=16, near=0.2):
     from paper_2509_06433_gb300._lib import GsConfig
     return GsConfig(W, H, tile, K, N, cap, near, 0.1, 0, 0)

@@ -652,6 +652,43 @@ def measure_viewer(dev, frames=300, views=2):
                 raise RuntimeError("viewer timed out")
             time.sleep(0.02)
 
+    # for comparison: the viewer as a high-priority stream inside the mapping process (kernel-level
+    # interleaving instead of the time-slicing of two processes' contexts)
+    inproc = None
+    try:
+        from paper_2509_06433_gb300.viewer import orbit_rig
+        low, high = torch.cuda.Stream(device=dev, priority=0), torch.cuda.Stream(device=dev, priority=-1)
+        vr = api.Rasterizer(672, 376, views, s.N, pair_capacity=max(1 << 20, 4 * s.N * views), device=dev)
+        vcams = torch.as_tensor(orbit_rig(0, views, (0.0, 0.0, 5.0), 4.0, 336.0, 672, 376)).to(dev)
+        vr.plan(shared.g, vcams, headroom=2.0)
+        vout = vr.new_outputs()
+        torch.cuda.synchronize(dev)
+        n_map = 1500
+        t0 = time.perf_counter()
+        with torch.cuda.stream(low):
+            for _ in range(n_map):
+                step.replay()
+        done = torch.cuda.Event()
+        done.record(low)
+        t_frames = []
+        for i in range(frames):
+            f0 = time.perf_counter()
+            with torch.cuda.stream(high):
+                vcams.copy_(torch.as_tensor(orbit_rig(i, views, (0.0, 0.0, 5.0), 4.0, 336.0, 672, 376)),
+                            non_blocking=False)
+                vr.render(shared.g, vcams, vout, stream=high)
+            high.synchronize()
+            t_frames.append(time.perf_counter() - f0)
+            if done.query():
+                break
+        map_busy = not done.query()
+        done.synchronize()
+        t_map = time.perf_counter() - t0
+        inproc = {"viewer_fps_during_mapping": round(len(t_frames) / sum(t_frames), 1),
+                  "viewer_frames": len(t_frames), "mapping_busy_throughout": map_busy,
+                  "mapping_iters_per_s": round(n_map / t_map, 1)}
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line instead of failing the bench
+        inproc = {"error": str(e)[-300:]}
     try:
         proc, out, ready = viewer("idle")  # viewer alone (mapper idle)
         wait_for(out, proc)
@@ -674,7 +711,8 @@ def measure_viewer(dev, frames=300, views=2):
             "mapping_slowdown": round(alone / during, 3) if during else None,
             "viewer_fps_alone": round(v_alone["fps"], 1), "viewer_fps_during_mapping": round(v_busy["fps"], 1),
             "viewer_frame_ms_median": round(v_busy["frame_ms_median"], 3), "viewer_frames": frames,
-            "viewer_device_error": v_busy["device_error_word"]}
+            "viewer_device_error": v_busy["device_error_word"],
+            "in_process_high_priority_stream": inproc}
 
 
 def load_peaks():

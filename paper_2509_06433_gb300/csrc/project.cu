@@ -123,14 +123,11 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project(Layout L, GaussPtrs G
     for (int i = threadIdx.x; i < gcells; i += kProjBlock) s_grid[i] = 0;
   __syncthreads();
   uint32_t count = 0, item_key = 0xffffffffu;
-  // what the row-span table needs once the warp has its entries
-  Ellipse E_keep{};
-  int span_x0 = 0, span_x1 = 0, span_y0 = 0, row_first = 0;
-  uint32_t nrows = 0;
-  constexpr int kCachedRows = 4;  // spans of the rectangle's first rows, kept for the table
-  int2 spc[kCachedRows];
-#pragma unroll
-  for (int q = 0; q < kCachedRows; ++q) spc[q] = make_int2(1, 0);
+  // the item's widened ellipse and tile rectangle, for the warp's row passes below
+  Ellipse E{};
+  int x0 = 0, x1 = 0, y0 = 0, y1 = 0, kv = 0;
+  bool live = false;
+  float z_item = 0.0f;
   if (idx < L.KN) {
     const int k = static_cast<int>(idx / L.N);
     const int64_t g = idx - static_cast<int64_t>(k) * L.N;
@@ -245,7 +242,7 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project(Layout L, GaussPtrs G
     const float x1f = fminf(fmaxf(__fadd_rn(floorf(__fmul_rn(__fadd_rn(u, rf), inv_tile)), 1.0f), 0.0f), Txf);
     const float y0f = fminf(fmaxf(floorf(__fmul_rn(__fsub_rn(v, rf), inv_tile)), 0.0f), Tyf);
     const float y1f = fminf(fmaxf(__fadd_rn(floorf(__fmul_rn(__fadd_rn(v, rf), inv_tile)), 1.0f), 0.0f), Tyf);
-    int x0 = 0, x1 = 0, y0 = 0, y1 = 0, radius = 0;
+    int radius = 0;
     if (valid) {
       x0 = static_cast<int>(x0f);
       x1 = static_cast<int>(x1f);
@@ -255,53 +252,26 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project(Layout L, GaussPtrs G
       if ((x1 - x0) * (y1 - y0) == 0) {
         x0 = x1 = y0 = y1 = radius = 0;
       } else {
-        // the widened alpha >= 1/255 ellipse and, row by row, the rectangle's tiles it meets
+        // the widened alpha >= 1/255 ellipse; its rows are examined by the warp below
         const float op = __fdiv_rn(1.0f, __fadd_rn(1.0f, exp_det(-lg)));
         const float Lg = log_det(__fmul_rn(255.0f, op));
         const float Lm = __fadd_rn(__fadd_rn(Lg, __fmul_rn(0.02f, fabsf(Lg))), 1.5e-4f);
         if (Lm >= 0.0f) {
           const float kap = __fmul_rn(2.0f, Lm);
-          const Ellipse E{u, v, bb, __fdiv_rn(1.0f, c), __fsqrt_rn(det), __fsqrt_rn(__fmul_rn(kap, a)),
-                          __fsqrt_rn(__fmul_rn(kap, c)), __fdiv_rn(bb, a)};
+          E = Ellipse{u, v, bb, __fdiv_rn(1.0f, c), __fsqrt_rn(det), __fsqrt_rn(__fmul_rn(kap, a)),
+                      __fsqrt_rn(__fmul_rn(kap, c)), __fdiv_rn(bb, a)};
           at<Ellipse>(ws, L.proj_ell)[idx] = E;
-          int32_t* dg = (use_sgrid && k == k_block)
-                            ? s_grid
-                            : at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * gcells;
-          int first = -1, last = -1;
-          auto add_row = [&](int ty, int2 sp) {
-            if (sp.x > sp.y) return;
-            count += static_cast<uint32_t>(sp.y - sp.x + 1);
-            atomicAdd(&dg[ty * gstride + sp.x], 1);  // row-wise prefix sum: pairs per tile
-            atomicAdd(&dg[ty * gstride + sp.y + 1], -1);
-            if (first < 0) first = ty;
-            last = ty;
-          };
-#pragma unroll
-          for (int q = 0; q < kCachedRows; ++q)
-            if (y0 + q < y1) {
-              spc[q] = row_span(E, y0 + q, x0, x1);
-              add_row(y0 + q, spc[q]);
-            }
-          for (int ty = y0 + kCachedRows; ty < y1; ++ty) add_row(ty, row_span(E, ty, x0, x1));
-          if (count) {
-            E_keep = E;
-            span_x0 = x0;
-            span_x1 = x1;
-            span_y0 = y0;
-            row_first = first;
-            nrows = static_cast<uint32_t>(last - first + 1);
-          }
+          live = true;
         }
       }
     }
     at<uint32_t>(ws, L.proj_depth_key)[idx] = __float_as_uint(zc);
-    if (count) item_key = __float_as_uint(zc);
     at<int32_t>(ws, L.proj_radius)[idx] = radius;
-    at<int4>(ws, L.proj_tiles)[idx] =
-        make_int4(0, static_cast<int>(pack16(x0, x1)), static_cast<int>(pack16(y0, y1)), static_cast<int>(count));
+    kv = k;
+    z_item = zc;
 
     // ---------------- continuous path ----------------------------------------------
-    if (count) {
+    if (live) {  // (the records of an item that emits nothing are never read)
       const FF X = dot3_plus(R[0], R[1], R[2], p0, p1, p2, t[0]);
       const FF Y = dot3_plus(R[3], R[4], R[5], p0, p1, p2, t[1]);
       const FF Z = dot3_plus(R[6], R[7], R[8], p0, p1, p2, t[2]);
@@ -313,11 +283,87 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project(Layout L, GaussPtrs G
       at<float4>(ws, L.proj_conic)[idx] = make_float4(c * inv_det, -bb * inv_det, a * inv_det, Z.hi);
     }
   }
-  // row-span table entries for the item's rows first..last (one counter atomic per warp);
-  // rows past the first kCachedRows of the rectangle are recomputed bit for bit by the same
-  // function
+
+  // ---------------- the rectangle's rows, shared out over the warp -------------------
+  // The warp's items' rows are numbered consecutively (item by item) and examined 32 at a time,
+  // one row per lane, so a warp holding one tall rectangle does not idle the other lanes. A row
+  // owner's ellipse and rectangle come from its lane by shuffles. Pass 1 counts each item's
+  // emitted tiles and finds its first and last non-empty rows (and adds the spans to the span
+  // grid); pass 2 writes the item's row-span table entries.
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  __shared__ int s_acc[kProjBlock / 32][3][32];  // per warp and lane: tiles, first row, last row
+  s_acc[wib][0][lane] = 0;
+  s_acc[wib][1][lane] = 0x7fffffff;
+  s_acc[wib][2][lane] = -1;
+  auto owner = [&](int st, int r) {  // the last lane whose first row number is <= r
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int cand = o + step;
+      const int sc = __shfl_sync(0xffffffffu, st, cand & 31);
+      if (cand < 32 && sc <= r) o = cand;
+    }
+    return o;
+  };
+  auto owner_ellipse = [&](int o) {
+    Ellipse e;
+    e.u = __shfl_sync(0xffffffffu, E.u, o);
+    e.v = __shfl_sync(0xffffffffu, E.v, o);
+    e.b = __shfl_sync(0xffffffffu, E.b, o);
+    e.inv_c = __shfl_sync(0xffffffffu, E.inv_c, o);
+    e.sdet = __shfl_sync(0xffffffffu, E.sdet, o);
+    e.hx = __shfl_sync(0xffffffffu, E.hx, o);
+    e.hy = __shfl_sync(0xffffffffu, E.hy, o);
+    e.kxy = __shfl_sync(0xffffffffu, E.kxy, o);
+    return e;
+  };
+  auto warp_excl_scan = [&](int x, int& total) {
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - x;
+  };
   {
-    const int lane = threadIdx.x & 31;
+    int total = 0;
+    const int st = warp_excl_scan(live ? y1 - y0 : 0, total);
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+      const int r = base + lane;
+      const int o = owner(st, r);
+      const Ellipse eo = owner_ellipse(o);
+      const int ox0 = __shfl_sync(0xffffffffu, x0, o), ox1 = __shfl_sync(0xffffffffu, x1, o);
+      const int oy0 = __shfl_sync(0xffffffffu, y0, o), ok = __shfl_sync(0xffffffffu, kv, o);
+      const int ost = __shfl_sync(0xffffffffu, st, o);
+      if (r < total) {
+        const int ty = oy0 + (r - ost);
+        const int2 sp = row_span(eo, ty, ox0, ox1);
+        if (sp.x <= sp.y) {
+          atomicAdd(&s_acc[wib][0][o], sp.y - sp.x + 1);
+          atomicMin(&s_acc[wib][1][o], ty);
+          atomicMax(&s_acc[wib][2][o], ty);
+          int32_t* dg = (use_sgrid && ok == k_block) ? s_grid
+                                                      : at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(ok) * gcells;
+          atomicAdd(&dg[ty * gstride + sp.x], 1);  // row-wise prefix sum: pairs per tile
+          atomicAdd(&dg[ty * gstride + sp.y + 1], -1);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  count = static_cast<uint32_t>(s_acc[wib][0][lane]);
+  const int row_first = s_acc[wib][1][lane];
+  const uint32_t nrows = count ? static_cast<uint32_t>(s_acc[wib][2][lane] - row_first + 1) : 0u;
+  if (idx < L.KN) {
+    if (count) item_key = __float_as_uint(z_item);
+    at<int4>(ws, L.proj_tiles)[idx] =
+        make_int4(0, static_cast<int>(pack16(x0, x1)), static_cast<int>(pack16(y0, y1)), static_cast<int>(count));
+  }
+  // row-span table entries for the item's rows first..last (one counter atomic per warp)
+  {
     uint32_t incl = nrows;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -327,27 +373,44 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project(Layout L, GaussPtrs G
     uint32_t base = 0;
     if (lane == 31 && incl) base = atomicAdd(&at<Status>(ws, L.status)->row_ctr, incl);
     base = __shfl_sync(0xffffffffu, base, 31) + (incl - nrows);
-    if (nrows) {
-      if (static_cast<uint64_t>(base) + nrows <= static_cast<uint64_t>(L.cap)) {
-        int2* tab = at<int2>(ws, L.row_table) + base;
-        const int row_end = row_first + static_cast<int>(nrows);
-        int cum = 0;
-        auto put = [&](int ty, int2 sp) {
-          tab[ty - row_first] = make_int2(cum, (sp.x & 0xffff) | (ty << 16));
-          if (sp.x <= sp.y) cum += sp.y - sp.x + 1;
-        };
-#pragma unroll
-        for (int q = 0; q < kCachedRows; ++q)
-          if (span_y0 + q >= row_first && span_y0 + q < row_end) put(span_y0 + q, spc[q]);
-        for (int ty = max(span_y0 + kCachedRows, row_first); ty < row_end; ++ty)
-          put(ty, row_span(E_keep, ty, span_x0, span_x1));
-        at<uint2>(ws, L.proj_rows)[idx] = make_uint2(base, nrows);
-      } else {
-        atomicOr(&at<Status>(ws, L.status)->err, GS_DEVERR_PAIR_OVERFLOW);
-        at<uint2>(ws, L.proj_rows)[idx] = make_uint2(0, 0);
+    const bool fits = nrows && static_cast<uint64_t>(base) + nrows <= static_cast<uint64_t>(L.cap);
+    if (nrows && !fits) atomicOr(&at<Status>(ws, L.status)->err, GS_DEVERR_PAIR_OVERFLOW);
+    if (idx < L.KN) at<uint2>(ws, L.proj_rows)[idx] = fits ? make_uint2(base, nrows) : make_uint2(0, 0);
+    int total = 0;
+    const int st = warp_excl_scan(fits ? static_cast<int>(nrows) : 0, total);
+    int2* tab = at<int2>(ws, L.row_table);
+    __shared__ int s_carry[kProjBlock / 32][32];  // tiles in the item's rows already written
+    s_carry[wib][lane] = 0;
+    __syncwarp();
+    for (int b2 = 0; b2 < total; b2 += 32) {
+      const int r = b2 + lane;
+      const int o = owner(st, r);
+      const Ellipse eo = owner_ellipse(o);
+      const int ox0 = __shfl_sync(0xffffffffu, x0, o), ox1 = __shfl_sync(0xffffffffu, x1, o);
+      const int ofirst = __shfl_sync(0xffffffffu, row_first, o);
+      const uint32_t obase = __shfl_sync(0xffffffffu, base, o);
+      const int ost = __shfl_sync(0xffffffffu, st, o);
+      int2 sp = make_int2(1, 0);
+      int ty = 0, len = 0;
+      if (r < total) {
+        ty = ofirst + (r - ost);
+        sp = row_span(eo, ty, ox0, ox1);
+        len = sp.x <= sp.y ? sp.y - sp.x + 1 : 0;
       }
-    } else if (idx < L.KN) {
-      at<uint2>(ws, L.proj_rows)[idx] = make_uint2(0, 0);
+      // inclusive sum of len over this round's rows of the same item (they are adjacent lanes)
+      int inc = len;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+        const int od = __shfl_up_sync(0xffffffffu, o, d);
+        if (lane >= d && od == o) inc += y;
+      }
+      const int carry = s_carry[wib][o];
+      if (r < total) tab[obase + static_cast<uint32_t>(ty - ofirst)] = make_int2(carry + inc - len, (sp.x & 0xffff) | (ty << 16));
+      const int onext = __shfl_down_sync(0xffffffffu, o, 1);
+      __syncwarp();
+      if (lane == 31 || onext != o) s_carry[wib][o] = carry + inc;
+      __syncwarp();
     }
   }
   // depth-sort key of the item (culled items sort last and emit nothing) and its digit counts

@@ -243,7 +243,7 @@ struct SortArgsT {
   uint32_t first_tile;        // diagnostic: 1 withholds tile 0, so its successors' waits run out
   int items;                  // keys per thread per tile: 8 or 15 (0: kSortItems)
 };
-__host__ __device__ inline int sort_items(int items) { return items == 8 ? items : kSortItems; }
+__host__ __device__ inline int sort_items(int items) { return (items == 4 || items == 8) ? items : kSortItems; }
 // onesweep tiles of n keys at `items` keys per thread
 __host__ __device__ inline int64_t sort_tiles(int64_t n, int items) {
   const int64_t tk = static_cast<int64_t>(kSortThreads) * sort_items(items);
@@ -251,7 +251,8 @@ __host__ __device__ inline int64_t sort_tiles(int64_t n, int items) {
 }
 // Keys per thread for a sort of up to n keys: small sorts take short tiles, so that enough
 // blocks share the work.
-inline int pick_sort_items(int64_t n) { return n <= 600000 ? 8 : kSortItems; }
+// keys per thread: small sorts take small tiles (more blocks, shorter per-tile latency)
+inline int pick_sort_items(int64_t n) { return n <= 200000 ? 4 : (n <= 600000 ? 8 : kSortItems); }
 using SortArgs = SortArgsT<uint64_t>;
 using SortArgs32 = SortArgsT<uint32_t>;
 cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s);

@@ -274,6 +274,7 @@ cudaError_t onesweep_passes_it(const SortArgsT<KeyT>& a, cudaStream_t s) {
 template <class KeyT>
 cudaError_t onesweep_passes(const SortArgsT<KeyT>& a, cudaStream_t s) {
   switch (sort_items(a.items)) {
+    case 4: return onesweep_passes_it<KeyT, 4>(a, s);
     case 8: return onesweep_passes_it<KeyT, 8>(a, s);
     default: return onesweep_passes_it<KeyT, kSortItems>(a, s);
   }

@@ -111,6 +111,8 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->item_kg = take(KN * 8);
   L->tile_diff = take(static_cast<size_t>(L->K) * (L->Tx + 1) * (L->Ty + 1) * 4);
   L->n_emit_blocks = (L->cap + kEmitPairs - 1) / kEmitPairs;
+  L->emit_first = take(static_cast<size_t>(L->n_emit_blocks) * 4);
+  L->emit_last = take(static_cast<size_t>(L->n_emit_blocks) * 4);
   L->total = o;
   return true;
 }

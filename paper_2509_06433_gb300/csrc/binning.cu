@@ -122,6 +122,20 @@ __global__ void __launch_bounds__(kProjBlock) k_item_offsets(Layout L, uint8_t* 
   for (int w = 0; w < kProjBlock / 32; ++w) wo += (w < warp) ? s_warp[w] : 0u;
   const uint64_t cap = static_cast<uint64_t>(L.cap);
   const uint64_t off = at<uint64_t>(ws, L.block_offsets)[blockIdx.x] + wo + incl - cnt;
+  if (s < L.KN && cnt) {
+    // the emission blocks (kEmitPairs pairs each) whose first or last pair is one of this item's
+    // pairs learn here which item that is (the block's window of items)
+    const uint64_t n = at<Status>(ws, L.status)->num_pairs;
+    const uint64_t lo = off, hi = off + cnt < n ? off + cnt : n;
+    uint32_t* first_item = at<uint32_t>(ws, L.emit_first);
+    uint32_t* last_item = at<uint32_t>(ws, L.emit_last);
+    for (uint64_t b = lo / kEmitPairs; b * kEmitPairs < hi; ++b) {
+      const uint64_t b0 = b * kEmitPairs;
+      const uint64_t b1 = (b0 + kEmitPairs < n ? b0 + kEmitPairs : n) - 1;
+      if (b0 >= lo) first_item[b] = static_cast<uint32_t>(s);
+      if (b1 < hi) last_item[b] = static_cast<uint32_t>(s);
+    }
+  }
   if (s < L.KN) {
     uint32_t* offsets = at<uint32_t>(ws, L.item_offsets);
     offsets[s] = static_cast<uint32_t>(off < cap ? off : cap);
@@ -242,15 +256,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
   if (start >= n) return;
   const uint64_t end = start + kEmitPairs < n ? start + kEmitPairs : n;
   const uint32_t* offsets = at<uint32_t>(ws, L.item_offsets);
-  if (threadIdx.x < 2) {
-    // last item whose offset <= target
-    const uint64_t target = threadIdx.x == 0 ? start : end - 1;
-    int64_t lo = 0, hi = L.KN;  // offsets[lo] <= target < offsets[hi]
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (offsets[mid] <= target) lo = mid; else hi = mid;
-    }
-    if (threadIdx.x == 0) s_lo = lo; else s_hi = lo;
+  if (threadIdx.x == 0) {  // the items holding the block's first and last pairs (k_item_offsets)
+    s_lo = at<uint32_t>(ws, L.emit_first)[blockIdx.x];
+    s_hi = at<uint32_t>(ws, L.emit_last)[blockIdx.x];
   }
   __syncthreads();
   const int64_t lo = s_lo;

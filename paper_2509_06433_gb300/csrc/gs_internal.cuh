@@ -79,6 +79,7 @@ struct Layout {
   // emitted row span; its row-wise prefix sum is the number of pairs of each tile
   size_t tile_diff;
   int64_t n_emit_blocks;    // ceil(cap / kEmitPairs)
+  size_t emit_first, emit_last;  // u32 [n_emit_blocks]: items holding each emission block's first / last pair
   size_t total;
 };
 

@@ -3,8 +3,8 @@
 //   k_sorted_counts   tiles emitted per item in depth order, per-block totals
 //   k_scan_blocks     exclusive scan of the block totals, pair count, capacity check
 //   k_item_offsets    per item (depth order): first pair index, rectangle, ids
-//   k_tile_prefix     row-wise prefix sum of each view's span grid = pairs per tile
-//   k_tile_scan       tile ranges [start, end) and the digit histograms of the pair sort
+//   k_tile_scan       row-wise prefix sum of each view's span grid = pairs per tile, then the
+//                     tile ranges [start, end) and the digit histograms of the pair sort
 //   k_emit_pairs      one (key, value) pair per emitted (view, Gaussian, tile), 1024 pairs per block
 //
 // An item emits, row by row through its tile rectangle, the tiles of each row's span that
@@ -152,69 +152,61 @@ __global__ void __launch_bounds__(kProjBlock) k_item_offsets(Layout L, uint8_t* 
   }
 }
 
-// One block per view: in-place row-wise prefix sum of the (Ty+1) x (Tx+1) span grid; cell
-// (ty, tx) then holds the number of pairs of tile (ty, tx). The grid is staged in shared
-// memory when it fits, else summed in place in global memory.
-__global__ void k_tile_prefix(Layout L, uint8_t* __restrict__ ws) {
-  pdl_begin();
-  __shared__ int32_t sg[kProjGridCells];
-  const int stride = L.Tx + 1;
-  const int cells = stride * (L.Ty + 1);
-  int32_t* gg = at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(blockIdx.x) * cells;
-  const bool in_smem = cells <= kProjGridCells;
-  int32_t* g = in_smem ? sg : gg;
-  if (in_smem) {
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) sg[i] = gg[i];
-    __syncthreads();
-  }
-  for (int y = threadIdx.x; y < L.Ty; y += blockDim.x) {
-    int32_t acc = 0;
-    for (int x = 0; x <= L.Tx; ++x) {
-      acc += g[y * stride + x];
-      g[y * stride + x] = acc;
-    }
-  }
-  if (in_smem) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) gg[i] = sg[i];
-  }
-}
-
-// Exclusive scan of the per-tile pair counts over global tile ids: ranges (clamped to the
-// pairs actually emitted) and the digit histograms of the pair sort.
+// One block: per view, the row-wise prefix sum of its (Ty+1) x (Tx+1) span grid (cell (ty, tx)
+// then holds the number of pairs of tile (ty, tx); staged in shared memory when it fits, else
+// summed in place in global memory), then the exclusive scan of the per-tile pair counts over
+// the global tile ids: ranges (clamped to the pairs actually emitted; [0, 0) for an empty tile)
+// and the digit histograms of the pair sort.
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* __restrict__ ws) {
   pdl_begin();
   __shared__ uint64_t tmp[32];
   __shared__ uint32_t s_hist[4 * 256];
+  __shared__ int32_t sg[kProjGridCells];
   for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
-  __syncthreads();
   const Status* st = at<Status>(ws, L.status);
   // after a capacity overflow the pair sort does not run: leave every tile empty
   const uint64_t n = st->total_pairs > static_cast<uint64_t>(L.cap) ? 0 : st->num_pairs;
-  const int32_t* grid = at<int32_t>(ws, L.tile_diff);
   uint32_t* ranges = at<uint32_t>(ws, L.ranges);
+  const int stride = L.Tx + 1;
+  const int cells = stride * (L.Ty + 1);
+  const bool in_smem = cells <= kProjGridCells;
   const int64_t per_view = static_cast<int64_t>(L.Tx) * L.Ty;
   uint64_t carry = 0;
-  for (int64_t base = 0; base < L.n_tiles; base += kScanThreads) {
-    const int64_t t = base + threadIdx.x;
-    uint32_t c = 0;
-    if (t < L.n_tiles) {
-      const int64_t k = t / per_view, r = t - k * per_view;
-      const int64_t ty = r / L.Tx, tx = r - ty * L.Tx;
-      c = static_cast<uint32_t>(grid[k * (L.Tx + 1) * (L.Ty + 1) + ty * (L.Tx + 1) + tx]);
+  for (int k = 0; k < L.K; ++k) {
+    int32_t* gg = at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * cells;
+    int32_t* g = in_smem ? sg : gg;
+    __syncthreads();
+    if (in_smem)
+      for (int i = threadIdx.x; i < cells; i += kScanThreads) sg[i] = gg[i];
+    __syncthreads();
+    for (int y = threadIdx.x; y < L.Ty; y += kScanThreads) {
+      int32_t acc = 0;
+      for (int x = 0; x <= L.Tx; ++x) {
+        acc += g[y * stride + x];
+        g[y * stride + x] = acc;
+      }
     }
-    uint64_t tot;
-    const uint64_t incl = block_inclusive_scan1024(c, tmp, &tot);
-    if (t < L.n_tiles) {
-      // an empty tile's range is [0, 0)
-      const uint64_t start = c ? carry + incl - c : 0, end = c ? carry + incl : 0;
-      ranges[2 * t] = static_cast<uint32_t>(start < n ? start : n);
-      ranges[2 * t + 1] = static_cast<uint32_t>(end < n ? end : n);
-      if (c)
-        for (int p = 0; p < L.passes; ++p)
-          atomicAdd(&s_hist[p * 256 + ((static_cast<uint32_t>(t) >> (8 * p)) & 0xffu)], c);
+    __syncthreads();
+    for (int64_t base = 0; base < per_view; base += kScanThreads) {
+      const int64_t r = base + threadIdx.x;
+      uint32_t c = 0;
+      if (r < per_view) {
+        const int64_t ty = r / L.Tx, tx = r - ty * L.Tx;
+        c = static_cast<uint32_t>(g[ty * stride + tx]);
+      }
+      uint64_t tot;
+      const uint64_t incl = block_inclusive_scan1024(c, tmp, &tot);
+      if (r < per_view) {
+        const int64_t tg = k * per_view + r;
+        const uint64_t start = c ? carry + incl - c : 0, end = c ? carry + incl : 0;
+        ranges[2 * tg] = static_cast<uint32_t>(start < n ? start : n);
+        ranges[2 * tg + 1] = static_cast<uint32_t>(end < n ? end : n);
+        if (c)
+          for (int p = 0; p < L.passes; ++p)
+            atomicAdd(&s_hist[p * 256 + ((static_cast<uint32_t>(tg) >> (8 * p)) & 0xffu)], c);
+      }
+      carry += tot;
     }
-    carry += tot;
   }
   __syncthreads();
   uint32_t* hist = at<uint32_t>(ws, L.hist);
@@ -362,7 +354,6 @@ cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s) {
   launch(k_sorted_counts, static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s, L, w);
   launch(k_scan_blocks, 1, kScanThreads, 0, s, L, w);
   launch(k_item_offsets, static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s, L, w);
-  launch(k_tile_prefix, L.K, 256, 0, s, L, w);
   launch(k_tile_scan, 1, kScanThreads, 0, s, L, w);
   launch(k_emit_pairs, static_cast<unsigned>(L.n_emit_blocks), kEmitThreads, 0, s, L, w);
   return cudaGetLastError();

@@ -285,8 +285,8 @@ cudaError_t onesweep_passes(const SortArgsT<KeyT>& a, cudaStream_t s) {
 cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s) { return onesweep_passes(a, s); }
 
 int bin_sort_launch_count(const Layout& L) {
-  // counts, scan, item offsets, tile prefix, tile scan, emission; 4 item passes; pair passes
-  return 6 + (L.KN > 0 ? 4 : 0) + L.passes;
+  // counts, scan, item offsets, tile scan, emission; 4 item passes; pair passes
+  return 5 + (L.KN > 0 ? 4 : 0) + L.passes;
 }
 cudaError_t launch_onesweep(const SortArgs32& a, cudaStream_t s) { return onesweep_passes(a, s); }
 

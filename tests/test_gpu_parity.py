@@ -376,7 +376,7 @@ def test_large_item_and_pair_counts():
     torch, api = torch_mods()
     s = make_scene("window500k", n=350_000, K=2, W=96, H=64, f=80.0)
     r, g, ct, out = gpu_render(s.params(), s.cams, s.W, s.H, cap=2_000_000)
-    assert r.layout.bin_sort_launches == 6 + 4 + r.layout.sort_passes
+    assert r.layout.bin_sort_launches == 5 + 4 + r.layout.sort_passes
     d = read_discrete(r)
     orc = oracle.forward(s.params(), s.cams, s.W, s.H)
     L = orc["lists"]

@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the tracking and mapping-window fields")
+    ap.add_argument("--clock-log-dir", default=None,
+                    help="directory for the nvidia-smi clock samples of the timed region (default: a temp dir)")
     ap.add_argument("--px", default=None,
                     help="pixels per thread of the forward and backward compositing kernels, e.g. 2,4, "
                          "with the default chunk depths (default: both autotuned on the workload)")
@@ -221,8 +224,9 @@ def run_ours(args, rank, world):
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
-    clock_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
-    os.makedirs(os.path.dirname(clock_path), exist_ok=True)
+    clock_dir = args.clock_log_dir or tempfile.gettempdir()
+    clock_path = os.path.join(clock_dir, f"bench_clocks_r{rank}.csv")
+    os.makedirs(clock_dir, exist_ok=True)
     with ClockSampler(clock_path) as clk:
         for i in range(args.steps):
             flush.fill_(float(i))

@@ -357,7 +357,7 @@ GS_API gs_status_t gs_keyframe_insert(const gs_camera_t* d_cam, const float* rgb
 
 /* ---------------------------------------------------------------- map-accuracy metrics
  *
- * Sec. IV judges a map by the PSNR and SSIM of its rendered views against the key-frames (and
+ * Sec. IV measures a map by the PSNR and SSIM of its rendered views against the key-frames (and
  * its generation speed by the time a new frame takes to reach its final PSNR / SSIM). The
  * paper gives no formula; these are the standard definitions of the splatting literature:
  *   PSNR of an image = 10 log10(R^2 / MSE) over its C*H*W values (+inf when MSE = 0);

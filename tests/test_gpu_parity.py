@@ -393,6 +393,32 @@ def test_aerial_two_views_fp16_storage_forward_and_backward():
         assert e < GRAD_RTOL, (k, e)
 
 
+@pytest.mark.parametrize("n,K", [(30_000, 1), (65_536, 2), (80_000, 2), (1, 1)])
+def test_depth_sort_sizes(n, K):
+    """Depth-sort sizes: 30k items, 131072 = 2^17 items (a whole number of 4-key and 8-key
+    sort tiles), 160k and a single item; the pair keys, values and ranges equal the oracle's,
+    which fixes the depth order of every emitting item."""
+    s = make_scene("window500k", n=n, K=K, W=96, H=64, f=80.0) if n > 1 else None
+    if s is None:
+        params = (np.array([[0.1, -0.1, 2.0]], np.float32), np.array([[-1.0, -1.2, -1.1]], np.float32),
+                  np.array([[1.0, 0.0, 0.0, 0.0]], np.float32), np.array([2.0], np.float32),
+                  np.array([[0.2, 0.5, 0.7]], np.float32))
+        cams = camera_array(60, 60, 48, 32, np.eye(3), np.zeros(3))
+        W, H = 96, 64
+    else:
+        params, cams, W, H = s.params(), s.cams, s.W, s.H
+    r, g, ct, out = gpu_render(params, cams, W, H)
+    assert r.layout.bin_sort_launches == 5 + 4 + r.layout.sort_passes
+    d = read_discrete(r)
+    orc = oracle.forward(params, cams, W, H)
+    L = orc["lists"]
+    assert d["status"] == 0 and d["total_pairs"] == len(L.keys) > 0
+    np.testing.assert_array_equal(d["keys"], L.keys)
+    np.testing.assert_array_equal(d["vals"], L.vals)
+    np.testing.assert_array_equal(d["ranges"], L.ranges)
+    check_images(to_np(out), orc)
+
+
 def test_large_item_and_pair_counts():
     """700k items (15-key sort tiles for the depth sort) and a 2M pair capacity: keys,
     values and ranges equal the oracle's, and the forward images match."""

@@ -164,8 +164,9 @@ class HostMappingStep(MappingStep):
     pinned host buffers; copies and kernels are one CUDA graph.
 
     The Gaussians and cameras travel as one packed buffer each way and the gradients with the
-    loss as one, so a replay makes three host-to-device copies (the targets on a side stream,
-    overlapping the projection and binning) and one device-to-host copy.
+    loss as one, so a replay makes three host-to-device copies (the packed inputs first; then
+    the targets on a side stream, overlapping the projection and binning) and one
+    device-to-host copy.
 
     Fill the tensors of ``host_in`` (views of the pinned buffers: the five Gaussian arrays,
     ``cams``, ``rgb_t``, ``depth_t``) before ``replay()``; ``host_out`` (the gradients and
@@ -218,13 +219,13 @@ class HostMappingStep(MappingStep):
     def _iteration(self):
         r, o = self.r, self.out
         main = torch.cuda.current_stream()
-        # the key-frame targets are needed only by the forward: they are copied on a side stream
-        # while the Gaussians and cameras go first and the projection and binning run
+        # the Gaussians and cameras go first, alone on the link; the key-frame targets, needed
+        # only by the forward, follow on a side stream while the projection and binning run
+        self._d_pack.copy_(self._h_pack, non_blocking=True)
         self._side.wait_stream(main)
         with torch.cuda.stream(self._side):
             for k in ("rgb_t", "depth_t"):
                 self.dev_in[k].copy_(self.host_in[k], non_blocking=True)
-        self._d_pack.copy_(self._h_pack, non_blocking=True)
         api.gs_project(r.cfg, self.g, self.cams, r.ws)
         api.gs_bin_sort(r.cfg, r.ws)
         main.wait_stream(self._side)

@@ -86,9 +86,20 @@ class ClockSampler:
         try:
             self.f = open(self.out_path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        # the timed region is short (tens of ms): start it only once the sampler is producing
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None and os.path.getsize(self.out_path) == 0:
+            time.sleep(0.01)
+        self.start_line = 0
+        try:
+            with open(self.out_path) as fh:
+                self.start_line = sum(1 for _ in fh)  # samples taken before the timed region
+        except OSError:
+            pass
         return self
 
     def __exit__(self, *a):
@@ -105,7 +116,10 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.out_path):
+        lines = open(self.out_path).read().splitlines()
+        # drop the samples taken before the timed region started (keep them if nothing followed)
+        lines = lines[getattr(self, "start_line", 0):] or lines
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9 or parts[0] != str(device_index):
                 continue

@@ -62,7 +62,9 @@ typedef enum {
   GS_ERR_DEVICE_TIMEOUT = 4,       /* returned by gs_read_status: a bounded device wait gave up */
   GS_ERR_CUDA = 5,                 /* a CUDA runtime call or kernel launch failed */
   GS_ERR_NONFINITE = 6,            /* returned by gs_read_status: non-finite input seen */
-  GS_ERR_SIZE_LIMIT = 7            /* n exceeds a fixed maximum (gs_sort_pairs_noalloc) */
+  GS_ERR_SIZE_LIMIT = 7,           /* n exceeds a fixed maximum (gs_sort_pairs_noalloc) */
+  GS_ERR_INDEX_CHECK = 8           /* returned by gs_read_status: an index check of the debug build
+                                      failed (GS_DEVERR_BOUNDS; the access was skipped) */
 } gs_status_t;
 
 /* Bits of the device error word (gs_read_status). */

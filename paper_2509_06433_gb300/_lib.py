@@ -18,7 +18,8 @@ c_int32, c_int64, c_float, c_void_p, c_size_t, c_uint32 = (ctypes.c_int32, ctype
 
 GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_WORKSPACE_TOO_SMALL", 3: "GS_ERR_CAPACITY_OVERFLOW",
-                4: "GS_ERR_DEVICE_TIMEOUT", 5: "GS_ERR_CUDA", 6: "GS_ERR_NONFINITE", 7: "GS_ERR_SIZE_LIMIT"}
+                4: "GS_ERR_DEVICE_TIMEOUT", 5: "GS_ERR_CUDA", 6: "GS_ERR_NONFINITE", 7: "GS_ERR_SIZE_LIMIT",
+                8: "GS_ERR_INDEX_CHECK"}
 SORT_NOALLOC_MAX_PAIRS = 1048576
 DEVERR_PAIR_OVERFLOW, DEVERR_TIMEOUT, DEVERR_NONFINITE = 0x1, 0x2, 0x4
 GS_F32, GS_BF16, GS_F16 = 0, 1, 2

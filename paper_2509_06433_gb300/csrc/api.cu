@@ -187,6 +187,7 @@ gs_status_t gs_read_status(const gs_config_t* cfg, const void* ws, size_t ws_byt
   if (err_word) *err_word = h.err;
   if (num_pairs) *num_pairs = static_cast<int64_t>(h.total_pairs);
   if (evals) *evals = static_cast<int64_t>(h.evals);
+  if (h.err & GS_DEVERR_BOUNDS) return GS_ERR_INDEX_CHECK;
   if (h.err & GS_DEVERR_PAIR_OVERFLOW) return GS_ERR_CAPACITY_OVERFLOW;
   if (h.err & GS_DEVERR_TIMEOUT) return GS_ERR_DEVICE_TIMEOUT;
   if (h.err & GS_DEVERR_NONFINITE) return GS_ERR_NONFINITE;

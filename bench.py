@@ -173,32 +173,43 @@ def run_ours(args, rank, world):
              "rgb": torch.zeros((s.N, 3), device=dev), "pose": torch.zeros((s.K, 6), device=dev)}
     stream = torch.cuda.current_stream(dev)
     cfg, ws = r.cfg, r.ws
+    from paper_2509_06433_gb300.tracking import fuses_backward
+    fused = fuses_backward(cfg)
     # kernels of ours per step: project; gs_bin_sort (item depth sort, counts, scan, item
-    # offsets, tile prefix, tile scan, emission, pair sort); raster fwd with the fused L1 loss;
-    # raster bwd; project bwd + pose reduction (gradients are stored, not accumulated: no zeroing)
-    n_launch = 1 + r.layout.bin_sort_launches + 1 + 1 + 2
+    # offsets, tile scan, emission, pair sort); raster fwd with the fused L1 loss continuing into
+    # the raster bwd (one launch when both use the same pixels per thread, else two); project bwd
+    # + pose reduction (gradients are stored, not accumulated: no zeroing)
+    n_launch = 1 + r.layout.bin_sort_launches + (1 if fused else 2) + 2
 
     def zero_grads():
         pass  # gs_project_bwd(overwrite=True) stores every gradient
 
-    stage_names = ["project", "bin_sort", "raster_fwd_l1", "raster_bwd", "project_bwd"]
+    stage_names = (["project", "bin_sort", "raster_fwd_l1_bwd", "project_bwd"] if fused else
+                   ["project", "bin_sort", "raster_fwd_l1", "raster_bwd", "project_bwd"])
 
-    def step(ev=None):
-        def mark(i):
+    def step(ev=None, two_calls=False):
+        marks = iter(range(len(stage_names) + 2))
+
+        def mark():
+            i = next(marks)
             if ev is not None:
                 ev[i].record(stream)
-        mark(0)
+        mark()
         api.gs_project(cfg, g, cams, ws, stream)
-        mark(1)
+        mark()
         api.gs_bin_sort(cfg, ws, stream)
-        mark(2)
-        api.gs_raster_fwd_l1(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], rgb_t, depth_t, g_rgb,
-                             g_depth, loss, stream)
-        mark(3)
-        api.gs_raster_bwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth, None, stream)
-        mark(4)
+        mark()
+        if fused and not two_calls:
+            api.gs_raster_fwd_l1_bwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], rgb_t, depth_t, g_rgb,
+                                     g_depth, loss, stream)
+        else:
+            api.gs_raster_fwd_l1(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], rgb_t, depth_t, g_rgb,
+                                 g_depth, loss, stream)
+            mark()
+            api.gs_raster_bwd(cfg, ws, out["rgb"], out["depth"], out["T"], out["last"], g_rgb, g_depth, None, stream)
+        mark()
         api.gs_project_bwd(cfg, g, cams, ws, grads, stream, overwrite=True)
-        mark(5)
+        mark()
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
@@ -229,6 +240,14 @@ def run_ours(args, rank, world):
         step(evs[i])
     torch.cuda.synchronize(dev)
     stage_ms = {nm: [e[j].elapsed_time(e[j + 1]) for e in evs] for j, nm in enumerate(stage_names)}
+    # the same with the forward and backward compositing as two launches (for comparison)
+    two = ["project", "bin_sort", "raster_fwd_l1", "raster_bwd", "project_bwd"]
+    evs2 = [[torch.cuda.Event(enable_timing=True) for _ in range(len(two) + 1)] for _ in range(n_stage)]
+    for i in range(n_stage):
+        flush.fill_(float(i))
+        step(evs2[i], two_calls=True)
+    torch.cuda.synchronize(dev)
+    two_ms = {nm: statistics.median(e[j].elapsed_time(e[j + 1]) for e in evs2) for j, nm in enumerate(two)}
 
     # ---- the timed value: the whole mapping iteration replayed from one CUDA graph,
     # CUDA events around each replay, L2 flushed (256 MB write) between replays
@@ -334,6 +353,7 @@ def run_ours(args, rank, world):
         "blended_evals_per_step": blended,
         "gaussian_pixel_evals_per_s": evals * iters / (total_ms / 1e3),
         "stage_ms_median": {k: round(v, 5) for k, v in med.items()},
+        "stage_ms_median_two_launch_compositing": {k: round(v, 5) for k, v in two_ms.items()},
         "roofline": roof,
         "mapping_with_adam": adam,
         "autotune": {"fwd_ms": _keys(tuned["fwd"]), "bwd_ms": _keys(tuned["bwd"]),
@@ -791,11 +811,10 @@ def roofline(stage, ms_list, counts, pairs, s, r):
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
     t = statistics.mean(ms_list) / 1e3
-    if stage in ("raster_fwd", "raster_fwd_l1", "raster_bwd"):
-        if stage != "raster_bwd":
-            flop = FLOP_EVAL * counts["evals"] + FLOP_FWD_BLEND * counts["blended"]
-        else:
-            flop = FLOP_EVAL * counts["evals_bwd"] + FLOP_BWD_BLEND * counts["blended"]
+    if stage in ("raster_fwd", "raster_fwd_l1", "raster_bwd", "raster_fwd_l1_bwd"):
+        fwd = FLOP_EVAL * counts["evals"] + FLOP_FWD_BLEND * counts["blended"]
+        bwd = FLOP_EVAL * counts["evals_bwd"] + FLOP_BWD_BLEND * counts["blended"]
+        flop = {"raster_bwd": bwd, "raster_fwd_l1_bwd": fwd + bwd}.get(stage, fwd)
         return {"kernel": stage, "bound": "alu", "achieved": flop / t / 1e12, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": flop / t / 1e12 / fp32_peak_tflops, "traffic": measured_traffic(stage),
                 "peak_source": f"FP32 = {sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz (max clock; {src} peaks file)"}

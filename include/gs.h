@@ -238,6 +238,19 @@ GS_API gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_
                              float* T_final, int32_t* last, const float* rgb_target, const float* depth_target,
                              float* dL_drgb, float* dL_ddepth, float* d_loss, void* stream);
 
+/* gs_raster_fwd_l1 and then gs_raster_bwd (dL_dT = NULL) in one launch: each tile's block runs
+ * the backward pass of its tile as soon as its forward and loss are done, from the loss gradient,
+ * colour, depth and last contributor of its pixels held in registers (no wait for every tile's
+ * forward, no reload of those images). Writes everything both calls write: rgb, depth, T_final,
+ * last, dL/drgb, dL/ddepth, d_loss and the per-pair gradient records that gs_project_bwd
+ * consumes; bit for bit the results of the two calls when gs_config_t.bwd_px_per_thread equals
+ * fwd_px_per_thread (the backward phase runs with the forward's pixels per thread). The mapping
+ * step's form of the forward and backward compositing (Sec. II-B). */
+GS_API gs_status_t gs_raster_fwd_l1_bwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                                         float* T_final, int32_t* last, const float* rgb_target,
+                                         const float* depth_target, float* dL_drgb, float* dL_ddepth, float* d_loss,
+                                         void* stream);
+
 /* gs_raster_fwd occluded by an external surface (the digital twin's virtual objects; the
  * viewer composites the map against them): ext_depth [K,H,W] (camera depth of the surface per
  * pixel, +inf or very large = none), ext_rgb [K,3,H,W] (its colour; NULL = black). Per pixel

@@ -26,7 +26,7 @@ GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 
 #: every entry point declared in include/gs.h
 EXPORTS = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
-           "gs_raster_fwd", "gs_raster_fwd_stats", "gs_raster_fwd_l1", "gs_raster_fwd_occluded", "gs_loss_l1", "gs_raster_bwd", "gs_project_bwd", "gs_screen_grads",
+           "gs_raster_fwd", "gs_raster_fwd_stats", "gs_raster_fwd_l1", "gs_raster_fwd_l1_bwd", "gs_raster_fwd_occluded", "gs_loss_l1", "gs_raster_bwd", "gs_project_bwd", "gs_screen_grads",
            "gs_pose_adam_step", "gs_sort_pairs_tmp_size", "gs_sort_pairs", "gs_sort_diag_withheld_tile",
            "gs_sort_pairs_noalloc", "gs_map_adam_state_size", "gs_map_adam_step", "gs_keyframe_tmp_size",
            "gs_keyframe_insert", "gs_metrics_tmp_size", "gs_psnr", "gs_ssim",
@@ -95,6 +95,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                 "gs_raster_fwd": [P, P, c_size_t, P, P, P, P, P],
                 "gs_raster_fwd_stats": [P, P, c_size_t, P, P, P, P, P],
                 "gs_raster_fwd_l1": [P, P, c_size_t, P, P, P, P, P, P, P, P, P, P],
+                "gs_raster_fwd_l1_bwd": [P, P, c_size_t, P, P, P, P, P, P, P, P, P, P],
                 "gs_raster_fwd_occluded": [P, P, c_size_t, P, P, P, P, P, P, P],
                 "gs_loss_l1": [P, P, P, P, P, P, P, P, P, c_size_t, P],
                 "gs_raster_bwd": [P, P, c_size_t, P, P, P, P, P, P, P, P],

@@ -113,6 +113,13 @@ def gs_raster_fwd_l1(cfg, ws, rgb, depth, T_final, last, rgb_target, depth_targe
          _p(rgb_target), _p(depth_target), _p(dL_drgb), _p(dL_ddepth), _p(loss), _s(stream))
 
 
+def gs_raster_fwd_l1_bwd(cfg, ws, rgb, depth, T_final, last, rgb_target, depth_target, dL_drgb, dL_ddepth, loss,
+                         stream=None):
+    """gs_raster_fwd_l1 followed by gs_raster_bwd (no dL/dT) in one launch."""
+    call("gs_raster_fwd_l1_bwd", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
+         _p(rgb_target), _p(depth_target), _p(dL_drgb), _p(dL_ddepth), _p(loss), _s(stream))
+
+
 def gs_raster_fwd_occluded(cfg, ws, rgb, depth, T_final, last, ext_depth, ext_rgb=None, stream=None):
     call("gs_raster_fwd_occluded", ctypes.byref(cfg), _p(ws), ws.numel(), _p(rgb), _p(depth), _p(T_final), _p(last),
          _p(ext_depth), _p(ext_rgb), _s(stream))

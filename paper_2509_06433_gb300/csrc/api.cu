@@ -265,6 +265,18 @@ gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_bytes, 
   return launched(launch_raster_fwd(L, ws, rgb, depth, T_final, last, false, &F, static_cast<cudaStream_t>(stream)));
 }
 
+gs_status_t gs_raster_fwd_l1_bwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
+                                 float* T_final, int32_t* last, const float* rgb_target, const float* depth_target,
+                                 float* dL_drgb, float* dL_ddepth, float* d_loss, void* stream) {
+  const TraceRange trace_("gs_raster_fwd_l1_bwd");
+  Layout L;
+  gs_status_t st = check(cfg, ws, ws_bytes, &L);
+  if (st != GS_OK) return st;
+  if (!rgb || !depth || !rgb_target || !depth_target || !dL_drgb || !dL_ddepth || !d_loss) return GS_ERR_INVALID_ARG;
+  const FusedLossArgs F{rgb_target, depth_target, dL_drgb, dL_ddepth, d_loss};
+  return launched(launch_raster_fwd_l1_bwd(L, ws, rgb, depth, T_final, last, F, static_cast<cudaStream_t>(stream)));
+}
+
 gs_status_t gs_loss_l1(const gs_config_t* cfg, const float* rgb, const float* depth, const float* rgb_target,
                        const float* depth_target, float* dL_drgb, float* dL_ddepth, float* d_loss, void* ws,
                        size_t ws_bytes, void* stream) {

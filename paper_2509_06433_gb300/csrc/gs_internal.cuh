@@ -214,6 +214,9 @@ struct FusedLossArgs {
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
                               bool stats, const FusedLossArgs* loss, cudaStream_t s, const float* ext_depth = nullptr,
                               const float* ext_rgb = nullptr);
+// the loss-fused forward continuing, block by block, into the backward pass (dL_dT = 0)
+cudaError_t launch_raster_fwd_l1_bwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
+                                     const FusedLossArgs& loss, cudaStream_t s);
 cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const float* depth, const float* T_final,
                               const int32_t* last, const float* dL_drgb, const float* dL_ddepth, const float* dL_dT,
                               cudaStream_t s);

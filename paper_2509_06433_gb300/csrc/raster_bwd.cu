@@ -1,63 +1,10 @@
-// Backward compositing (gs_raster_bwd); see raster_common.cuh for the staging and the
-// opacity test both compositing kernels share.
-#include "raster_common.cuh"
+// Backward compositing (gs_raster_bwd): loads the forward outputs and the upstream gradients
+// of its pixels, then runs the tile's backward sweep (raster_sweep.cuh).
+#include "raster_sweep.cuh"
 
 namespace gs {
 namespace {
 
-// ============================================================================ backward
-
-// Sum of 10 values over a warp, leaving each value in some lane (12 shuffles): halves of
-// the value set are exchanged across lane bit 4 (5 pairs), then bit 3 (2 pairs + 1 plain),
-// bit 2 (1 pair + 1 plain), bit 1 (1 pair), bit 0 (plain). On return, lane l with l & 1 == 0
-// holds value reduce10_index(l) when (l & 2) == 0 or (l & 12) == 0.
-__device__ __forceinline__ float warp_reduce10(const float (&x)[10], int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-  float y[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const float send = b4 ? x[i] : x[i + 5];
-    const float keep = b4 ? x[i + 5] : x[i];
-    y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  float z[3];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float send = b3 ? y[2 * i] : y[2 * i + 1];
-    const float keep = b3 ? y[2 * i + 1] : y[2 * i];
-    z[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  z[2] = y[4] + __shfl_xor_sync(0xffffffffu, y[4], 8);
-  float w[2];
-  {
-    const float send = b2 ? z[0] : z[1];
-    const float keep = b2 ? z[1] : z[0];
-    w[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  w[1] = z[2] + __shfl_xor_sync(0xffffffffu, z[2], 4);
-  float u;
-  {
-    const float send = b1 ? w[0] : w[1];
-    const float keep = b1 ? w[1] : w[0];
-    u = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  return u + __shfl_xor_sync(0xffffffffu, u, 1);
-}
-__device__ __forceinline__ int reduce10_index(int lane) {
-  const int half = (lane & 16) ? 5 : 0;
-  return (lane & 2) ? half + 4 : half + ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1);
-}
-__device__ __forceinline__ bool reduce10_writer(int lane) { return !(lane & 1) && (!(lane & 2) || !(lane & 12)); }
-
-// Gradient record layout (floats): 0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 dz, 6 do, 7 dr, 8 dg, 9 db.
-//
-// Per pixel, with dpow = dL/dpower / ln 2 (zero where the splat is skipped or clamped) and
-// (dx, dy) the offset mean - pixel centre, the geometric terms are sums over the pixels of
-//   du = ln2 (2 qa dx + qb dy) dpow,  dv = ln2 (qb dx + 2 qc dy) dpow,
-//   dA = -dx^2 dpow / 2,  dB = -dx dy dpow,  dC = -dy^2 dpow / 2,  do = dpow / opacity.
-// A lane's pixels share dx, so it keeps only P0 = sum dpow, P1 = sum dy dpow, P2 = sum dy^2 dpow
-// and the warp reduces R = (dx P0, P1, dx^2 P0, dx P1, P2, P0); the splat's coefficients
-// qa, qb, qc, opacity are applied once per pair when the warp partials are summed.
 template <int PX, int CH>
 __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8_t* __restrict__ ws,
                                                                  const float* __restrict__ rgb,
@@ -68,32 +15,16 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
                                                                  const float* __restrict__ g_depth,
                                                                  const float* __restrict__ g_T) {
   pdl_wait();
-  constexpr int kThreads = kTilePixels / PX;
-  constexpr int kWarps = kThreads / 32;
-  __shared__ Stage<CH> S;
-  __shared__ uint32_t s_slot[CH];
-  __shared__ float s_part[kWarps][CH][10];
-  __shared__ int s_maxlast[kWarps];
+  __shared__ BwdSmem<PX, CH> M;
   const TileCoord tc = tile_coord(L, blockIdx.x);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * PX;
   const int px = tc.tx * kTile + lx, py = tc.ty * kTile + ly;
-  const uint64_t* keys = at<uint64_t>(ws, (L.passes & 1) ? L.keys[1] : L.keys[0]);
-  const uint32_t* slots = at<uint32_t>(ws, (L.passes & 1) ? L.vals[1] : L.vals[0]);  // emission index = record slot
   const uint2 rg = at<uint2>(ws, L.ranges)[blockIdx.x];
-  const float ox = static_cast<float>(tc.tx * kTile), oy = static_cast<float>(tc.ty * kTile);
-  const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
-  const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
-  float* pair_grads = at<float>(ws, L.pair_grads);
-  uint32_t* pair_valid = at<uint32_t>(ws, L.pair_valid);
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
-
-  float T[PX], Sg[PX], hT[PX], gr[PX], gg[PX], gb[PX], gd[PX];
+  float Sg[PX], hT[PX], gr[PX], gg[PX], gb[PX], gd[PX];
   int last[PX];
-  int wl = 0;
 #pragma unroll
   for (int q = 0; q < PX; ++q) {
-    T[q] = 1.0f;
     Sg[q] = hT[q] = gr[q] = gg[q] = gb[q] = gd[q] = 0.0f;
     last[q] = 0;
     const int y = py + q;
@@ -104,114 +35,13 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8
       gg[q] = g_rgb[c0 + HW];
       gb[q] = g_rgb[c0 + 2 * HW];
       gd[q] = g_depth[tc.k * HW + pix];
-      Sg[q] = gr[q] * rgb[c0] + gg[q] * rgb[c0 + HW] + gb[q] * rgb[c0 + 2 * HW] + gd[q] * depth[tc.k * HW + pix];
+      Sg[q] = weighted_colour(gr[q], gg[q], gb[q], gd[q], rgb[c0], rgb[c0 + HW], rgb[c0 + 2 * HW],
+                              depth[tc.k * HW + pix]);
       if (g_T) hT[q] = g_T[tc.k * HW + pix] * T_final[tc.k * HW + pix];
       last[q] = last_in[tc.k * HW + pix];
-      wl = max(wl, last[q]);
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-  const int warp_last = wl;  // this warp's pixels need list positions [0, warp_last)
-  if (lane == 0) s_maxlast[warp] = wl;
-  __syncthreads();
-  int max_last = 0;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) max_last = max(max_last, s_maxlast[w]);
-  const uint32_t stop = min(rg.y, rg.x + static_cast<uint32_t>(max_last));
-  const int idx = reduce10_index(lane);
-  const bool writer = reduce10_writer(lane);
-  constexpr float kLn2 = 0.6931471805599453f;
-
-  for (uint32_t base = rg.x; base < stop; base += CH) {
-    for (int jj = threadIdx.x; jj < CH; jj += kThreads) {
-      const uint32_t i = base + jj;
-      if (i < stop) {
-        stage_splat(S, jj, L, ws, keys, i, tc.k, ox, oy);
-        s_slot[jj] = slots[i];
-      }
-    }
-    for (int e = threadIdx.x; e < kWarps * CH * 10; e += kThreads) (&s_part[0][0][0])[e] = 0.0f;
-    __syncthreads();
-    const int n = min(CH, static_cast<int>(stop - base));
-    const int pos0 = static_cast<int>(base - rg.x);
-    const int nw = min(n, warp_last - pos0);  // splats of this chunk this warp must visit
-    for (int j = 0; j < nw; ++j) {
-      if (!(S.rows[j] & wrows)) continue;
-      const float4 A = S.A[j], B = S.B[j];
-      const float dx = __fsub_rn(A.x, pxc);
-      const Column col = splat_column(A, B, dx);
-      const int pos = pos0 + j;
-      // phase 1: opacity and keep/skip decision for the thread's pixels
-      Alpha a[PX];
-      float dy[PX];
-      bool okq[PX];
-      bool contrib = false;
-#pragma unroll
-      for (int q = 0; q < PX; ++q) {
-        dy[q] = __fsub_rn(A.y, pyc + static_cast<float>(q));
-        a[q] = splat_alpha(B, col, dy[q]);
-        okq[q] = a[q].keep && (pos < last[q]);
-        contrib = contrib || okq[q];
-      }
-      // phase 2 (skipped when no pixel of the warp keeps the splat): gradient terms
-      if (!__any_sync(0xffffffffu, contrib)) continue;
-      const float4 C = S.C[j];
-      float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f, cz = 0.0f, cr = 0.0f, cgr = 0.0f, cb = 0.0f;
-#pragma unroll
-      for (int q = 0; q < PX; ++q) {
-        // aok = alpha for a kept splat, else 0: then w = 0 and Sg, T stay bit for bit unchanged
-        const bool ok = okq[q];
-        const bool open = ok && !(a[q].raw > kAlphaMax);  // the 0.99 clamp passes no gradient
-        const float Tq = T[q];
-        const float aok = ok ? a[q].alpha : 0.0f;
-        const float w = __fmul_rn(aok, Tq);
-        const float cgz = C.x * gr[q] + C.y * gg[q] + C.z * gb[q] + B.z * gd[q];
-        const float sg = __fmaf_rn(-cgz, w, Sg[q]);  // colour/depth behind this splat, weighted by dL/dpixel
-        const float dalpha = Tq * cgz - __fdividef(sg + hT[q], 1.0f - a[q].alpha);
-        const float dpow = (open ? a[q].alpha : 0.0f) * dalpha;
-        const float ydp = dy[q] * dpow;
-        P0 += dpow;
-        P1 += ydp;
-        P2 = fmaf(dy[q], ydp, P2);
-        cz = fmaf(w, gd[q], cz);
-        cr = fmaf(w, gr[q], cr);
-        cgr = fmaf(w, gg[q], cgr);
-        cb = fmaf(w, gb[q], cb);
-        Sg[q] = sg;
-        T[q] = __fmaf_rn(-Tq, aok, Tq);
-      }
-      const float dxP0 = dx * P0;
-      const float v[10] = {dxP0, P1, dx * dxP0, dx * P1, P2, cz, P0, cr, cgr, cb};
-      const float r = warp_reduce10(v, lane);
-      if (writer) s_part[warp][j][idx] = r;
-    }
-    __syncthreads();
-    for (int jj = threadIdx.x; jj < n; jj += kThreads) {
-      float R[10];
-#pragma unroll
-      for (int q = 0; q < 10; ++q) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) acc += s_part[w][jj][q];
-        R[q] = acc;
-      }
-      // R = (sum dx P0, sum P1, sum dx^2 P0, sum dx P1, sum P2, dz, sum P0, dr, dg, db)
-      const float4 A = S.A[jj], B = S.B[jj];
-      const float du = kLn2 * (2.0f * A.z * R[0] + A.w * R[1]);
-      const float dv = kLn2 * (2.0f * B.x * R[1] + A.w * R[0]);
-      const float dop = R[6] != 0.0f ? R[6] / B.y : 0.0f;
-      const uint32_t slot = s_slot[jj];
-      if (!GS_INDEX_OK(static_cast<int64_t>(slot) < L.cap, &at<Status>(ws, L.status)->err)) continue;
-      float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(slot) * kPairGradStride);
-      dst[0] = make_float4(du, dv, -0.5f * R[2], -R[3]);
-      dst[1] = make_float4(-0.5f * R[4], R[5], dop, R[7]);
-      dst[2] = make_float4(R[8], R[9], 0.0f, 0.0f);
-      atomicOr(&pair_valid[slot >> 5], 1u << (slot & 31));
-    }
-    __syncthreads();
-  }
-  // pairs behind every pixel's last contributor get no record: their bit stays clear
+  bwd_sweep<PX, CH>(M, L, ws, tc, rg, Sg, hT, gr, gg, gb, gd, last);
   pdl_trigger();
 }
 

@@ -1,6 +1,7 @@
-// Forward compositing (gs_raster_fwd, gs_raster_fwd_stats, gs_raster_fwd_l1); see
-// raster_common.cuh for the staging and the opacity test both compositing kernels share.
-#include "raster_common.cuh"
+// Forward compositing (gs_raster_fwd, gs_raster_fwd_stats, gs_raster_fwd_l1, and with the
+// backward pass fused, gs_raster_fwd_l1_bwd); see raster_common.cuh for the staging and the
+// opacity test both compositing kernels share.
+#include "raster_sweep.cuh"
 
 namespace gs {
 namespace {
@@ -37,7 +38,11 @@ struct Occlusion {
   const float* rgb;
 };
 
-template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false>
+// CHB > 0 (with LOSS only): the block continues into the backward pass of its tile (the sweep
+// of gs_raster_bwd, staging CHB splats per chunk) as soon as its forward is done, from the loss
+// gradient, colour, depth and last contributor of its pixels still in registers; the results
+// equal gs_raster_fwd_l1 followed by gs_raster_bwd (dL_dT = NULL) with PX pixels per thread.
+template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false, int CHB = 0>
 __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
                                                                  float* __restrict__ out_rgb,
                                                                  float* __restrict__ out_depth,
@@ -46,6 +51,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
                                                                  uint64_t* __restrict__ evals_out,
                                                                  uint64_t* __restrict__ blended_out, FusedLoss F,
                                                                  Occlusion O) {
+  static_assert(CHB == 0 || (LOSS && !STATS && !OCC), "the fused backward follows the loss-fused forward");
   pdl_wait();
   constexpr int kThreads = kTilePixels / PX;
   constexpr int kWarps = kThreads / 32;
@@ -148,9 +154,12 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
       }
     }
   }
-  pdl_trigger();
+  if (CHB == 0) pdl_trigger();  // (the fused backward lets the next grid launch only at its end)
   const int64_t HW = static_cast<int64_t>(L.H) * L.W;
   const int len = static_cast<int>(rg.y - rg.x);
+  float bg[CHB > 0 ? PX : 1][4];  // the loss gradient of each pixel (fused backward)
+#pragma unroll
+  for (int q = 0; q < (CHB > 0 ? PX : 1); ++q) bg[q][0] = bg[q][1] = bg[q][2] = bg[q][3] = 0.0f;
   uint32_t evals = 0;
   float loss = 0.0f;
   const float inv3 = 1.0f / (3.0f * static_cast<float>(HW));
@@ -185,11 +194,15 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
         for (int ch = 0; ch < 3; ++ch) {
           const float d = c[ch] - tgt[LOSS ? q : 0][ch];
           loss += fabsf(d) * inv3;
-          F.g_rgb[c0 + ch * HW] = sgn(d) * inv3;
+          const float gv = sgn(d) * inv3;
+          F.g_rgb[c0 + ch * HW] = gv;
+          if (CHB > 0) bg[CHB > 0 ? q : 0][ch] = gv;
         }
         const float d = cd[q] - tgt[LOSS ? q : 0][3];
         loss += fabsf(d) * invd;
-        F.g_depth[tc.k * HW + pix] = sgn(d) * invd;
+        const float gv = sgn(d) * invd;
+        F.g_depth[tc.k * HW + pix] = gv;
+        if (CHB > 0) bg[CHB > 0 ? q : 0][3] = gv;
       }
     }
   }
@@ -226,6 +239,27 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
       }
     }
   }
+  if constexpr (CHB > 0) {
+    // the backward pass of this tile, from registers: the weighted colour behind the first
+    // splat is the loss gradient applied to the pixel's output (no dL/dT_final term)
+    __shared__ BwdSmem<PX, CHB> M;
+    float Sg[PX], hT[PX], gr[PX], gg[PX], gb[PX], gd[PX];
+    int lst[PX];
+#pragma unroll
+    for (int q = 0; q < PX; ++q) {
+      gr[q] = bg[q][0];
+      gg[q] = bg[q][1];
+      gb[q] = bg[q][2];
+      gd[q] = bg[q][3];
+      const bool in = px < L.W && py + q < L.H;
+      Sg[q] = in ? weighted_colour(gr[q], gg[q], gb[q], gd[q], cr[q], cg[q], cb[q], cd[q]) : 0.0f;
+      hT[q] = 0.0f;
+      lst[q] = in ? last[q] : 0;
+    }
+    // the workspace is the caller's mutable buffer; the forward only reads it
+    bwd_sweep<PX, CHB>(M, L, const_cast<uint8_t*>(ws), tc, rg, Sg, hT, gr, gg, gb, gd, lst);
+    pdl_trigger();
+  }
   if (STATS) {
     uint32_t e = evals, c = blended;
 #pragma unroll
@@ -251,6 +285,40 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
 }
 
 }  // namespace
+
+cudaError_t launch_raster_fwd_l1_bwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
+                                     const FusedLossArgs& loss, cudaStream_t s) {
+  Status* st = at<Status>(ws, L.status);
+  if (L.n_tiles == 0) {
+    cudaMemsetAsync(loss.d_loss, 0, sizeof(float), s);
+    return cudaGetLastError();
+  }
+  const unsigned grid = static_cast<unsigned>(L.n_tiles);
+  const uint8_t* w = static_cast<const uint8_t*>(ws);
+  uint64_t *ev = &st->evals, *cp = &st->composited;
+  const FusedLoss F{loss.rgb_t, loss.depth_t, loss.g_rgb, loss.g_depth, at<float>(ws, L.tile_loss), &st->loss_ctr,
+                    loss.d_loss};
+  const int px = pick_px(L.fwd_px, kDefaultFwdPx);
+  const int ch = pick_chunk(L.fwd_chunk, 64, 256, kFwdChunk);
+  // the backward phase stages kBwdChunk splats per chunk (the chunk depth changes no result)
+#define GS_FB(P, C)                                                                                          \
+  launch(k_raster_fwd<P, C, false, true, false, kBwdChunk>, grid, kTilePixels / P, 0, s, L, w, rgb, depth, T_final, \
+         last, ev, cp, F, Occlusion{})
+#define GS_FB_CH(P)                  \
+  switch (ch) {                      \
+    case 64: GS_FB(P, 64); break;    \
+    case 256: GS_FB(P, 256); break;  \
+    default: GS_FB(P, 128); break;   \
+  }
+  switch (px) {
+    case 1: GS_FB_CH(1); break;
+    case 2: GS_FB_CH(2); break;
+    default: GS_FB_CH(4); break;
+  }
+#undef GS_FB_CH
+#undef GS_FB
+  return cudaGetLastError();
+}
 
 cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* depth, float* T_final, int32_t* last,
                               bool stats, const FusedLossArgs* loss, cudaStream_t s, const float* ext_depth,

@@ -17,6 +17,25 @@ import torch
 from . import api
 
 
+def fuses_backward(cfg) -> bool:
+    """Whether the forward and backward compositing run as one launch (gs_raster_fwd_l1_bwd):
+    when both use the same pixels per thread, so the results are those of the two calls bit for bit."""
+    px = lambda v: v if v in (1, 2, 4) else 2  # noqa: E731  (0 = the library default, 2)
+    return px(cfg.fwd_px_per_thread) == px(cfg.bwd_px_per_thread)
+
+
+def fwd_l1_bwd(r, out, rgb_t, depth_t, g_rgb, g_depth, loss, stream=None):
+    """Forward with the fused L1 loss, then the backward compositing: one launch
+    (gs_raster_fwd_l1_bwd) when fuses_backward(r.cfg), else gs_raster_fwd_l1 + gs_raster_bwd."""
+    c = r.cfg
+    args = (c, r.ws, out["rgb"], out["depth"], out["T"], out["last"])
+    if fuses_backward(c):
+        api.gs_raster_fwd_l1_bwd(*args, rgb_t, depth_t, g_rgb, g_depth, loss, stream)
+    else:
+        api.gs_raster_fwd_l1(*args, rgb_t, depth_t, g_rgb, g_depth, loss, stream)
+        api.gs_raster_bwd(*args, g_rgb, g_depth, None, stream)
+
+
 class _Captured:
     def __init__(self, graph: bool):
         self.use_graph = graph
@@ -81,9 +100,7 @@ class Tracker(_Captured):
         r, o = self.r, self.out
         api.gs_project(r.cfg, self.g, self.cams, r.ws)
         api.gs_bin_sort(r.cfg, r.ws)
-        api.gs_raster_fwd_l1(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.rgb_obs, self.depth_obs,
-                             self.g_rgb, self.g_depth, self.loss)
-        api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
+        fwd_l1_bwd(r, o, self.rgb_obs, self.depth_obs, self.g_rgb, self.g_depth, self.loss)
         api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, {"pose": self.pose_grad}, overwrite=True)
         api.gs_pose_adam_step(self.cams, self.pose_grad, self.state, self.lr[0], self.lr[1], zero_grad=False)
 
@@ -148,9 +165,7 @@ class MappingStep(_Captured):
         r, o = self.r, self.out
         api.gs_project(r.cfg, self.g, self.cams, r.ws)
         api.gs_bin_sort(r.cfg, r.ws)
-        api.gs_raster_fwd_l1(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.rgb_t, self.depth_t,
-                             self.g_rgb, self.g_depth, self.loss)
-        api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
+        fwd_l1_bwd(r, o, self.rgb_t, self.depth_t, self.g_rgb, self.g_depth, self.loss)
         api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, self.grads, overwrite=True)
         if self.optimizer is not None:
             self.optimizer.step(self.grads)
@@ -229,9 +244,7 @@ class HostMappingStep(MappingStep):
         api.gs_project(r.cfg, self.g, self.cams, r.ws)
         api.gs_bin_sort(r.cfg, r.ws)
         main.wait_stream(self._side)
-        api.gs_raster_fwd_l1(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.rgb_t, self.depth_t,
-                             self.g_rgb, self.g_depth, self.loss)
-        api.gs_raster_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], self.g_rgb, self.g_depth)
+        fwd_l1_bwd(r, o, self.rgb_t, self.depth_t, self.g_rgb, self.g_depth, self.loss)
         api.gs_project_bwd(r.cfg, self.g, self.cams, r.ws, self.grads, overwrite=True)
         self._h_out.copy_(self._d_out, non_blocking=True)
 

@@ -26,7 +26,10 @@ def test_bench_line():
     e = d["e2e"]
     assert 0 < e["value"] < d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] > 10_000_000 and e["d2h_bytes_per_step"] > 5_000_000
-    assert d["gpu_launches"] == 20 * (5 + 11)  # per step: 5 launches + the 11 of gs_bin_sort at 640x480
+    # per step: project, the 11 kernels of gs_bin_sort at 640x480, the fused forward + backward
+    # compositing, the backward projection and its pose reduction
+    assert d["gpu_launches"] == 20 * (1 + 11 + 1 + 2)
+    assert d["roofline"]["kernel"] == "raster_fwd_l1_bwd"
     r = d["roofline"]
     assert r["bound"] in ("alu", "hbm") and r["unit"] in ("TFLOP/s", "GB/s")
     assert 0 < r["frac"] < 1.5 and abs(r["achieved"] / r["peak"] - r["frac"]) < 1e-9

@@ -339,6 +339,55 @@ def test_backward_on_deep_lists():
         assert e < GRAD_RTOL, (k, e)
 
 
+@pytest.mark.parametrize("name", ["ragged_tiny", "map100k", "window_k3"])
+def test_fused_forward_backward_equals_the_two_calls(name):
+    """gs_raster_fwd_l1_bwd (each tile's block continues into its backward pass) equals
+    gs_raster_fwd_l1 followed by gs_raster_bwd bit for bit: images, T, last, loss gradient images,
+    loss and, through gs_project_bwd, every parameter and pose gradient, for every pixels-per-
+    thread and forward chunk depth."""
+    torch, api = torch_mods()
+    s = scene(name)
+    r, g, ct, _, _ = gpu_fwd(name)
+    rgb_t = torch.as_tensor(random_image(21, (s.K, 3, s.H, s.W))).cuda().abs()
+    depth_t = torch.as_tensor(random_image(22, (s.K, s.H, s.W))).cuda().abs() * 5.0
+
+    def grads_of():
+        d = "cuda"
+        gr = {"means": torch.empty((s.N, 3), device=d), "log_scales": torch.empty((s.N, 3), device=d),
+              "quats": torch.empty((s.N, 4), device=d), "opacity_logits": torch.empty(s.N, device=d),
+              "rgb": torch.empty((s.N, 3), device=d), "pose": torch.empty((s.K, 6), device=d)}
+        api.gs_project_bwd(r.cfg, g, ct, r.ws, gr, overwrite=True)
+        return gr
+
+    def run(fused):
+        r.project_and_sort(g, ct)  # fresh binning: clears the record bits of the previous run
+        o = r.new_outputs()
+        g_rgb, g_depth, loss = torch.empty_like(o["rgb"]), torch.empty_like(o["depth"]), torch.empty(1, device="cuda")
+        args = (r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"])
+        if fused:
+            api.gs_raster_fwd_l1_bwd(*args, rgb_t, depth_t, g_rgb, g_depth, loss)
+        else:
+            api.gs_raster_fwd_l1(*args, rgb_t, depth_t, g_rgb, g_depth, loss)
+            api.gs_raster_bwd(*args, g_rgb, g_depth)
+        res = {**{k: v.clone() for k, v in o.items()}, "g_rgb": g_rgb, "g_depth": g_depth, "loss": loss}
+        res.update({"d_" + k: v for k, v in grads_of().items()})
+        return res
+
+    try:
+        for px, fch in ((1, 128), (2, 64), (2, 256), (4, 64), (4, 128), (4, 256)):
+            r.cfg.fwd_px_per_thread = r.cfg.bwd_px_per_thread = px
+            r.cfg.fwd_chunk = fch
+            a, b = run(False), run(True)
+            torch.cuda.synchronize()
+            assert r.status()[0] == 0
+            for k in a:
+                assert torch.equal(a[k], b[k]), (name, px, fch, k)
+            assert torch.count_nonzero(a["d_means"]).item() > 0
+    finally:
+        r.cfg.fwd_px_per_thread = r.cfg.bwd_px_per_thread = 0
+        r.cfg.fwd_chunk = 0
+
+
 def test_counting_forward_equals_plain_forward():
     """gs_raster_fwd_stats takes the same decisions and writes the same outputs as
     gs_raster_fwd (bit for bit); only it updates the evaluation counters."""

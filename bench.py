@@ -174,7 +174,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     cfg, ws = r.cfg, r.ws
     from paper_2509_06433_gb300.tracking import fuses_backward
-    fused = fuses_backward(cfg)
+    fused = fuses_backward(r)
     # kernels of ours per step: project; gs_bin_sort (item depth sort, counts, scan, item
     # offsets, tile scan, emission, pair sort); raster fwd with the fused L1 loss continuing into
     # the raster bwd (one launch when both use the same pixels per thread, else two); project bwd
@@ -357,7 +357,9 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "mapping_with_adam": adam,
         "autotune": {"fwd_ms": _keys(tuned["fwd"]), "bwd_ms": _keys(tuned["bwd"]),
-                     "px_per_thread": list(tuned["choice"]), "chunk": list(tuned.get("chunks", (0, 0)))},
+                     "px_per_thread": list(tuned["choice"]), "chunk": list(tuned.get("chunks", (0, 0))),
+                     "fused_compositing": fused, "two_launch_ms": tuned.get("two_launch_ms"),
+                     "fused_ms": _keys(tuned.get("fused_ms"))},
         "clocks": clocks,
     }
     return line

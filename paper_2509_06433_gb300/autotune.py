@@ -2,12 +2,15 @@
 
 The forward and backward compositing kernels come in variants that differ in how many pixels
 each thread owns (1, 2 or 4) and in how many splats a block stages in shared memory per step
-(the chunk depth: 64, 128 or 256 for the forward, 32, 64 or 128 for the backward). Every
+(the chunk depth: 64, 128 or 256 for the forward, 32, 64 or 128 for the backward), and the
+mapping step's forward + L1 loss + backward runs either as one launch (gs_raster_fwd_l1_bwd,
+one pixels-per-thread value for both passes) or as two. Every
 variant takes the same decisions (the forward outputs are bit-identical, the gradients differ
 only in summation order), but which is fastest depends on the image size, the number of views
 and how deep the tiles' lists are. ``tune`` times each variant on the caller's own workspace
 (the projection and binning of the real scene) with CUDA events and writes the fastest choice
-into the rasterizer's config. (The tile size stays 16: the pairs are defined on 16x16 tiles.)
+into the rasterizer's config, and the one-or-two-launch choice into ``r.fused_compositing``.
+(The tile size stays 16: the pairs are defined on 16x16 tiles.)
 """
 from __future__ import annotations
 
@@ -38,8 +41,11 @@ def tune(r: "api.Rasterizer", g: "api.Gaussians", cams: torch.Tensor, reps: int 
     """Chooses (pixels per thread, chunk depth) of gs_raster_fwd and gs_raster_bwd for ``r``.
 
     Runs the projection and binning once, then times every variant with a fixed upstream
-    gradient. Returns {"fwd": {(px, chunk): ms}, "bwd": {(px, chunk): ms},
-    "choice": (fwd_px, bwd_px), "chunks": (fwd_chunk, bwd_chunk)}.
+    gradient; then the loss-fused forward followed by the backward (the chosen variants) against
+    the one-launch form for each pixels-per-thread value (with that value's best forward chunk),
+    against a zero target. Returns {"fwd": {(px, chunk): ms}, "bwd": {(px, chunk): ms},
+    "choice": (fwd_px, bwd_px), "chunks": (fwd_chunk, bwd_chunk), "two_launch_ms": ms,
+    "fused_ms": {(px, chunk): ms}, "fused": bool}.
     """
     stream = stream if stream is not None else torch.cuda.current_stream()
     out = r.new_outputs()
@@ -66,4 +72,31 @@ def tune(r: "api.Rasterizer", g: "api.Gaussians", cams: torch.Tensor, reps: int 
     c.bwd_px_per_thread, c.bwd_chunk = bbest
     if not all(fbest + bbest):
         c.fwd_px_per_thread, c.bwd_px_per_thread, c.fwd_chunk, c.bwd_chunk = saved
-    return {"fwd": fwd, "bwd": bwd, "choice": (fbest[0], bbest[0]), "chunks": (fbest[1], bbest[1])}
+    # the mapping step's compositing: two launches with the choices above, or one
+    rgb_t, depth_t = torch.zeros_like(out["rgb"]), torch.zeros_like(out["depth"])
+    lg_rgb, lg_depth = torch.empty_like(out["rgb"]), torch.empty_like(out["depth"])
+    loss = torch.empty(1, device=out["rgb"].device)
+    imgs = (out["rgb"], out["depth"], out["T"], out["last"])
+
+    def two_launches():
+        api.gs_raster_fwd_l1(c, r.ws, *imgs, rgb_t, depth_t, lg_rgb, lg_depth, loss, stream)
+        api.gs_raster_bwd(c, r.ws, *imgs, lg_rgb, lg_depth, None, stream)
+
+    two = _time(two_launches, reps, stream)
+    chosen = (c.fwd_px_per_thread, c.bwd_px_per_thread, c.fwd_chunk)
+    fused = {}
+    for px in PX:
+        ch = min((k for k in fwd if k[0] == px), key=fwd.get)[1]
+        c.fwd_px_per_thread = c.bwd_px_per_thread = px
+        c.fwd_chunk = ch
+        fused[(px, ch)] = _time(lambda: api.gs_raster_fwd_l1_bwd(c, r.ws, *imgs, rgb_t, depth_t, lg_rgb, lg_depth,
+                                                                 loss, stream), reps, stream)
+    c.fwd_px_per_thread, c.bwd_px_per_thread, c.fwd_chunk = chosen
+    fb = min(fused, key=fused.get)
+    r.fused_compositing = bool(fused[fb] < two)
+    if r.fused_compositing:
+        c.fwd_px_per_thread = c.bwd_px_per_thread = fb[0]
+        c.fwd_chunk = fb[1]
+    return {"fwd": fwd, "bwd": bwd, "choice": (c.fwd_px_per_thread, c.bwd_px_per_thread),
+            "chunks": (c.fwd_chunk, c.bwd_chunk), "two_launch_ms": two, "fused_ms": fused,
+            "fused": r.fused_compositing}

@@ -17,19 +17,22 @@ import torch
 from . import api
 
 
-def fuses_backward(cfg) -> bool:
-    """Whether the forward and backward compositing run as one launch (gs_raster_fwd_l1_bwd):
-    when both use the same pixels per thread, so the results are those of the two calls bit for bit."""
+def fuses_backward(r) -> bool:
+    """Whether the rasterizer's forward and backward compositing run as one launch
+    (gs_raster_fwd_l1_bwd): only when both use the same pixels per thread (then the results are
+    those of the two calls bit for bit), and not when the autotuner found two launches faster
+    (``r.fused_compositing``)."""
     px = lambda v: v if v in (1, 2, 4) else 2  # noqa: E731  (0 = the library default, 2)
-    return px(cfg.fwd_px_per_thread) == px(cfg.bwd_px_per_thread)
+    c = r.cfg
+    return px(c.fwd_px_per_thread) == px(c.bwd_px_per_thread) and getattr(r, "fused_compositing", True)
 
 
 def fwd_l1_bwd(r, out, rgb_t, depth_t, g_rgb, g_depth, loss, stream=None):
     """Forward with the fused L1 loss, then the backward compositing: one launch
-    (gs_raster_fwd_l1_bwd) when fuses_backward(r.cfg), else gs_raster_fwd_l1 + gs_raster_bwd."""
+    (gs_raster_fwd_l1_bwd) when fuses_backward(r), else gs_raster_fwd_l1 + gs_raster_bwd."""
     c = r.cfg
     args = (c, r.ws, out["rgb"], out["depth"], out["T"], out["last"])
-    if fuses_backward(c):
+    if fuses_backward(r):
         api.gs_raster_fwd_l1_bwd(*args, rgb_t, depth_t, g_rgb, g_depth, loss, stream)
     else:
         api.gs_raster_fwd_l1(*args, rgb_t, depth_t, g_rgb, g_depth, loss, stream)

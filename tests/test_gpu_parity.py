@@ -417,8 +417,14 @@ def test_autotuner_picks_a_variant():
     assert (r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread) == res["choice"]
     assert res["chunks"][0] in (64, 128, 256) and res["chunks"][1] in (32, 64, 128)
     assert (r.cfg.fwd_chunk, r.cfg.bwd_chunk) == res["chunks"]
+    assert r.fused_compositing == res["fused"] and set(k[0] for k in res["fused_ms"]) == {1, 2, 4}
+    assert res["two_launch_ms"] > 0 and all(v > 0 for v in res["fused_ms"].values())
+    if res["fused"]:  # one launch: one pixels-per-thread value for both passes
+        assert r.cfg.fwd_px_per_thread == r.cfg.bwd_px_per_thread
     check_images(to_np(r.render(g, ct)), oracle_fwd("fwd10k"))
     r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0
+    r.cfg.fwd_chunk, r.cfg.bwd_chunk = 0, 0
+    del r.fused_compositing
 
 
 def test_aerial_two_views_fp16_storage_forward_and_backward():

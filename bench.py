@@ -414,7 +414,8 @@ def measure_tracking(dev, iters=100, frames=3):
             "iters_per_s": frames * iters / (ms / 1e3), "ms_per_iter": ms / (frames * iters),
             "rot_err_deg": [round(before[0], 4), round(after[0], 4)],
             "trans_err_m": [round(before[1], 5), round(after[1], 5)], "status": code,
-            "px_per_thread": [tr.r.cfg.fwd_px_per_thread, tr.r.cfg.bwd_px_per_thread]}
+            "px_per_thread": [tr.r.cfg.fwd_px_per_thread, tr.r.cfg.bwd_px_per_thread],
+            "fused_compositing": _fused(tr.r)}
 
 
 def measure_window(dev, reps=10):
@@ -486,7 +487,8 @@ def measure_window(dev, reps=10):
             "pairs": pairs,
             "batched_bf16_graph_iters_per_s": 1e3 / ms_batched, "plain_fp32_sequential_iters_per_s": 1e3 / ms_plain,
             "speedup": ms_plain / ms_batched,
-            "px_per_thread": [rb.cfg.fwd_px_per_thread, rb.cfg.bwd_px_per_thread]}
+            "px_per_thread": [rb.cfg.fwd_px_per_thread, rb.cfg.bwd_px_per_thread],
+            "fused_compositing": _fused(rb)}
 
 
 def measure_aerial(dev, reps=3, track_iters=50):
@@ -548,7 +550,8 @@ def measure_aerial(dev, reps=3, track_iters=50):
             "tracking_iters_per_s": track_iters / (tms / 1e3),
             "tracking_rot_err_deg": [round(before[0], 4), round(after[0], 4)],
             "tracking_trans_err_m": [round(before[1], 5), round(after[1], 5)],
-            "px_per_thread": [r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread]}
+            "px_per_thread": [r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread],
+            "fused_compositing": _fused(r)}
 
 
 def measure_time_to_psnr(dev, iters=100, every=5):
@@ -772,6 +775,12 @@ def load_peaks():
 FLOP_EVAL = 10.0
 FLOP_FWD_BLEND = 11.0
 FLOP_BWD_BLEND = 44.0
+
+
+def _fused(r):
+    """Whether the rasterizer's mapping / tracking iteration composites in one launch."""
+    from paper_2509_06433_gb300.tracking import fuses_backward
+    return fuses_backward(r)
 
 
 def _keys(d):

@@ -244,8 +244,9 @@ GS_API gs_status_t gs_raster_fwd_l1(const gs_config_t* cfg, void* ws, size_t ws_
  * forward, no reload of those images). Writes everything both calls write: rgb, depth, T_final,
  * last, dL/drgb, dL/ddepth, d_loss and the per-pair gradient records that gs_project_bwd
  * consumes; bit for bit the results of the two calls when gs_config_t.bwd_px_per_thread equals
- * fwd_px_per_thread (the backward phase runs with the forward's pixels per thread). The mapping
- * step's form of the forward and backward compositing (Sec. II-B). */
+ * fwd_px_per_thread (the backward phase runs with the forward's pixels per thread). rgb, depth,
+ * the targets, the gradient images and d_loss must not be NULL (else GS_ERR_INVALID_ARG); T_final
+ * and last may be. The mapping step's form of the forward and backward compositing (Sec. II-B). */
 GS_API gs_status_t gs_raster_fwd_l1_bwd(const gs_config_t* cfg, void* ws, size_t ws_bytes, float* rgb, float* depth,
                                          float* T_final, int32_t* last, const float* rgb_target,
                                          const float* depth_target, float* dL_drgb, float* dL_ddepth, float* d_loss,

@@ -10,8 +10,10 @@
  * implemented here is the tile-based EWA splatting rasterizer:
  *
  *   gs_project      per (view, Gaussian): 2D mean, conic, depth, radius, tile rectangle
- *   gs_bin_sort     prefix sum of tiles touched, (tile << 32 | depth bits) keys, stable
- *                   onesweep LSD radix sort, per-tile [start, end) ranges
+ *   gs_bin_sort     prefix sum of tiles touched, one (tile, Gaussian) pair per tile an item
+ *                   touches, stored as the key (tile << 32 | Gaussian id) with its emission
+ *                   index as the value, put in the order of the (tile << 32 | depth bits)
+ *                   keys by stable onesweep LSD radix sorts; per-tile [start, end) ranges
  *   gs_raster_fwd   front-to-back alpha compositing of colour, depth, transmittance
  *   gs_loss_l1      photometric L1(RGB) + lambda L1(depth) and its image gradient
  *   gs_raster_bwd   reverse of the compositing into per-(Gaussian, tile) gradients
@@ -460,8 +462,11 @@ GS_API gs_status_t gs_ipc_event_destroy(void* event);
  * - n > GS_SORT_NOALLOC_MAX_PAIRS returns GS_ERR_SIZE_LIMIT and enqueues nothing.
  * - All calls share the one scratch array: calls whose GPU work overlaps (other streams,
  *   other host threads on the same device) race and must be serialised by the caller.
- * - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *   with that device current; make that first call before any stream capture.
+ * - Every call made outside a stream capture looks up the array's device address
+ *   (cudaGetSymbolAddress) with the current device, so a context re-created after
+ *   cudaDeviceReset is followed; a call inside a capture reuses the last address looked up on
+ *   that device. Make the first call on a device before any stream capture (a call captured
+ *   with no earlier call on its device returns GS_ERR_CUDA).
  * - d_err_word (device, may be NULL) receives GS_DEVERR_TIMEOUT if a look-back wait gave up. */
 GS_API gs_status_t gs_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int64_t n, int32_t key_bits,
                                          uint32_t* d_err_word, void* stream);

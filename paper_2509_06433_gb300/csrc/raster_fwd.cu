@@ -1,6 +1,8 @@
 // Forward compositing (gs_raster_fwd, gs_raster_fwd_stats, gs_raster_fwd_l1, and with the
 // backward pass fused, gs_raster_fwd_l1_bwd); see raster_common.cuh for the staging and the
 // opacity test both compositing kernels share.
+#include <type_traits>
+
 #include "raster_sweep.cuh"
 
 namespace gs {
@@ -42,8 +44,13 @@ struct Occlusion {
 // of gs_raster_bwd, staging CHB splats per chunk) as soon as its forward is done, from the loss
 // gradient, colour, depth and last contributor of its pixels still in registers; the results
 // equal gs_raster_fwd_l1 followed by gs_raster_bwd (dL_dT = NULL) with PX pixels per thread.
+// The workspace is read-only to the forward; the variant with the fused backward also writes
+// its gradient records, record bits and error word there, so it takes a mutable pointer.
+template <int CHB>
+using RasterWs = typename std::conditional<(CHB > 0), uint8_t*, const uint8_t*>::type;
+
 template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false, int CHB = 0>
-__global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const uint8_t* __restrict__ ws,
+__global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws,
                                                                  float* __restrict__ out_rgb,
                                                                  float* __restrict__ out_depth,
                                                                  float* __restrict__ out_T,
@@ -256,8 +263,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, const
       hT[q] = 0.0f;
       lst[q] = in ? last[q] : 0;
     }
-    // the workspace is the caller's mutable buffer; the forward only reads it
-    bwd_sweep<PX, CHB>(M, L, const_cast<uint8_t*>(ws), tc, rg, Sg, hT, gr, gg, gb, gd, lst);
+    bwd_sweep<PX, CHB>(M, L, ws, tc, rg, Sg, hT, gr, gg, gb, gd, lst);
     pdl_trigger();
   }
   if (STATS) {
@@ -294,7 +300,7 @@ cudaError_t launch_raster_fwd_l1_bwd(const Layout& L, void* ws, float* rgb, floa
     return cudaGetLastError();
   }
   const unsigned grid = static_cast<unsigned>(L.n_tiles);
-  const uint8_t* w = static_cast<const uint8_t*>(ws);
+  uint8_t* w = static_cast<uint8_t*>(ws);
   uint64_t *ev = &st->evals, *cp = &st->composited;
   const FusedLoss F{loss.rgb_t, loss.depth_t, loss.g_rgb, loss.g_depth, at<float>(ws, L.tile_loss), &st->loss_ctr,
                     loss.d_loss};

@@ -237,28 +237,38 @@ __global__ void k_sort_hist(SortArgs a) {
   }
 }
 
+// Per-device launch facts, looked up once per device (a process may drive several GPUs).
+constexpr int kMaxDevices = 64;
+
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+  return dev;
+}
+
 int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
+  static int sms[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!sms[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = n > 0 ? n : 1;
   }
-  return sms;
+  return sms[dev];
 }
 
 template <class KeyT, int IT>
 int sort_grid(int64_t max_tiles) {
-  static int blocks_per_sm = -1;
-  if (blocks_per_sm < 0) {
+  static int blocks_per_sm[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!blocks_per_sm[dev]) {
+    int b = 0;
     cudaFuncSetAttribute(k_onesweep<KeyT, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(sizeof(SortSmem<KeyT, IT>)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_onesweep<KeyT, IT>, kSortThreads,
-                                                  sizeof(SortSmem<KeyT, IT>));
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_onesweep<KeyT, IT>, kSortThreads, sizeof(SortSmem<KeyT, IT>));
+    blocks_per_sm[dev] = b > 0 ? b : 1;
   }
-  const int64_t resident = static_cast<int64_t>(blocks_per_sm) * num_sms();
+  const int64_t resident = static_cast<int64_t>(blocks_per_sm[dev]) * num_sms();
   const int64_t g = max_tiles < resident ? max_tiles : resident;
   return static_cast<int>(g > 0 ? g : 1);
 }

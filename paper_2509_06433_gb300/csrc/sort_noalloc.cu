@@ -16,9 +16,11 @@
 // internal error word).
 //
 // Host code cannot use the array's name as a device address: it is a host-side stand-in.
-// The device address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, the first time the entry point is called on it (so that first call
-// should happen before any stream capture).
+// The device address is looked up with cudaGetSymbolAddress, with the device current, on
+// every call made outside a stream capture (the lookup is cheap, and a context that was torn
+// down and re-created, e.g. after cudaDeviceReset, may place the array elsewhere), and kept
+// per device for calls made while a stream is being captured. So the first call on a device
+// must come before any stream capture that contains a call.
 #include <mutex>
 
 #include "gs_internal.cuh"
@@ -44,18 +46,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_sort_scratch on the current device (looked up on first use).
-cudaError_t scratch_address(void** out) {
+// Device address of g_sort_scratch on the current device: looked up again unless `stream` is
+// being captured, then the address of the last lookup on this device.
+cudaError_t scratch_address(cudaStream_t stream, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_sort_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = p;
+  } else if (!g_scratch_addr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;  // no lookup on this device before the capture
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -71,9 +79,9 @@ extern "C" gs_status_t gs_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int
   if (n > kMaxPairs) return GS_ERR_SIZE_LIMIT;
   if (n == 0) return GS_OK;
   if (!keys || !vals) return GS_ERR_INVALID_ARG;
-  void* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return GS_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* base = nullptr;
+  if (scratch_address(s, &base) != cudaSuccess) return GS_ERR_CUDA;
   SortArgs a{};
   a.keys[0] = keys;
   a.vals[0] = vals;

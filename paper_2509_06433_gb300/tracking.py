@@ -181,8 +181,8 @@ class HostMappingStep(MappingStep):
     backward to every parameter and the poses) and copies the gradients and the loss back to
     pinned host buffers; copies and kernels are one CUDA graph.
 
-    The Gaussians and cameras travel as one packed buffer each way and the gradients with the
-    loss as one, so a replay makes three host-to-device copies (the packed inputs first; then
+    The Gaussians (in their storage precision) and cameras travel as one packed buffer and the
+    gradients with the loss as one, so a replay makes three host-to-device copies (the packed inputs first; then
     the targets on a side stream, overlapping the projection and binning) and one
     device-to-host copy.
 
@@ -196,18 +196,22 @@ class HostMappingStep(MappingStep):
                  host_rgb_t: torch.Tensor, host_depth_t: torch.Tensor, graph=True):
         d = torch.device("cuda", torch.cuda.current_device()) if r.device.index is None else r.device
         src = {k: getattr(host_gaussians, k) for k in self._IN[:5]}
-        src["cams"] = host_cams
-        shapes = {k: tuple(v.shape) for k, v in src.items()}
-        sizes = {k: int(torch.Size(v).numel()) for k, v in shapes.items()}
-        total = sum(sizes.values())
-        self._h_pack = torch.empty(total, dtype=torch.float32, pin_memory=True)
-        self._d_pack = torch.empty(total, dtype=torch.float32, device=d)
-        self.host_in, self.dev_in, off = {}, {}, 0
+        src["cams"] = host_cams.float()
+        # one byte buffer holds every input in its own dtype (the Gaussians in their storage
+        # precision), each array starting on a 256-byte boundary
+        offs, off = {}, 0
         for k in self._IN:
-            self.host_in[k] = self._h_pack[off:off + sizes[k]].view(shapes[k])
-            self.dev_in[k] = self._d_pack[off:off + sizes[k]].view(shapes[k])
-            self.host_in[k].copy_(src[k].reshape(shapes[k]))
-            off += sizes[k]
+            offs[k] = off
+            off += (src[k].numel() * src[k].element_size() + 255) // 256 * 256
+        self._h_pack = torch.empty(off, dtype=torch.uint8, pin_memory=True)
+        self._d_pack = torch.empty(off, dtype=torch.uint8, device=d)
+        self.host_in, self.dev_in = {}, {}
+        for k in self._IN:
+            v = src[k]
+            n = v.numel() * v.element_size()
+            self.host_in[k] = self._h_pack[offs[k]:offs[k] + n].view(v.dtype).view(v.shape)
+            self.dev_in[k] = self._d_pack[offs[k]:offs[k] + n].view(v.dtype).view(v.shape)
+            self.host_in[k].copy_(v)
         for k, v in (("rgb_t", host_rgb_t), ("depth_t", host_depth_t)):
             self.host_in[k] = v.contiguous().float().pin_memory()
             self.dev_in[k] = torch.empty_like(self.host_in[k], device=d)
@@ -253,5 +257,5 @@ class HostMappingStep(MappingStep):
 
     def transfer_bytes(self):
         """(host-to-device, device-to-host) bytes per replay."""
-        h2d = 4 * (self._h_pack.numel() + self.host_in["rgb_t"].numel() + self.host_in["depth_t"].numel())
+        h2d = self._h_pack.numel() + 4 * (self.host_in["rgb_t"].numel() + self.host_in["depth_t"].numel())
         return h2d, 4 * self._h_out.numel()

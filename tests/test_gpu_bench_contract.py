@@ -22,12 +22,13 @@ def test_bench_line():
     assert d["n_gpus"] == 1 and d["steps"] == 20 and d["warmup"] == 3 and d["higher_is_better"] is True
     assert d["scaling"] == "weak" and d["vs_baseline"] is None and d["dtype"] == "f32"
     assert d["value"] > 0 and abs(d["value"] * d["ms_per_step"] / 1e3 - 1.0) < 1e-6
-    assert d["config"]["workload"].startswith("map100k") and "l2" in d["config"]
+    assert d["config"]["workload"].startswith("aerial2m") and d["config"]["K"] == 16 and "l2" in d["config"]
+    assert d["config"]["storage"] == "f16"
     e = d["e2e"]
     assert 0 < e["value"] < d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] > 10_000_000 and e["d2h_bytes_per_step"] > 5_000_000
-    # per step: project, the 11 kernels of gs_bin_sort at 640x480, the fused forward + backward
-    # compositing, the backward projection and its pose reduction
+    # per step: project, the 11 kernels of gs_bin_sort at 16 x 1280x720, the fused forward +
+    # backward compositing, the backward projection and its pose reduction
     assert d["gpu_launches"] == 20 * (1 + 11 + 1 + 2)
     assert d["roofline"]["kernel"] == "raster_fwd_l1_bwd"
     r = d["roofline"]

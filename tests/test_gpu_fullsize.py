@@ -1,49 +1,56 @@
-"""Parity at the full sizes of the benchmark's secondary workloads, in the configuration the
-benchmark launches (autotuned compositing variants, reduced-precision storage where the
-workload stores it): the sorted keys, values and tile ranges of the whole scene bit-exact
-against the oracle; images on sampled tiles (every pixel of each) within 1e-4 of the FP64
-oracle; gradients through the identity sum_g dL/dmean_g = sum_k R_k^T dL/drho_k, which holds
-at any size (a world translation is a translation of every camera)."""
+"""Parity at the full sizes of the large workloads (track300k, window500k, aerial2m), in the
+configuration the benchmark launches: autotuned compositing variants, reduced-precision storage
+where the workload stores it, and the mapping iteration the benchmark replays (projection,
+binning, forward compositing with the fused L1 loss, backward compositing, backward projection;
+one CUDA graph). Against the FP64 oracle:
+  * the sorted keys, values and tile ranges of the whole scene, bit-exact;
+  * every pixel of every view (RGB, depth, T, last contributor) within 1e-4 max-abs;
+  * the L1 loss, and every gradient tensor (means, log-scales, quaternions, opacity logits,
+    colours, the se(3) pose of every view) within 1e-3 relative L2.
+The key-frame targets are seeded random images (input data from neither side)."""
 import numpy as np
 import pytest
 
 import oracle
 from scenes import make_scene, random_image
-from tests.gpu_common import check_images, read_discrete, torch_mods
+from tests.gpu_common import GRAD_RTOL, check_images, read_discrete, rel_l2, torch_mods
 
 pytestmark = pytest.mark.gpu
 
-CASES = {
-    "track300k": ("f32", 6),
-    "window500k": ("bf16", 3),
-    "aerial2m": ("f16", 2),
-}
+CASES = {"track300k": "f32", "window500k": "bf16", "aerial2m": "f16"}
+GRADS = ("means", "log_scales", "quats", "opacity_logits", "rgb", "pose")
 
 
 def setup_case(name):
     torch, api = torch_mods()
     from paper_2509_06433_gb300 import autotune
-    storage, tiles_per_view = CASES[name]
+    from paper_2509_06433_gb300.tracking import MappingStep
+    storage = CASES[name]
     s = make_scene(name)
-    cams_np = s.track_cams if name == "track300k" else s.cams
+    cams_np = np.ascontiguousarray((s.track_cams if name == "track300k" else s.cams).reshape(-1, 16))
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[storage]
     g = api.Gaussians.from_numpy(s.params(), dtype=dt)
     # the oracle consumes the stored (dequantised) attributes
     params = tuple(t.float().cpu().numpy() for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb))
-    cams = torch.as_tensor(np.ascontiguousarray(cams_np.reshape(-1, 16))).cuda()
-    r = api.Rasterizer(s.W, s.H, cams.shape[0], s.N)
+    K, W, H = cams_np.shape[0], s.W, s.H
+    cams = torch.as_tensor(cams_np).cuda()
+    r = api.Rasterizer(W, H, K, s.N)
     r.plan(g, cams, headroom=1.2)
     autotune.tune(r, g, cams)
-    out = r.render(g, cams)
+    rgb_t = random_image(51, (K, 3, H, W), 0.0, 1.0)
+    depth_t = random_image(52, (K, H, W), 0.0, 8.0)
+    m = MappingStep(r, g, cams, torch.as_tensor(rgb_t).cuda(), torch.as_tensor(depth_t).cuda(), graph=True)
+    m.replay()
     torch.cuda.synchronize()
-    return s, params, cams_np.reshape(-1, 16), g, cams, r, out, tiles_per_view
+    gpu = {"out": {k: v.cpu().numpy() for k, v in m.out.items()},
+           "grads": {k: v.cpu().numpy() for k, v in m.grads.items()}, "loss": float(m.loss.item())}
+    return s, params, cams_np, r, gpu, rgb_t, depth_t
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_full_size_lists_images_and_gradient_identity(name):
-    torch, api = torch_mods()
-    s, params, cams_np, g, cams, r, out, tpv = setup_case(name)
-    K, W, H = cams_np.shape[0], s.W, s.H
+def test_full_size_mapping_iteration_against_oracle(name):
+    s, params, cams_np, r, gpu, rgb_t, depth_t = setup_case(name)
+    W, H = s.W, s.H
     d = read_discrete(r)
     assert d["status"] == 0
     L = oracle.discrete(params, cams_np, W, H)
@@ -51,29 +58,17 @@ def test_full_size_lists_images_and_gradient_identity(name):
     np.testing.assert_array_equal(d["keys"], L.keys)
     np.testing.assert_array_equal(d["vals"], L.vals)
     np.testing.assert_array_equal(d["ranges"], L.ranges)
-    # images on sampled tiles (every pixel), against the FP64 render of those tiles
-    Tx, Ty = r.layout.tiles_x, r.layout.tiles_y
-    rng = np.random.default_rng(5)
-    tiles = np.concatenate([k * Tx * Ty + rng.choice(Tx * Ty, tpv, replace=False) for k in range(K)])
-    o = oracle.render_tiles(params, cams_np, W, H, L.vals, L.ranges, tiles)
-    gpu = {k: v.cpu().numpy() for k, v in out.items()}
-    got = {"rgb": np.empty_like(o["rgb"]), "depth": np.empty_like(o["depth"]), "T": np.empty_like(o["T"]),
-           "last": np.empty_like(o["last"])}
-    for i, tg in enumerate(tiles):
-        k, rem = divmod(int(tg), Tx * Ty)
-        ty, tx = divmod(rem, Tx)
-        ys, xs = slice(ty * 16, ty * 16 + 16), slice(tx * 16, tx * 16 + 16)
-        got["rgb"][i] = gpu["rgb"][k][:, ys, xs]
-        got["depth"][i], got["T"][i], got["last"][i] = gpu["depth"][k][ys, xs], gpu["T"][k][ys, xs], gpu["last"][k][ys, xs]
-    assert np.all(o["near"] >= 0)  # the sampled tiles lie inside the image (sizes are multiples of 16)
-    check_images(got, o)
-    # gradients: the translation identity over every Gaussian and view
-    gr = torch.as_tensor(random_image(31, (K, 3, H, W))).cuda()
-    gd = torch.as_tensor(random_image(32, (K, H, W))).cuda()
-    grads = r.backward(g, cams, out, gr, gd)
-    sm = grads["means"].double().sum(0).cpu().numpy()
-    R = cams_np[:, 4:13].astype(np.float64).reshape(-1, 3, 3)
-    rho = grads["pose"][:, :3].double().cpu().numpy()
-    rhs = np.einsum("kji,kj->i", R, rho)
-    assert np.abs(sm - rhs).max() <= 1e-4 * np.abs(rhs).max() + 1e-6, (sm, rhs)
-    assert np.abs(rhs).max() > 0
+    # every pixel of every view
+    o = oracle.render_fwd(params, cams_np, W, H, L.vals, L.ranges)
+    rep = check_images(gpu["out"], o)
+    # the loss and every gradient tensor of the iteration
+    loss, gr, gd = oracle.loss_l1(o["rgb"], o["depth"], rgb_t, depth_t, 0.1)
+    assert abs(gpu["loss"] - loss) <= 1e-5 * abs(loss), (gpu["loss"], loss)
+    og = oracle.backward(params, cams_np, W, H, L, gr, gd)
+    gerr = {k: rel_l2(gpu["grads"][k], og[k]) for k in GRADS}
+    print(f"\nERRORS | {name} full | {CASES[name]} | rgb {rep['rgb']:.2e} | depth {rep['depth']:.2e} | "
+          f"T {rep['T']:.2e} | near px {rep['near_pixels']} | excluded {rep['excluded']} | "
+          + " | ".join(f"{k} {v:.1e}" for k, v in gerr.items()))
+    bad = {k: v for k, v in gerr.items() if not v < GRAD_RTOL}
+    assert not bad, bad
+    assert np.abs(og["pose"]).max() > 0 and np.abs(og["means"]).max() > 0

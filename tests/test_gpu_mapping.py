@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from oracle import mapping as om
-from scenes import make_scene
+from scenes import make_scene, random_image
 from tests.gpu_common import torch_mods
 
 pytestmark = pytest.mark.gpu
@@ -143,4 +143,31 @@ def test_host_mapping_step_equals_device_step():
     torch.cuda.synchronize()
     assert host.host_out["loss"].item() != dev.loss.item()
     h2d, d2h = host.transfer_bytes()
-    assert h2d == 4 * (s.N * 14 + 16 + 4 * s.W * s.H) and d2h == 4 * (s.N * 14 + 6 + 1)
+    # the packed inputs start on 256-byte boundaries: at most 255 bytes of padding per array
+    assert 0 <= h2d - 4 * (s.N * 14 + 16 + 4 * s.W * s.H) < 6 * 256 and d2h == 4 * (s.N * 14 + 6 + 1)
+
+
+def test_host_mapping_step_reduced_storage():
+    """HostMappingStep with FP16 Gaussians on the host (packed in their storage precision)
+    equals the device MappingStep on the same FP16 map bit for bit."""
+    torch, api = torch_mods()
+    from paper_2509_06433_gb300.tracking import HostMappingStep, MappingStep
+    s = make_scene("aerial2m", n=20_000, K=2, W=160, H=96, f=110.0)
+    cams = torch.as_tensor(s.cams).cuda()
+    r = api.Rasterizer(s.W, s.H, s.K, s.N)
+    g = api.Gaussians.from_numpy(s.params(), dtype=torch.float16)
+    r.plan(g, cams)
+    rgb_t = torch.as_tensor(random_image(61, (s.K, 3, s.H, s.W), 0.0, 1.0)).cuda()
+    depth_t = torch.as_tensor(random_image(62, (s.K, s.H, s.W), 0.0, 8.0)).cuda()
+    dev = MappingStep(r, g, cams, rgb_t, depth_t, graph=True)
+    dev.replay()
+    host_g = api.Gaussians(*(t.cpu() for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb)))
+    host = HostMappingStep(r, host_g, cams.cpu(), rgb_t.cpu(), depth_t.cpu(), graph=True)
+    assert host.dev_in["quats"].dtype == torch.float16 and host.dev_in["means"].dtype == torch.float32
+    host.replay()
+    torch.cuda.synchronize()
+    for k, v in dev.grads.items():
+        assert torch.equal(host.host_out[k], v.cpu()), k
+    assert host.host_out["loss"].item() == dev.loss.item()
+    h2d, _ = host.transfer_bytes()
+    assert 0 <= h2d - (s.N * (12 + 11 * 2) + 4 * s.K * (16 + 4 * s.W * s.H)) < 6 * 256

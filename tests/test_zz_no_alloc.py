@@ -22,9 +22,13 @@ def test_noalloc_sort_matches_gs_sort_pairs_on_consecutive_calls():
     from paper_2509_06433_gb300 import _lib, api
     lib = _lib.load()
     stream = torch.cuda.current_stream()
-    # two calls in a row with different sizes and key widths: the second call must not see
-    # anything left in the shared scratch by the first
-    for call_no, (n, bits) in enumerate([(300_001, 48), (77_777, 43)]):
+    # calls in a row with different sizes and key widths: a call must not see anything left in
+    # the shared scratch by the one before. Even pass counts (48, 43 bits: 6 passes) end in the
+    # caller's arrays; odd ones (40 bits: 5 passes, 24 bits: 3) end in the scratch array and are
+    # copied back; the largest accepted n fills the scratch and its look-back status completely.
+    cases = [(300_001, 48), (77_777, 43), (_lib.SORT_NOALLOC_MAX_PAIRS, 40), (123_457, 24),
+             (_lib.SORT_NOALLOC_MAX_PAIRS, 48)]
+    for call_no, (n, bits) in enumerate(cases):
         rng = np.random.default_rng(100 + call_no)
         keys = rng.integers(0, 1 << bits, n, dtype=np.uint64)
         keys[rng.integers(0, n, n // 4)] = keys[0]  # many equal keys: stability matters

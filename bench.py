@@ -195,7 +195,8 @@ def run_mapping(args, rank, world, name, steps, warmup, clocks=True, extras=True
     # kernels of ours per step: project; gs_bin_sort; raster fwd with the fused L1 loss continuing
     # into the raster bwd (one launch when fused, else two); project bwd + pose reduction
     # (gradients are stored, not accumulated: no zeroing)
-    n_launch = 1 + r.layout.bin_sort_launches + (1 if fused else 2) + 2
+    n_launch = r.layout.project_launches + r.layout.bin_sort_launches + (1 if fused else 2) + \
+        r.layout.project_bwd_launches
     stage_names = (["project", "bin_sort", "raster_fwd_l1_bwd", "project_bwd"] if fused else
                    ["project", "bin_sort", "raster_fwd_l1", "raster_bwd", "project_bwd"])
 

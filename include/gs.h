@@ -149,9 +149,9 @@ typedef struct {
                             u32[8] sort tile counters, u64 evals that blended a splat */
   size_t proj_uv;        /* float4 [K*N]: u_hi, u_lo, v_hi, v_lo (u = u_hi + u_lo) */
   size_t proj_conic;     /* float4 [K*N]: conic A, B, C (Sigma2^-1 entries 00, 01, 11), depth z */
-  size_t proj_tiles;     /* int4 [K*N]: pair offset, x0 | x1 << 16, y0 | y1 << 16, tiles emitted */
+  size_t proj_tiles;     /* int4 [K*N]: -, x0 | x1 << 16, y0 | y1 << 16, tiles emitted */
   size_t proj_depth_key; /* u32 [K*N]: binary32 bits of the camera depth (sort key low word) */
-  size_t proj_radius;    /* i32 [K*N]: pixel radius (0 when culled) */
+  size_t proj_radius;    /* i32 [K*N]: pixel radius */
   size_t color_opacity;  /* float4 [N]: r, g, b, opacity; [K*N] (view-major) with GS_COLOR_SH of
                             degree >= 1, whose colours depend on the view */
   size_t keys_sorted;    /* u64 [pair_capacity], valid prefix num_pairs, after gs_bin_sort:
@@ -166,6 +166,16 @@ typedef struct {
   int32_t bin_sort_launches; /* kernels one gs_bin_sort launches */
   size_t pair_valid;     /* u32 [ceil(pair_capacity / 32)]: bit (slot & 31) of word slot / 32 is set
                             when gs_raster_bwd wrote the record of the pair with that slot */
+  size_t live_mask;      /* u32 [ceil(K*N / 32)]: bit (i & 31) of word i / 32 is set when item
+                            i = k*N + g emits at least one pair (is live). The proj_* records above
+                            are written for live items only */
+  int32_t project_launches;     /* kernels one gs_project launches */
+  int32_t project_bwd_launches; /* kernels one gs_project_bwd launches when it stores (overwrite) parameter
+                                   gradients and the pose gradient */
+  size_t live_off;       /* u32 [K*N]: first pair index of each live item, the items taken in
+                            increasing k*N + g order (entry j: the j-th live item); valid prefix:
+                            the number of live items. The pairs of a live item occupy the slots
+                            [first, first + tiles emitted) */
 } gs_ws_layout_t;
 
 /* ---------------------------------------------------------------- sizing / status */

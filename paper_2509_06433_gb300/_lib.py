@@ -63,7 +63,8 @@ class GsWsLayout(ctypes.Structure):
                 ("color_opacity", c_size_t), ("keys_sorted", c_size_t), ("vals_sorted", c_size_t),
                 ("ranges", c_size_t), ("pair_grads", c_size_t), ("sort_passes", c_int32), ("tiles_x", c_int32),
                 ("tiles_y", c_int32), ("bin_sort_launches", c_int32),
-                ("pair_valid", c_size_t)]
+                ("pair_valid", c_size_t), ("live_mask", c_size_t), ("project_launches", c_int32),
+                ("project_bwd_launches", c_int32), ("live_off", c_size_t)]
 
 
 class GsError(RuntimeError):

@@ -34,6 +34,7 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->N = cfg->num_gaussians;
   L->K = cfg->num_views;
   L->KN = L->N * L->K;
+  if (L->KN > 0x7fffffffLL) return false;  // item indices k N + g are 31-bit
   L->W = cfg->width;
   L->H = cfg->height;
   L->Tx = (L->W + kTile - 1) / kTile;
@@ -61,6 +62,10 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   // colours depend on the view only through spherical harmonics of degree >= 1
   L->color_stride = (cfg->color_mode == GS_COLOR_SH && cfg->sh_degree > 0) ? L->N : 0;
   L->n_proj_blocks = L->KN > 0 ? (L->KN + kProjBlock - 1) / kProjBlock : 1;
+  L->proj_items = kProjThreads;
+  while (L->proj_items < kProjItemsMax && L->KN >= static_cast<int64_t>(2 * L->proj_items) * kProjTargetBlocks)
+    L->proj_items *= 2;
+  L->n_proj_groups = L->KN > 0 ? (L->KN + L->proj_items - 1) / L->proj_items : 1;
   L->item_sort_items = pick_sort_items(L->KN);
   L->pair_sort_items = pick_sort_items(L->cap);
   L->max_sort_tiles = sort_tiles(L->cap, L->pair_sort_items);
@@ -113,6 +118,18 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->n_emit_blocks = (L->cap + kEmitPairs - 1) / kEmitPairs;
   L->emit_first = take(static_cast<size_t>(L->n_emit_blocks) * 4);
   L->emit_last = take(static_cast<size_t>(L->n_emit_blocks) * 4);
+  L->live_mask = take((KN + 31) / 32 * 4);
+  L->live_wpre = take((KN + 31) / 32 * 4);
+  L->live_g = take((N + 31) / 32 * 4);
+  L->live_kg = take(KN * 4);
+  L->live_count = take(KN * 4);
+  L->live_rows = take(KN * 8);
+  L->live_off = take(KN * 4);
+  L->live_blocks = take(static_cast<size_t>(L->n_proj_groups) * 4);
+  L->live_bases = take(static_cast<size_t>(L->n_proj_groups) * 4);
+  L->view_lb = take(static_cast<size_t>(L->K) * 8);
+  L->lg_list = take(N * 4);
+  L->lg_lb = take((static_cast<size_t>(compact_blocks((L->N + 31) / 32)) + 2) * 8);
   L->total = o;
   return true;
 }
@@ -169,6 +186,10 @@ gs_status_t gs_workspace_layout(const gs_config_t* cfg, gs_ws_layout_t* out) {
   out->pair_valid = L.pair_valid;
   out->sort_passes = L.passes;
   out->bin_sort_launches = bin_sort_launch_count(L);
+  out->live_mask = L.live_mask;
+  out->live_off = L.live_off;
+  out->project_launches = 3;
+  out->project_bwd_launches = 4;
   out->tiles_x = L.Tx;
   out->tiles_y = L.Ty;
   return GS_OK;
@@ -207,6 +228,8 @@ gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, 
   if (cudaMemsetAsync(at<uint32_t>(ws, L.item_hist), 0, 4 * 256 * 4, s) != cudaSuccess) return GS_ERR_CUDA;
   if (cudaMemsetAsync(at<int32_t>(ws, L.tile_diff), 0, static_cast<size_t>(L.K) * (L.Tx + 1) * (L.Ty + 1) * 4, s) !=
       cudaSuccess)
+    return GS_ERR_CUDA;
+  if (cudaMemsetAsync(at<uint32_t>(ws, L.live_g), 0, (static_cast<size_t>(L.N) + 31) / 32 * 4, s) != cudaSuccess)
     return GS_ERR_CUDA;
   return launched(launch_project(L, g, d_cams, ws, s));
 }

@@ -24,26 +24,39 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kEmitThreads = 256;
 
-// Tiles touched by each item in depth order, and per-block totals for the scan.
+// Tiles touched by each live item in depth order, and per-chunk totals for the scan (chunks of
+// kProjBlock items; the blocks stride over the chunks of the n_live live items). Block 0 also
+// resets what the tile scan accumulates into: the pair sort's digit histograms, the per-view
+// look-back status and the view counter.
 __global__ void __launch_bounds__(kProjBlock) k_sorted_counts(Layout L, uint8_t* __restrict__ ws) {
   pdl_begin();
-  const int64_t s = static_cast<int64_t>(blockIdx.x) * kProjBlock + threadIdx.x;
-  uint32_t cnt = 0;
-  if (s < L.KN) {
-    const uint32_t kg = at<uint32_t>(ws, L.item_vals[0])[s];
-    cnt = static_cast<uint32_t>(at<int4>(ws, L.proj_tiles)[kg].w);
+  Status* st = at<Status>(ws, L.status);
+  if (blockIdx.x == 0) {
+    uint32_t* hist = at<uint32_t>(ws, L.hist);
+    for (int i = threadIdx.x; i < 4 * 256; i += kProjBlock) hist[i] = 0;
+    uint64_t* vlb = at<uint64_t>(ws, L.view_lb);
+    for (int i = threadIdx.x; i < L.K; i += kProjBlock) vlb[i] = 0;
+    if (threadIdx.x == 0) st->view_ctr = 0;
   }
-  at<uint32_t>(ws, L.sorted_counts)[s] = cnt;
+  const int64_t n_live = st->n_live;
+  const int64_t chunks = (n_live + kProjBlock - 1) / kProjBlock;
   __shared__ uint32_t warp_sums[kProjBlock / 32];
-  uint32_t v = cnt;
+  for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+    const int64_t s = c * kProjBlock + threadIdx.x;
+    uint32_t cnt = 0;
+    if (s < n_live) cnt = at<uint32_t>(ws, L.live_count)[at<uint32_t>(ws, L.item_vals[0])[s]];
+    at<uint32_t>(ws, L.sorted_counts)[s] = cnt;
+    uint32_t v = cnt;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t tot = 0;
-    for (int w = 0; w < kProjBlock / 32; ++w) tot += warp_sums[w];
-    at<uint32_t>(ws, L.block_sums)[blockIdx.x] = tot;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < kProjBlock / 32; ++w) tot += warp_sums[w];
+      at<uint32_t>(ws, L.block_sums)[c] = tot;
+    }
+    __syncthreads();
   }
 }
 
@@ -81,17 +94,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(Layout L, uint8_t*
   pdl_begin();
   const uint32_t* sums = at<uint32_t>(ws, L.block_sums);
   uint64_t* offs = at<uint64_t>(ws, L.block_offsets);
+  Status* st = at<Status>(ws, L.status);
+  const int64_t chunks = (static_cast<int64_t>(st->n_live) + kProjBlock - 1) / kProjBlock;
   __shared__ uint64_t tmp[32];
   uint64_t carry = 0;
-  for (int64_t base = 0; base < L.n_proj_blocks; base += kScanThreads) {
+  for (int64_t base = 0; base < chunks; base += kScanThreads) {
     const int64_t i = base + threadIdx.x;
-    const uint64_t x = (i < L.n_proj_blocks) ? sums[i] : 0;
+    const uint64_t x = (i < chunks) ? sums[i] : 0;
     uint64_t tot;
     const uint64_t incl = block_inclusive_scan1024(x, tmp, &tot);
-    if (i < L.n_proj_blocks) offs[i] = carry + incl - x;
+    if (i < chunks) offs[i] = carry + incl - x;
     carry += tot;
   }
-  Status* st = at<Status>(ws, L.status);
   if (threadIdx.x == 0) {
     st->total_pairs = carry;
     st->num_pairs = static_cast<uint32_t>(carry < static_cast<uint64_t>(L.cap) ? carry : L.cap);
@@ -100,70 +114,82 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(Layout L, uint8_t*
   if (threadIdx.x < 4) st->tile_ctr[4 + threadIdx.x] = 0;
 }
 
-// Per item in depth order: its first pair index (clamped to the capacity), and the compact
+// Per live item in depth order: its first pair index (clamped to the capacity), and the compact
 // record the pair-parallel emission reads. Also stores the offset with the projection record
-// (the backward pass finds a pair's gradient slot from it).
+// (the backward pass finds a pair's gradient slot from it). The blocks stride over the chunks.
 __global__ void __launch_bounds__(kProjBlock) k_item_offsets(Layout L, uint8_t* __restrict__ ws) {
   pdl_begin();
   __shared__ uint32_t s_warp[kProjBlock / 32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t s = static_cast<int64_t>(blockIdx.x) * kProjBlock + t;
-  const uint32_t cnt = at<uint32_t>(ws, L.sorted_counts)[s];
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  uint32_t wo = 0;
-#pragma unroll
-  for (int w = 0; w < kProjBlock / 32; ++w) wo += (w < warp) ? s_warp[w] : 0u;
+  const Status* st = at<Status>(ws, L.status);
+  const int64_t n_live = st->n_live;
+  const int64_t chunks = (n_live + kProjBlock - 1) / kProjBlock;
   const uint64_t cap = static_cast<uint64_t>(L.cap);
-  const uint64_t off = at<uint64_t>(ws, L.block_offsets)[blockIdx.x] + wo + incl - cnt;
-  if (s < L.KN && cnt) {
-    // the emission blocks (kEmitPairs pairs each) whose first or last pair is one of this item's
-    // pairs learn here which item that is (the block's window of items)
-    const uint64_t n = at<Status>(ws, L.status)->num_pairs;
-    const uint64_t lo = off, hi = off + cnt < n ? off + cnt : n;
-    uint32_t* first_item = at<uint32_t>(ws, L.emit_first);
-    uint32_t* last_item = at<uint32_t>(ws, L.emit_last);
-    for (uint64_t b = lo / kEmitPairs; b * kEmitPairs < hi; ++b) {
-      const uint64_t b0 = b * kEmitPairs;
-      const uint64_t b1 = (b0 + kEmitPairs < n ? b0 + kEmitPairs : n) - 1;
-      if (b0 >= lo) first_item[b] = static_cast<uint32_t>(s);
-      if (b1 < hi) last_item[b] = static_cast<uint32_t>(s);
+  const uint64_t n = st->num_pairs;
+  uint32_t* offsets = at<uint32_t>(ws, L.item_offsets);
+  if (blockIdx.x == 0 && t == 0 && n_live == 0) offsets[0] = 0;
+  for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+    const int64_t s = c * kProjBlock + t;
+    const uint32_t cnt = at<uint32_t>(ws, L.sorted_counts)[s];
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-  }
-  if (s < L.KN) {
-    uint32_t* offsets = at<uint32_t>(ws, L.item_offsets);
-    offsets[s] = static_cast<uint32_t>(off < cap ? off : cap);
-    if (s == L.KN - 1) offsets[L.KN] = static_cast<uint32_t>(off + cnt < cap ? off + cnt : cap);
-    if (cnt) {
-      const uint32_t kg = at<uint32_t>(ws, L.item_vals[0])[s];
-      int4* tiles = at<int4>(ws, L.proj_tiles);
-      tiles[kg].x = static_cast<int>(off < cap ? off : cap);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t wo = 0;
+#pragma unroll
+    for (int w = 0; w < kProjBlock / 32; ++w) wo += (w < warp) ? s_warp[w] : 0u;
+    __syncthreads();
+    const uint64_t off = at<uint64_t>(ws, L.block_offsets)[c] + wo + incl - cnt;
+    if (s < n_live && cnt) {
+      // the emission blocks (kEmitPairs pairs each) whose first or last pair is one of this item's
+      // pairs learn here which item that is (the block's window of items)
+      const uint64_t lo = off, hi = off + cnt < n ? off + cnt : n;
+      uint32_t* first_item = at<uint32_t>(ws, L.emit_first);
+      uint32_t* last_item = at<uint32_t>(ws, L.emit_last);
+      for (uint64_t b = lo / kEmitPairs; b * kEmitPairs < hi; ++b) {
+        const uint64_t b0 = b * kEmitPairs;
+        const uint64_t b1 = (b0 + kEmitPairs < n ? b0 + kEmitPairs : n) - 1;
+        if (b0 >= lo) first_item[b] = static_cast<uint32_t>(s);
+        if (b1 < hi) last_item[b] = static_cast<uint32_t>(s);
+      }
+    }
+    if (s < n_live) {
+      offsets[s] = static_cast<uint32_t>(off < cap ? off : cap);
+      if (s == n_live - 1) offsets[n_live] = static_cast<uint32_t>(off + cnt < cap ? off + cnt : cap);
+      const uint32_t pos = at<uint32_t>(ws, L.item_vals[0])[s];
+      const uint32_t kg = at<uint32_t>(ws, L.live_kg)[pos];
+      at<uint32_t>(ws, L.live_off)[pos] = static_cast<uint32_t>(off < cap ? off : cap);
       const uint32_t k = static_cast<uint32_t>(kg / static_cast<uint64_t>(L.N));
-      const uint2 rows = at<uint2>(ws, L.proj_rows)[kg];
+      const uint2 rows = at<uint2>(ws, L.live_rows)[pos];
       at<int4>(ws, L.item_rect)[s] = make_int4(static_cast<int>(rows.x), static_cast<int>(rows.y), 0, 0);
       at<uint2>(ws, L.item_kg)[s] = make_uint2(k, kg - k * static_cast<uint32_t>(L.N));
     }
   }
 }
 
-// One block: per view, the row-wise prefix sum of its (Ty+1) x (Tx+1) span grid (cell (ty, tx)
-// then holds the number of pairs of tile (ty, tx); staged in shared memory when it fits, else
-// summed in place in global memory), then the exclusive scan of the per-tile pair counts over
-// the global tile ids: ranges (clamped to the pairs actually emitted; [0, 0) for an empty tile)
-// and the digit histograms of the pair sort.
+// One block per view (views numbered in block start order): the row-wise prefix sum of the
+// view's (Ty+1) x (Tx+1) span grid (cell (ty, tx) then holds the number of pairs of tile (ty, tx);
+// staged in shared memory when it fits, else summed in place in global memory), the view's pair
+// total, the pair offset of the view (decoupled look-back over the lower-numbered views), then
+// the exclusive scan of the per-tile pair counts over the view's tiles: ranges (clamped to the
+// pairs actually emitted; [0, 0) for an empty tile) and the digit histograms of the pair sort.
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* __restrict__ ws) {
   pdl_begin();
   __shared__ uint64_t tmp[32];
   __shared__ uint32_t s_hist[4 * 256];
   __shared__ int32_t sg[kProjGridCells];
+  __shared__ uint32_t s_view;
+  __shared__ uint64_t s_base;
+  Status* st = at<Status>(ws, L.status);
+  if (threadIdx.x == 0) s_view = atomicAdd(&st->view_ctr, 1u);
   for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
-  const Status* st = at<Status>(ws, L.status);
+  __syncthreads();
+  const int k = static_cast<int>(s_view);
+  if (k >= L.K) return;
   // after a capacity overflow the pair sort does not run: leave every tile empty
   const uint64_t n = st->total_pairs > static_cast<uint64_t>(L.cap) ? 0 : st->num_pairs;
   uint32_t* ranges = at<uint32_t>(ws, L.ranges);
@@ -171,46 +197,53 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* _
   const int cells = stride * (L.Ty + 1);
   const bool in_smem = cells <= kProjGridCells;
   const int64_t per_view = static_cast<int64_t>(L.Tx) * L.Ty;
-  uint64_t carry = 0;
-  for (int k = 0; k < L.K; ++k) {
-    int32_t* gg = at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * cells;
-    int32_t* g = in_smem ? sg : gg;
-    __syncthreads();
-    if (in_smem)
-      for (int i = threadIdx.x; i < cells; i += kScanThreads) sg[i] = gg[i];
-    __syncthreads();
-    for (int y = threadIdx.x; y < L.Ty; y += kScanThreads) {
-      int32_t acc = 0;
-      for (int x = 0; x <= L.Tx; ++x) {
-        acc += g[y * stride + x];
-        g[y * stride + x] = acc;
-      }
+  int32_t* gg = at<int32_t>(ws, L.tile_diff) + static_cast<int64_t>(k) * cells;
+  int32_t* g = in_smem ? sg : gg;
+  if (in_smem)
+    for (int i = threadIdx.x; i < cells; i += kScanThreads) sg[i] = gg[i];
+  __syncthreads();
+  // row-wise prefix sums, and the view's total (each thread sums the rows it owns)
+  uint64_t mine = 0;
+  for (int y = threadIdx.x; y < L.Ty; y += kScanThreads) {
+    int32_t acc = 0;
+    for (int x = 0; x <= L.Tx; ++x) {
+      acc += g[y * stride + x];
+      g[y * stride + x] = acc;
+      if (x < L.Tx) mine += static_cast<uint32_t>(acc);
     }
-    __syncthreads();
-    for (int64_t base = 0; base < per_view; base += kScanThreads) {
-      const int64_t r = base + threadIdx.x;
-      uint32_t c = 0;
-      if (r < per_view) {
-        const int64_t ty = r / L.Tx, tx = r - ty * L.Tx;
-        c = static_cast<uint32_t>(g[ty * stride + tx]);
-      }
-      uint64_t tot;
-      const uint64_t incl = block_inclusive_scan1024(c, tmp, &tot);
-      if (r < per_view) {
-        const int64_t tg = k * per_view + r;
-        const uint64_t start = c ? carry + incl - c : 0, end = c ? carry + incl : 0;
-        ranges[2 * tg] = static_cast<uint32_t>(start < n ? start : n);
-        ranges[2 * tg + 1] = static_cast<uint32_t>(end < n ? end : n);
-        if (c)
-          for (int p = 0; p < L.passes; ++p)
-            atomicAdd(&s_hist[p * 256 + ((static_cast<uint32_t>(tg) >> (8 * p)) & 0xffu)], c);
-      }
-      carry += tot;
+  }
+  uint64_t total;
+  block_inclusive_scan1024(mine, tmp, &total);
+  if (threadIdx.x < 32) {
+    const uint64_t base = lb_exclusive_warp(at<uint64_t>(ws, L.view_lb), static_cast<uint32_t>(k), total, &st->err);
+    if (threadIdx.x == 0) s_base = base;
+  }
+  __syncthreads();
+  uint64_t carry = s_base;
+  for (int64_t base = 0; base < per_view; base += kScanThreads) {
+    const int64_t r = base + threadIdx.x;
+    uint32_t c = 0;
+    if (r < per_view) {
+      const int64_t ty = r / L.Tx, tx = r - ty * L.Tx;
+      c = static_cast<uint32_t>(g[ty * stride + tx]);
     }
+    uint64_t tot;
+    const uint64_t incl = block_inclusive_scan1024(c, tmp, &tot);
+    if (r < per_view) {
+      const int64_t tg = k * per_view + r;
+      const uint64_t start = c ? carry + incl - c : 0, end = c ? carry + incl : 0;
+      ranges[2 * tg] = static_cast<uint32_t>(start < n ? start : n);
+      ranges[2 * tg + 1] = static_cast<uint32_t>(end < n ? end : n);
+      if (c)
+        for (int p = 0; p < L.passes; ++p)
+          atomicAdd(&s_hist[p * 256 + ((static_cast<uint32_t>(tg) >> (8 * p)) & 0xffu)], c);
+    }
+    carry += tot;
   }
   __syncthreads();
   uint32_t* hist = at<uint32_t>(ws, L.hist);
-  for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) hist[i] = s_hist[i];
+  for (int i = threadIdx.x; i < L.passes * 256; i += kScanThreads)
+    if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
 }
 
 // Pairs [b * kEmitPairs, (b + 1) * kEmitPairs) of the emission order. The block stages its
@@ -351,10 +384,13 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
 
 cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s) {
   auto* w = static_cast<uint8_t*>(ws);
-  launch(k_sorted_counts, static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s, L, w);
+  // the live items are counted on the device: the per-item kernels stride over their chunks
+  const int64_t resident = static_cast<int64_t>(device_sms()) * (2048 / kProjBlock);
+  const unsigned item_grid = static_cast<unsigned>(L.n_proj_blocks < resident ? L.n_proj_blocks : resident);
+  launch(k_sorted_counts, item_grid, kProjBlock, 0, s, L, w);
   launch(k_scan_blocks, 1, kScanThreads, 0, s, L, w);
-  launch(k_item_offsets, static_cast<unsigned>(L.n_proj_blocks), kProjBlock, 0, s, L, w);
-  launch(k_tile_scan, 1, kScanThreads, 0, s, L, w);
+  launch(k_item_offsets, item_grid, kProjBlock, 0, s, L, w);
+  launch(k_tile_scan, static_cast<unsigned>(L.K), kScanThreads, 0, s, L, w);
   launch(k_emit_pairs, static_cast<unsigned>(L.n_emit_blocks), kEmitThreads, 0, s, L, w);
   return cudaGetLastError();
 }

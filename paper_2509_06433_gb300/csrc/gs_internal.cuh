@@ -12,7 +12,11 @@ namespace gs {
 
 constexpr int kTile = 16;             // tile side (pixels)
 constexpr int kTilePixels = kTile * kTile;
-constexpr int kProjBlock = 256;       // (view, Gaussian) items per projection / scan block
+constexpr int kProjBlock = 256;       // (view, Gaussian) items per scan chunk of the binning
+constexpr int kProjItemsMax = 2048;   // (view, Gaussian) items per projection block: 256 to
+                                      // this, a power of two, so that there are >= kProjTargetBlocks
+constexpr int kProjTargetBlocks = 1216;
+constexpr int kProjThreads = 256;     // threads of a projection block
 constexpr int kEmitPairs = 1024;      // pairs emitted per emission block
 constexpr int kProjGridCells = 6144;  // largest (Tx+1)(Ty+1) difference grid kept in shared memory
 constexpr int kSortThreads = 256;     // onesweep block
@@ -35,6 +39,8 @@ struct Status {
   uint64_t composited;      // evaluations of the last forward raster that blended a splat
   uint32_t row_ctr;         // entries of the row-span table handed out by the projection
   uint32_t loss_ctr;        // blocks of the loss-fused forward done (reset by the last one)
+  uint32_t n_live;          // live items: (view, Gaussian) items that emit at least one pair
+  uint32_t view_ctr;        // tile-scan blocks started (one per view)
 };
 static_assert(sizeof(Status) <= 256, "status block");
 
@@ -53,6 +59,8 @@ struct Layout {
   int color_mode, sh_degree, sh_coeffs;  // gs_color_mode_t; SH degree and (degree + 1)^2
   int64_t color_stride;     // index of (view k, Gaussian g) in color_opacity = k * color_stride + g
   int64_t n_proj_blocks;    // ceil(KN / kProjBlock)
+  int64_t n_proj_groups;    // ceil(KN / proj_items): projection blocks
+  int proj_items;           // items per projection block
   int64_t max_sort_tiles;   // onesweep tiles of the pair sort at capacity
   int64_t n_pose_blocks;    // ceil(N / kPoseBlock)
   int64_t n_loss_blocks;
@@ -65,8 +73,8 @@ struct Layout {
   // in depth order: exclusive pair offset of each item (KN + 1 entries), its row-span
   // table entries (int4: first entry, number of entries, -, -), its (view, Gaussian id)
   size_t item_offsets, item_rect, item_kg;
-  // row-span table: per item, its rows from the first to the last non-empty one, each an
-  // int2 (pairs of the item in earlier rows, first column | row << 16); proj_rows: per item
+  // row-span table: per live item, its rows from the first to the last non-empty one, each an
+  // int2 (pairs of the item in earlier rows, first column | row << 16); proj_rows: per live item
   // (first entry, number of entries). Entries are handed out by an atomic counter; at most
   // pair_capacity of them (more is reported as a pair overflow).
   size_t row_table, proj_rows;
@@ -80,8 +88,198 @@ struct Layout {
   size_t tile_diff;
   int64_t n_emit_blocks;    // ceil(cap / kEmitPairs)
   size_t emit_first, emit_last;  // u32 [n_emit_blocks]: items holding each emission block's first / last pair
+  // Live items (those that emit at least one pair) and their compaction. Only live items get
+  // projection records (proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, proj_ell,
+  // proj_rows); the others are marked dead and nothing reads their records. A live item's position among
+  // the live items (in increasing k N + g order) is its rank in live_mask: live_wpre[i / 32] +
+  // the set bits of word i / 32 below bit i & 31 (live_rank).
+  //   live_mask  u32 [ceil(KN / 32)]: bit (i & 31) of word i / 32 set when item i = k N + g is live
+  //   live_wpre  u32 [ceil(KN / 32)]: live items before word i / 32
+  //   live_g     u32 [ceil(N / 32)]: bit set when Gaussian g is live in at least one view
+  //   live_kg    u32 [KN]: the live items in increasing k N + g order (valid prefix n_live)
+  //   live_count u32 [KN]: tiles emitted by each of them
+  //   live_rows  uint2 [KN]: their row-span table entries (first entry, number of entries)
+  //   live_off   u32 [KN]: their first pair index (emission order), clamped to the capacity
+  //   live_blocks, live_bases  u32 [n_proj_groups]: live items of each projection block, and
+  //              the block's first position among all live items (k_live_offsets)
+  //   view_lb    u64 [K]: look-back status of the per-view pair totals (tile scan)
+  //   lg_list    u32 [N] + lg_lb u64 [compact_blocks(ceil(N / 32)) + 2]: live Gaussians in
+  //              increasing order (gs_project_bwd); block counter, list length (low word),
+  //              look-back status of their compaction
+  size_t live_mask, live_wpre, live_g, live_kg, live_count, live_rows, live_off, live_blocks, live_bases, view_lb,
+      lg_list, lg_lb;
   size_t total;
 };
+
+// Decoupled look-back over a sequence of blocks numbered in their start order (Merrill &
+// Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016), on 64-bit
+// status words: the top two bits flag an aggregate (1) or an inclusive prefix (2), the low 62
+// bits hold the value; 0 = not published yet. Called by all 32 lanes of one warp of block
+// `id`, which first publishes the block's aggregate; the lanes then read kLbWindows * 32
+// predecessors per round (independent loads), consume the aggregates in front of the nearest
+// inclusive prefix (or in front of the nearest unpublished block, which is read again next
+// round), and return to every lane the sum of the
+// aggregates of blocks [0, id), after publishing the block's inclusive prefix. The wait for an
+// unpublished predecessor is bounded: after kSpinLimit polls without progress it sets
+// GS_DEVERR_TIMEOUT in *err and returns what it has.
+constexpr uint64_t kLbAggregate = 1ull << 62;
+constexpr uint64_t kLbPrefix = 2ull << 62;
+constexpr uint64_t kLbValue = (1ull << 62) - 1;
+__device__ __forceinline__ uint64_t lb_load(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void lb_store(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+constexpr int kLbWindows = 8;  // 32-block windows read per round (loads in flight together)
+__device__ __forceinline__ uint64_t lb_exclusive_warp(uint64_t* status, uint32_t id, uint64_t aggregate,
+                                                      uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  if (id == 0) {
+    if (lane == 0) lb_store(&status[0], kLbPrefix | aggregate);
+    return 0;
+  }
+  if (lane == 0) lb_store(&status[id], kLbAggregate | aggregate);
+  uint64_t excl = 0;
+  uint32_t spins = 0;
+  int64_t j = static_cast<int64_t>(id) - 1;  // window q, lane l: block j - 32 q - l
+  bool done = false;
+  while (!done) {
+    uint64_t v[kLbWindows];
+#pragma unroll
+    for (int q = 0; q < kLbWindows; ++q) {
+      const int64_t jj = j - 32 * q - lane;
+      v[q] = jj >= 0 ? lb_load(&status[jj]) : kLbPrefix;  // before block 0: a zero prefix
+    }
+    int64_t consumed = 0;
+#pragma unroll
+    for (int q = 0; q < kLbWindows; ++q) {
+      if (done) break;
+      const uint64_t f = v[q] & ~kLbValue;
+      const uint32_t pref = __ballot_sync(0xffffffffu, f == kLbPrefix);
+      const uint32_t blocked = __ballot_sync(0xffffffffu, f == 0);
+      const int p = pref ? __ffs(pref) - 1 : 32, b = blocked ? __ffs(blocked) - 1 : 32;
+      if (p < b) {  // every block in front of the nearest prefix has published: done
+        excl += warp_sum_u64(lane <= p ? (v[q] & kLbValue) : 0);
+        done = true;
+        break;
+      }
+      excl += warp_sum_u64(lane < b ? (v[q] & kLbValue) : 0);  // the aggregates in front of the gap
+      consumed += b;
+      if (b < 32) break;  // an unpublished block: read again from it
+    }
+    if (done) break;
+    j -= consumed;
+    if (consumed == 0 && ++spins > kSpinLimit) {
+      if (lane == 0) atomicOr(err, GS_DEVERR_TIMEOUT);
+      break;
+    }
+  }
+  if (lane == 0) lb_store(&status[id], kLbPrefix | (excl + aggregate));
+  return excl;
+}
+
+// Mask compaction (k_live_scan, k_live_gaussians): blocks of kCompactWarps warps, each warp
+// kCompactWords words of the mask (32 elements per word).
+constexpr int kCompactWarps = 16;
+constexpr int kCompactWords = 64;
+constexpr int64_t kCompactBlockWords = static_cast<int64_t>(kCompactWarps) * kCompactWords;
+__host__ __device__ inline int64_t compact_blocks(int64_t words) {
+  return words > 0 ? (words + kCompactBlockWords - 1) / kCompactBlockWords : 1;
+}
+
+// Compaction of a bit mask (bit i & 31 of word i / 32 set: element i is selected) into the
+// increasing list of the selected elements, by one block of kCompactWarps warps (all threads
+// call it). lb: [0] block counter, [1] -, [2..] look-back status (zeroed before the launch);
+// blocks are numbered in start order and block b takes words [b, b + 1) * kCompactBlockWords.
+// Writes wpre[w] (if not null) = the selected elements before word w, adds the block's count
+// to *n_out, and calls emit(i, pos) for every selected element i with its list position pos.
+// Lane l of a warp reads words 32 q + l (q < kCompactWords / 32); the elements of each
+// non-zero word are then emitted by the lanes of their bits, so the accesses of one word's
+// elements are consecutive.
+template <class Emit>
+__device__ __forceinline__ void compact_mask(const uint32_t* __restrict__ mask, int64_t n_words, uint32_t* wpre,
+                                             uint64_t* lb, uint32_t* n_out, uint32_t* err, Emit emit) {
+  constexpr int Q = kCompactWords / 32;
+  __shared__ uint32_t s_blk, s_wtot[kCompactWarps];
+  __shared__ uint64_t s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_blk = static_cast<uint32_t>(atomicAdd(reinterpret_cast<unsigned long long*>(&lb[0]), 1ull));
+  __syncthreads();
+  const uint32_t blk = s_blk;
+  const int64_t wb = static_cast<int64_t>(blk) * kCompactBlockWords + static_cast<int64_t>(warp) * kCompactWords;
+  uint32_t word[Q], excl[Q];
+  uint32_t running = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int64_t w = wb + 32 * q + lane;
+    word[q] = w < n_words ? mask[w] : 0u;
+    const uint32_t c = __popc(word[q]);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    excl[q] = running + incl - c;
+    running += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) s_wtot[warp] = running;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < kCompactWarps; ++w) tot += s_wtot[w];
+    const uint64_t base = lb_exclusive_warp(lb + 2, blk, tot, err);
+    if (lane == 0) {
+      s_base = base;
+      if (tot) atomicAdd(n_out, tot);
+    }
+  }
+  __syncthreads();
+  uint64_t wbase = s_base;
+  for (int w = 0; w < warp; ++w) wbase += s_wtot[w];
+  uint32_t lm;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lm));
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int64_t w = wb + 32 * q + lane;
+    if (wpre && w < n_words) wpre[w] = static_cast<uint32_t>(wbase + excl[q]);
+    uint32_t todo = __ballot_sync(0xffffffffu, word[q] != 0u);
+    // four non-zero words per round: their elements' emits are independent, so their loads
+    // are in flight together
+    while (todo) {
+      int src[4];
+      uint32_t m[4], e[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        src[r] = todo ? __ffs(todo) - 1 : -1;
+        todo &= todo ? todo - 1 : 0u;
+        m[r] = __shfl_sync(0xffffffffu, word[q], src[r] < 0 ? 0 : src[r]);
+        e[r] = __shfl_sync(0xffffffffu, excl[q], src[r] < 0 ? 0 : src[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (src[r] >= 0 && ((m[r] >> lane) & 1u))
+          emit((wb + 32 * q + src[r]) * 32 + lane, wbase + e[r] + __popc(m[r] & lm));
+    }
+  }
+}
+
+// Whether item kg is live (emits pairs); its projection records exist only then.
+__device__ __forceinline__ bool item_live(const uint32_t* live_mask, int64_t kg) {
+  return (live_mask[kg >> 5] >> (kg & 31)) & 1u;
+}
+// Position of live item kg among the live items.
+__device__ __forceinline__ uint32_t live_rank(const uint32_t* live_mask, const uint32_t* live_wpre, int64_t kg) {
+  return live_wpre[kg >> 5] + __popc(live_mask[kg >> 5] & ((1u << (kg & 31)) - 1u));
+}
 
 bool make_layout(const gs_config_t* cfg, Layout* L);
 
@@ -263,5 +461,6 @@ cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s);
 cudaError_t launch_onesweep(const SortArgs32& a, cudaStream_t s);
 cudaError_t launch_sort_prepare(const SortArgs& a, cudaStream_t s);  // zero status, build histogram
 int bin_sort_launch_count(const Layout& L);  // kernels one gs_bin_sort launches
+int device_sms();  // multiprocessors of the current device (cached per device)
 
 }  // namespace gs

@@ -112,13 +112,49 @@ __device__ __forceinline__ Sum10 sum_pairs_warp(const float* __restrict__ pg, co
   return mine;
 }
 
+// The Gaussians live in at least one view (live_g mask of the projection), compacted in
+// increasing order into lg_list (its length to the low word of lg_lb[1]).
+__global__ void __launch_bounds__(kCompactWarps * 32) k_live_gaussians(Layout L, uint8_t* __restrict__ ws) {
+  pdl_begin();
+  uint64_t* lb = at<uint64_t>(ws, L.lg_lb);
+  uint32_t* list = at<uint32_t>(ws, L.lg_list);
+  const uint32_t* live_g = at<uint32_t>(ws, L.live_g);
+  compact_mask(live_g, (L.N + 31) / 32, static_cast<uint32_t*>(nullptr), lb, reinterpret_cast<uint32_t*>(&lb[1]),
+               &at<Status>(ws, L.status)->err, [&](int64_t g, uint64_t pos) { list[pos] = static_cast<uint32_t>(g); });
+}
+
+// With out.overwrite: the gradients of the Gaussians no view sees are stored as zero.
+__global__ void __launch_bounds__(256) k_zero_unseen(Layout L, const uint8_t* __restrict__ ws, gs_grads_t out) {
+  pdl_begin();
+  const uint32_t* live_g = at<uint32_t>(ws, L.live_g);
+  const int cw = L.color_mode == GS_COLOR_SH ? 3 * L.sh_coeffs : 3;
+  for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < L.N;
+       g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if ((live_g[g >> 5] >> (g & 31)) & 1u) continue;
+    if (out.means) out.means[3 * g] = out.means[3 * g + 1] = out.means[3 * g + 2] = 0.0f;
+    if (out.log_scales) out.log_scales[3 * g] = out.log_scales[3 * g + 1] = out.log_scales[3 * g + 2] = 0.0f;
+    if (out.quats)
+      for (int j = 0; j < 4; ++j) out.quats[4 * g + j] = 0.0f;
+    if (out.opacity_logits) out.opacity_logits[g] = 0.0f;
+    if (out.rgb)
+      for (int j = 0; j < cw; ++j) out.rgb[cw * g + j] = 0.0f;
+  }
+}
+
+// One thread per live Gaussian (lg_list); blocks past the list's end return at once.
 __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                            const uint8_t* __restrict__ ws, gs_grads_t out,
                                                            float* __restrict__ pose_partials) {
   pdl_wait();
-  const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
-  const bool valid = g < L.N;
-  const int4* tiles = at<int4>(ws, L.proj_tiles);
+  const int64_t n_list = static_cast<int64_t>(*reinterpret_cast<const uint32_t*>(&at<uint64_t>(ws, L.lg_lb)[1]));
+  const int64_t li = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
+  if (static_cast<int64_t>(blockIdx.x) * kPoseBlock >= n_list) return;  // (whole block: uniform)
+  const bool valid = li < n_list;
+  const int64_t g = valid ? static_cast<int64_t>(at<uint32_t>(ws, L.lg_list)[li]) : 0;
+  const uint32_t* live_mask = at<uint32_t>(ws, L.live_mask);
+  const uint32_t* live_wpre = at<uint32_t>(ws, L.live_wpre);
+  const uint32_t* live_off = at<uint32_t>(ws, L.live_off);
+  const uint32_t* live_count = at<uint32_t>(ws, L.live_count);
   const float* pg = at<float>(ws, L.pair_grads);
   const uint32_t* pvalid = at<uint32_t>(ws, L.pair_valid);
   __shared__ float s_red[kPoseBlock / 32][6];
@@ -150,8 +186,13 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
 
   for (int k = 0; k < L.K; ++k) {
     float pose[6] = {0, 0, 0, 0, 0, 0};
-    int4 tl = make_int4(0, 0, 0, 0);
-    if (valid) tl = tiles[static_cast<int64_t>(k) * L.N + g];
+    int4 tl = make_int4(0, 0, 0, 0);  // (pair offset, -, -, tiles emitted)
+    const int64_t kg = static_cast<int64_t>(k) * L.N + g;
+    if (valid && item_live(live_mask, kg)) {
+      const uint32_t pos = live_rank(live_mask, live_wpre, kg);
+      tl.x = static_cast<int>(live_off[pos]);
+      tl.w = static_cast<int>(live_count[pos]);
+    }
     const Sum10 s =
         sum_pairs_warp(pg, pvalid, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
     if (tl.w > 0) {
@@ -357,9 +398,10 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
 }
 
 // pose[k][i] += (or, with overwrite, =) the sum over blocks of pose_partials[block][k][i].
-__global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_blocks, int K, float* __restrict__ pose,
-                              int overwrite) {
+__global__ void k_pose_reduce(const float* __restrict__ partials, const uint32_t* __restrict__ n_list, int K,
+                              float* __restrict__ pose, int overwrite) {
   pdl_begin();
+  const int64_t n_blocks = (static_cast<int64_t>(*n_list) + kPoseBlock - 1) / kPoseBlock;
   const int k = blockIdx.x;
   const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float v = 0.0f;
@@ -375,14 +417,21 @@ __global__ void __launch_bounds__(kPoseBlock) k_screen_grads(Layout L, const uin
   pdl_begin();
   const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
   const bool valid = g < L.N;  // no early return: the pair sums are warp-cooperative
-  const int4* tiles = at<int4>(ws, L.proj_tiles);
+  const uint32_t* live_wpre = at<uint32_t>(ws, L.live_wpre);
+  const uint32_t* live_off = at<uint32_t>(ws, L.live_off);
+  const uint32_t* live_count = at<uint32_t>(ws, L.live_count);
+  const uint32_t* live_mask = at<uint32_t>(ws, L.live_mask);
   const float* pg = at<float>(ws, L.pair_grads);
   const uint32_t* pvalid = at<uint32_t>(ws, L.pair_valid);
   float op = 0.0f, c[3] = {0, 0, 0};
   for (int k = 0; k < L.K; ++k) {
     const int64_t kg = static_cast<int64_t>(k) * L.N + g;
-    int4 tl = make_int4(0, 0, 0, 0);
-    if (valid) tl = tiles[kg];
+    int4 tl = make_int4(0, 0, 0, 0);  // (pair offset, -, -, tiles emitted)
+    if (valid && item_live(live_mask, kg)) {
+      const uint32_t pos = live_rank(live_mask, live_wpre, kg);
+      tl.x = static_cast<int>(live_off[pos]);
+      tl.w = static_cast<int>(live_count[pos]);
+    }
     const Sum10 s =
         sum_pairs_warp(pg, pvalid, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
     if (!valid) continue;
@@ -416,9 +465,20 @@ cudaError_t launch_project_bwd(const Layout& L, const GaussPtrs& g, const gs_cam
     return cudaGetLastError();
   }
   float* partials = at<float>(ws, L.pose_partials);
+  uint64_t* lb = at<uint64_t>(ws, L.lg_lb);
+  const int64_t cblocks = compact_blocks((L.N + 31) / 32);
+  cudaMemsetAsync(lb, 0, (static_cast<size_t>(cblocks) + 2) * 8, s);
+  launch(k_live_gaussians, static_cast<unsigned>(cblocks), kCompactWarps * 32, 0, s, L, static_cast<uint8_t*>(ws));
+  if (out.overwrite && (out.means || out.log_scales || out.quats || out.opacity_logits || out.rgb)) {
+    const int64_t zb = (L.N + 255) / 256, cap = static_cast<int64_t>(device_sms()) * 8;
+    launch(k_zero_unseen, static_cast<unsigned>(zb < cap ? zb : cap), 256, 0, s, L, static_cast<const uint8_t*>(ws),
+           out);
+  }
   launch(k_project_bwd, static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s, L, g, cams, static_cast<uint8_t*>(ws),
-                                                                              out, partials);
-  if (out.pose) launch(k_pose_reduce, L.K, 6 * 32, 0, s, partials, L.n_pose_blocks, L.K, out.pose, out.overwrite);
+         out, partials);
+  if (out.pose)
+    launch(k_pose_reduce, L.K, 6 * 32, 0, s, partials, reinterpret_cast<const uint32_t*>(lb + 1), L.K, out.pose,
+           out.overwrite);
   return cudaGetLastError();
 }
 

@@ -246,16 +246,7 @@ int current_device() {
   return dev;
 }
 
-int num_sms() {
-  static int sms[kMaxDevices] = {};
-  const int dev = current_device();
-  if (!sms[dev]) {
-    int n = 0;
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    sms[dev] = n > 0 ? n : 1;
-  }
-  return sms[dev];
-}
+int num_sms() { return device_sms(); }
 
 template <class KeyT, int IT>
 int sort_grid(int64_t max_tiles) {
@@ -292,6 +283,17 @@ cudaError_t onesweep_passes(const SortArgsT<KeyT>& a, cudaStream_t s) {
 
 }  // namespace
 
+int device_sms() {
+  static int sms[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!sms[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = n > 0 ? n : 1;
+  }
+  return sms[dev];
+}
+
 cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t s) { return onesweep_passes(a, s); }
 
 int bin_sort_launch_count(const Layout& L) {
@@ -322,7 +324,7 @@ cudaError_t launch_item_sort(const Layout& L, void* ws, cudaStream_t s) {
   a.vals[0] = at<uint32_t>(ws, L.item_vals[0]);
   a.vals[1] = at<uint32_t>(ws, L.item_vals[1]);
   Status* st = at<Status>(ws, L.status);
-  a.n_dev = nullptr;
+  a.n_dev = &st->n_live;  // the live items, compacted by the projection
   a.n_host = L.KN;
   a.hist = at<uint32_t>(ws, L.item_hist);
   a.tile_status = at<uint32_t>(ws, L.item_status);

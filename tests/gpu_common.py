@@ -42,7 +42,14 @@ def read_discrete(r):
     code, err, total, evals = r.status()
     KN = r.K * r.N
     lay = r.layout
+    # items that emit pairs (live); the projection records exist for those only
+    mask = r.ws_view("live_mask", torch.int32, (KN + 31) // 32).cpu().numpy().view(np.uint32)
+    live = ((mask[np.arange(KN) >> 5] >> (np.arange(KN) & 31).astype(np.uint32)) & 1).astype(bool)
     tiles = r.ws_view("proj_tiles", torch.int32, KN * 4).reshape(KN, 4).cpu().numpy()
+    tiles[~live] = 0
+    # a live item's first pair index, stored at its rank among the live items
+    n_live = int(live.sum())
+    tiles[live, 0] = r.ws_view("live_off", torch.int32, max(n_live, 1)).cpu().numpy()[:n_live]
     rx = tiles[:, 1].view(np.uint32)
     ry = tiles[:, 2].view(np.uint32)
     rect = np.stack([rx & 0xFFFF, rx >> 16, ry & 0xFFFF, ry >> 16], axis=1).astype(np.int32)
@@ -58,9 +65,10 @@ def read_discrete(r):
     keys = (tile << np.uint64(32)) | depth_bits[item].astype(np.uint64) if P else raw_keys
     d = {
         "status": code, "err": err, "total_pairs": total, "evals": evals,
+        "live": live,
         "offset": tiles[:, 0].copy(), "count": tiles[:, 3].view(np.uint32).copy(), "rect": rect,
         "depth_bits": depth_bits,
-        "radius": r.ws_view("proj_radius", torch.int32, KN).cpu().numpy(),
+        "radius": np.where(live, r.ws_view("proj_radius", torch.int32, KN).cpu().numpy(), 0),
         "uv": r.ws_view("proj_uv", torch.float32, KN * 4).reshape(KN, 4).cpu().numpy(),
         "conic": r.ws_view("proj_conic", torch.float32, KN * 4).reshape(KN, 4).cpu().numpy(),
         "keys": keys, "vals": gid.astype(np.uint32), "slots": raw_vals, "item": item,

@@ -114,6 +114,10 @@ typedef struct {
                                  Gradients do not depend on it. */
   int32_t color_mode;         /* gs_color_mode_t; 0 = GS_COLOR_RGB */
   int32_t sh_degree;          /* 0..3 with GS_COLOR_SH (ignored with GS_COLOR_RGB) */
+  int32_t raster_blocks_per_sm; /* cap on the resident blocks per multiprocessor of the compositing
+                                   kernels (gs_raster_fwd*, gs_raster_bwd): 1..32; 0 = as many as
+                                   fit. Enforced by padding each block's dynamic shared memory;
+                                   outputs do not depend on it. */
 } gs_config_t;
 
 /* Gaussian attributes. means may be F32 or BF16/F16 (means_dtype); the other four

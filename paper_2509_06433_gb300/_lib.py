@@ -38,7 +38,8 @@ class GsConfig(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("tile", c_int32), ("num_views", c_int32),
                 ("num_gaussians", c_int64), ("pair_capacity", c_int64), ("near_plane", c_float),
                 ("lambda_depth", c_float), ("fwd_px_per_thread", c_int32), ("bwd_px_per_thread", c_int32),
-                ("fwd_chunk", c_int32), ("bwd_chunk", c_int32), ("color_mode", c_int32), ("sh_degree", c_int32)]
+                ("fwd_chunk", c_int32), ("bwd_chunk", c_int32), ("color_mode", c_int32), ("sh_degree", c_int32),
+                ("raster_blocks_per_sm", c_int32)]
 
 
 class GsGaussians(ctypes.Structure):

@@ -36,13 +36,13 @@ COLOR_RGB, COLOR_SH = 0, 1
 
 
 def make_config(width, height, num_views, num_gaussians, pair_capacity, near_plane=0.2, lambda_depth=0.1,
-                fwd_px=0, bwd_px=0, fwd_chunk=0, bwd_chunk=0, sh_degree=None):
+                fwd_px=0, bwd_px=0, fwd_chunk=0, bwd_chunk=0, sh_degree=None, blocks_per_sm=0):
     """sh_degree None: the rgb array is the colour [N,3]; 0..3: it holds spherical-harmonic
     coefficients [N,(sh_degree+1)^2,3] evaluated per view."""
     mode = COLOR_RGB if sh_degree is None else COLOR_SH
     return GsConfig(int(width), int(height), TILE, int(num_views), int(num_gaussians), int(pair_capacity),
                     float(near_plane), float(lambda_depth), int(fwd_px), int(bwd_px), int(fwd_chunk), int(bwd_chunk),
-                    mode, int(sh_degree or 0))
+                    mode, int(sh_degree or 0), int(blocks_per_sm))
 
 
 def workspace_size(cfg: GsConfig) -> int:
@@ -327,7 +327,7 @@ class Rasterizer:
         old = getattr(self, "cfg", None)  # keep the tuned kernel variants across a capacity change
         tuned = (old.fwd_px_per_thread, old.bwd_px_per_thread, old.fwd_chunk, old.bwd_chunk) if old else (0, 0, 0, 0)
         self.cfg = make_config(self.W, self.H, self.K, self.N, self.cap, self.near_plane, self.lambda_depth, *tuned,
-                               sh_degree=self.sh_degree)
+                               sh_degree=self.sh_degree, blocks_per_sm=old.raster_blocks_per_sm if old else 0)
         self.ws = workspace(self.cfg, self.device)
         self.layout = workspace_layout(self.cfg)
 

@@ -4,7 +4,11 @@ The forward and backward compositing kernels come in variants that differ in how
 each thread owns (1, 2 or 4) and in how many splats a block stages in shared memory per step
 (the chunk depth: 64, 128 or 256 for the forward, 32, 64 or 128 for the backward), and the
 mapping step's forward + L1 loss + backward runs either as one launch (gs_raster_fwd_l1_bwd,
-one pixels-per-thread value for both passes) or as two. Every
+one pixels-per-thread value for both passes, the backward phase at a fixed chunk depth) or as
+two; the chosen form then runs with a cap on its resident blocks per SM (none, 8, 6 or 4),
+which trades occupancy for L1 cache and shared memory per block. When the one-launch form is
+chosen, the forward-only paths (the viewer, plain renders) run at its pixels per thread and
+chunk depth too. Every
 variant takes the same decisions (the forward outputs are bit-identical, the gradients differ
 only in summation order), but which is fastest depends on the image size, the number of views
 and how deep the tiles' lists are. ``tune`` times each variant on the caller's own workspace
@@ -23,6 +27,8 @@ from . import api
 PX = (1, 2, 4)
 FWD_CHUNKS = (64, 128, 256)
 BWD_CHUNKS = (32, 64, 128)
+BLOCKS_PER_SM = (0, 8, 6, 4)  # cap on resident compositing blocks per SM (0: as many as fit)
+FUSED_BWD_CHUNK = 64  # splats the backward phase of the one-launch form stages per chunk
 VARIANTS = PX  # pixels-per-thread values (kept for callers that enumerate them)
 
 
@@ -44,8 +50,8 @@ def tune(r: "api.Rasterizer", g: "api.Gaussians", cams: torch.Tensor, reps: int 
     gradient; then the loss-fused forward followed by the backward (the chosen variants) against
     the one-launch form for each pixels-per-thread value (with that value's best forward chunk),
     against a zero target. Returns {"fwd": {(px, chunk): ms}, "bwd": {(px, chunk): ms},
-    "choice": (fwd_px, bwd_px), "chunks": (fwd_chunk, bwd_chunk), "two_launch_ms": ms,
-    "fused_ms": {(px, chunk): ms}, "fused": bool}.
+    "choice": (fwd_px, bwd_px), "chunks": (fwd_chunk, bwd_chunk in use), "two_launch_ms": ms,
+    "fused_ms": {(px, chunk): ms}, "fused": bool, "blocks_per_sm_ms": {cap: ms}, "blocks_per_sm": cap}.
     """
     stream = stream if stream is not None else torch.cuda.current_stream()
     out = r.new_outputs()
@@ -57,6 +63,7 @@ def tune(r: "api.Rasterizer", g: "api.Gaussians", cams: torch.Tensor, reps: int 
     fwd, bwd = {}, {}
     c = r.cfg
     saved = (c.fwd_px_per_thread, c.bwd_px_per_thread, c.fwd_chunk, c.bwd_chunk)
+    c.raster_blocks_per_sm = 0  # the variants are compared without a cap
     for px in PX:
         for ch in FWD_CHUNKS:
             c.fwd_px_per_thread, c.fwd_chunk = px, ch
@@ -97,6 +104,16 @@ def tune(r: "api.Rasterizer", g: "api.Gaussians", cams: torch.Tensor, reps: int 
     if r.fused_compositing:
         c.fwd_px_per_thread = c.bwd_px_per_thread = fb[0]
         c.fwd_chunk = fb[1]
+    # blocks per SM of the chosen form: fewer resident blocks give each more L1 / shared memory
+    step = (lambda: api.gs_raster_fwd_l1_bwd(c, r.ws, *imgs, rgb_t, depth_t, lg_rgb, lg_depth, loss, stream)) \
+        if r.fused_compositing else two_launches
+    bps = {}
+    for b in BLOCKS_PER_SM:
+        c.raster_blocks_per_sm = b
+        bps[b] = _time(step, reps, stream)
+    c.raster_blocks_per_sm = min(bps, key=bps.get)
     return {"fwd": fwd, "bwd": bwd, "choice": (c.fwd_px_per_thread, c.bwd_px_per_thread),
-            "chunks": (c.fwd_chunk, c.bwd_chunk), "two_launch_ms": two, "fused_ms": fused,
-            "fused": r.fused_compositing}
+            # the one-launch form's backward phase stages FUSED_BWD_CHUNK splats whatever bwd_chunk says
+            "chunks": (c.fwd_chunk, FUSED_BWD_CHUNK if r.fused_compositing else c.bwd_chunk),
+            "two_launch_ms": two, "fused_ms": fused, "fused": r.fused_compositing,
+            "blocks_per_sm_ms": bps, "blocks_per_sm": c.raster_blocks_per_sm}

@@ -54,6 +54,8 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   if (cfg->bwd_chunk != 0 && cfg->bwd_chunk != 32 && cfg->bwd_chunk != 64 && cfg->bwd_chunk != 128) return false;
   L->fwd_chunk = cfg->fwd_chunk;
   L->bwd_chunk = cfg->bwd_chunk;
+  if (cfg->raster_blocks_per_sm < 0 || cfg->raster_blocks_per_sm > 32) return false;
+  L->raster_bps = cfg->raster_blocks_per_sm;
   if (cfg->color_mode != GS_COLOR_RGB && cfg->color_mode != GS_COLOR_SH) return false;
   if (cfg->color_mode == GS_COLOR_SH && (cfg->sh_degree < 0 || cfg->sh_degree > 3)) return false;
   L->color_mode = cfg->color_mode;
@@ -71,6 +73,7 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->max_sort_tiles = sort_tiles(L->cap, L->pair_sort_items);
   L->max_item_tiles = sort_tiles(L->KN, L->item_sort_items);
   L->n_pose_blocks = L->N > 0 ? (L->N + kPoseBlock - 1) / kPoseBlock : 1;
+  L->n_item_chunks = L->KN > 0 ? (L->KN + kPoseBlock - 1) / kPoseBlock : 1;
   const int64_t pixels = static_cast<int64_t>(L->K) * L->W * L->H;
   L->n_loss_blocks = (pixels + 255) / 256 < 1024 ? (pixels + 255) / 256 : 1024;
   size_t o = 0;
@@ -86,7 +89,6 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->proj_tiles = take(KN * 16);
   L->proj_depth_key = take(KN * 4);
   L->proj_radius = take(KN * 4);
-  L->proj_ell = take(KN * sizeof(Ellipse));
   L->proj_rows = take(KN * 8);
   L->row_table = take(cap * 8);
   L->pair_valid = take((cap + 31) / 32 * 4);
@@ -102,7 +104,7 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->hist = take(kMaxSortPasses * 256 * 4);
   L->sort_status = take(static_cast<size_t>(L->passes) * L->max_sort_tiles * 256 * 4);
   L->pair_grads = take(cap * kPairGradStride * 4);
-  L->pose_partials = take(static_cast<size_t>(L->n_pose_blocks) * L->K * 6 * 4);
+  L->pose_partials = take(static_cast<size_t>(kMaxPoseBlocks) * L->K * 6 * 4);
   L->loss_partials = take(static_cast<size_t>(L->n_loss_blocks) * 4);
   L->item_keys[0] = take(KN * 4);
   L->item_keys[1] = take(KN * 4);
@@ -120,7 +122,6 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->emit_last = take(static_cast<size_t>(L->n_emit_blocks) * 4);
   L->live_mask = take((KN + 31) / 32 * 4);
   L->live_wpre = take((KN + 31) / 32 * 4);
-  L->live_g = take((N + 31) / 32 * 4);
   L->live_kg = take(KN * 4);
   L->live_count = take(KN * 4);
   L->live_rows = take(KN * 8);
@@ -128,8 +129,7 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->live_blocks = take(static_cast<size_t>(L->n_proj_groups) * 4);
   L->live_bases = take(static_cast<size_t>(L->n_proj_groups) * 4);
   L->view_lb = take(static_cast<size_t>(L->K) * 8);
-  L->lg_list = take(N * 4);
-  L->lg_lb = take((static_cast<size_t>(compact_blocks((L->N + 31) / 32)) + 2) * 8);
+  L->item_partials = take(KN * 16 * 4);
   L->total = o;
   return true;
 }
@@ -188,8 +188,8 @@ gs_status_t gs_workspace_layout(const gs_config_t* cfg, gs_ws_layout_t* out) {
   out->bin_sort_launches = bin_sort_launch_count(L);
   out->live_mask = L.live_mask;
   out->live_off = L.live_off;
-  out->project_launches = 3;
-  out->project_bwd_launches = 4;
+  out->project_launches = 2;
+  out->project_bwd_launches = 3;
   out->tiles_x = L.Tx;
   out->tiles_y = L.Ty;
   return GS_OK;
@@ -228,8 +228,6 @@ gs_status_t gs_project(const gs_config_t* cfg, const gs_gaussians_t* gaussians, 
   if (cudaMemsetAsync(at<uint32_t>(ws, L.item_hist), 0, 4 * 256 * 4, s) != cudaSuccess) return GS_ERR_CUDA;
   if (cudaMemsetAsync(at<int32_t>(ws, L.tile_diff), 0, static_cast<size_t>(L.K) * (L.Tx + 1) * (L.Ty + 1) * 4, s) !=
       cudaSuccess)
-    return GS_ERR_CUDA;
-  if (cudaMemsetAsync(at<uint32_t>(ws, L.live_g), 0, (static_cast<size_t>(L.N) + 31) / 32 * 4, s) != cudaSuccess)
     return GS_ERR_CUDA;
   return launched(launch_project(L, g, d_cams, ws, s));
 }

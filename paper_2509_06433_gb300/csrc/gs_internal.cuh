@@ -24,7 +24,8 @@ constexpr int kSortItems = 15;        // keys per thread per onesweep tile (defa
 constexpr int kSortTileKeys = kSortThreads * kSortItems;
 constexpr int kMaxSortPasses = 8;
 constexpr int kPairGradStride = 12;   // floats per pair gradient record (10 used)
-constexpr int kPoseBlock = 256;       // Gaussians per projection-backward block
+constexpr int kPoseBlock = 256;       // Gaussians / live items per projection-backward block
+constexpr int kMaxPoseBlocks = 8 * 1024;  // bound on the blocks of the item-parallel backward (8 per SM)
 constexpr uint32_t kSpinLimit = 1u << 21;  // bounded decoupled look-back (about a second of polling)
 constexpr int kDefaultFwdPx = 2;      // pixels per thread of the compositing kernels when
 constexpr int kDefaultBwdPx = 2;      // gs_config_t leaves the choice to the library
@@ -41,6 +42,7 @@ struct Status {
   uint32_t loss_ctr;        // blocks of the loss-fused forward done (reset by the last one)
   uint32_t n_live;          // live items: (view, Gaussian) items that emit at least one pair
   uint32_t view_ctr;        // tile-scan blocks started (one per view)
+  uint32_t proj_done;       // projection blocks finished (the last one scans their live counts)
 };
 static_assert(sizeof(Status) <= 256, "status block");
 
@@ -56,6 +58,7 @@ struct Layout {
   float near_plane, lambda_depth;
   int fwd_px, bwd_px;       // pixels per thread of the compositing kernels (0 = default)
   int fwd_chunk, bwd_chunk; // splats staged per chunk of the compositing kernels (0 = default)
+  int raster_bps;           // cap on resident compositing blocks per SM (0 = none)
   int color_mode, sh_degree, sh_coeffs;  // gs_color_mode_t; SH degree and (degree + 1)^2
   int64_t color_stride;     // index of (view k, Gaussian g) in color_opacity = k * color_stride + g
   int64_t n_proj_blocks;    // ceil(KN / kProjBlock)
@@ -63,9 +66,10 @@ struct Layout {
   int proj_items;           // items per projection block
   int64_t max_sort_tiles;   // onesweep tiles of the pair sort at capacity
   int64_t n_pose_blocks;    // ceil(N / kPoseBlock)
+  int64_t n_item_chunks;    // ceil(KN / kPoseBlock): chunks of live items of the projection backward
   int64_t n_loss_blocks;
-  // byte offsets into the workspace (proj_ell: Ellipse [K*N], the widened alpha >= 1/255 ellipse)
-  size_t status, proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, proj_ell, color_opacity, block_sums,
+  // byte offsets into the workspace
+  size_t status, proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, color_opacity, block_sums,
       block_offsets, keys[2], vals[2], ranges, hist, sort_status, pair_grads, pose_partials, loss_partials;
   // per-item depth sort (u32 depth key, u32 item index), its histograms and look-back status,
   // and the tiles touched by each item in depth order
@@ -89,25 +93,22 @@ struct Layout {
   int64_t n_emit_blocks;    // ceil(cap / kEmitPairs)
   size_t emit_first, emit_last;  // u32 [n_emit_blocks]: items holding each emission block's first / last pair
   // Live items (those that emit at least one pair) and their compaction. Only live items get
-  // projection records (proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, proj_ell,
-  // proj_rows); the others are marked dead and nothing reads their records. A live item's position among
+  // projection records (proj_uv, proj_conic, proj_tiles, proj_depth_key, proj_radius, proj_rows);
+  // the others are marked dead and nothing reads their records. A live item's position among
   // the live items (in increasing k N + g order) is its rank in live_mask: live_wpre[i / 32] +
   // the set bits of word i / 32 below bit i & 31 (live_rank).
   //   live_mask  u32 [ceil(KN / 32)]: bit (i & 31) of word i / 32 set when item i = k N + g is live
   //   live_wpre  u32 [ceil(KN / 32)]: live items before word i / 32
-  //   live_g     u32 [ceil(N / 32)]: bit set when Gaussian g is live in at least one view
   //   live_kg    u32 [KN]: the live items in increasing k N + g order (valid prefix n_live)
   //   live_count u32 [KN]: tiles emitted by each of them
   //   live_rows  uint2 [KN]: their row-span table entries (first entry, number of entries)
   //   live_off   u32 [KN]: their first pair index (emission order), clamped to the capacity
   //   live_blocks, live_bases  u32 [n_proj_groups]: live items of each projection block, and
-  //              the block's first position among all live items (k_live_offsets)
+  //              the block's first position among all live items (scanned by the last block)
   //   view_lb    u64 [K]: look-back status of the per-view pair totals (tile scan)
-  //   lg_list    u32 [N] + lg_lb u64 [compact_blocks(ceil(N / 32)) + 2]: live Gaussians in
-  //              increasing order (gs_project_bwd); block counter, list length (low word),
-  //              look-back status of their compaction
-  size_t live_mask, live_wpre, live_g, live_kg, live_count, live_rows, live_off, live_blocks, live_bases, view_lb,
-      lg_list, lg_lb;
+  //   item_partials float [KN][16]: the projection backward's per-live-item partial gradients
+  size_t live_mask, live_wpre, live_kg, live_count, live_rows, live_off, live_blocks, live_bases, view_lb,
+      item_partials;
   size_t total;
 };
 
@@ -186,92 +187,6 @@ __device__ __forceinline__ uint64_t lb_exclusive_warp(uint64_t* status, uint32_t
   return excl;
 }
 
-// Mask compaction (k_live_scan, k_live_gaussians): blocks of kCompactWarps warps, each warp
-// kCompactWords words of the mask (32 elements per word).
-constexpr int kCompactWarps = 16;
-constexpr int kCompactWords = 64;
-constexpr int64_t kCompactBlockWords = static_cast<int64_t>(kCompactWarps) * kCompactWords;
-__host__ __device__ inline int64_t compact_blocks(int64_t words) {
-  return words > 0 ? (words + kCompactBlockWords - 1) / kCompactBlockWords : 1;
-}
-
-// Compaction of a bit mask (bit i & 31 of word i / 32 set: element i is selected) into the
-// increasing list of the selected elements, by one block of kCompactWarps warps (all threads
-// call it). lb: [0] block counter, [1] -, [2..] look-back status (zeroed before the launch);
-// blocks are numbered in start order and block b takes words [b, b + 1) * kCompactBlockWords.
-// Writes wpre[w] (if not null) = the selected elements before word w, adds the block's count
-// to *n_out, and calls emit(i, pos) for every selected element i with its list position pos.
-// Lane l of a warp reads words 32 q + l (q < kCompactWords / 32); the elements of each
-// non-zero word are then emitted by the lanes of their bits, so the accesses of one word's
-// elements are consecutive.
-template <class Emit>
-__device__ __forceinline__ void compact_mask(const uint32_t* __restrict__ mask, int64_t n_words, uint32_t* wpre,
-                                             uint64_t* lb, uint32_t* n_out, uint32_t* err, Emit emit) {
-  constexpr int Q = kCompactWords / 32;
-  __shared__ uint32_t s_blk, s_wtot[kCompactWarps];
-  __shared__ uint64_t s_base;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_blk = static_cast<uint32_t>(atomicAdd(reinterpret_cast<unsigned long long*>(&lb[0]), 1ull));
-  __syncthreads();
-  const uint32_t blk = s_blk;
-  const int64_t wb = static_cast<int64_t>(blk) * kCompactBlockWords + static_cast<int64_t>(warp) * kCompactWords;
-  uint32_t word[Q], excl[Q];
-  uint32_t running = 0;
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int64_t w = wb + 32 * q + lane;
-    word[q] = w < n_words ? mask[w] : 0u;
-    const uint32_t c = __popc(word[q]);
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    excl[q] = running + incl - c;
-    running += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  if (lane == 0) s_wtot[warp] = running;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t tot = 0;
-    for (int w = 0; w < kCompactWarps; ++w) tot += s_wtot[w];
-    const uint64_t base = lb_exclusive_warp(lb + 2, blk, tot, err);
-    if (lane == 0) {
-      s_base = base;
-      if (tot) atomicAdd(n_out, tot);
-    }
-  }
-  __syncthreads();
-  uint64_t wbase = s_base;
-  for (int w = 0; w < warp; ++w) wbase += s_wtot[w];
-  uint32_t lm;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lm));
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int64_t w = wb + 32 * q + lane;
-    if (wpre && w < n_words) wpre[w] = static_cast<uint32_t>(wbase + excl[q]);
-    uint32_t todo = __ballot_sync(0xffffffffu, word[q] != 0u);
-    // four non-zero words per round: their elements' emits are independent, so their loads
-    // are in flight together
-    while (todo) {
-      int src[4];
-      uint32_t m[4], e[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        src[r] = todo ? __ffs(todo) - 1 : -1;
-        todo &= todo ? todo - 1 : 0u;
-        m[r] = __shfl_sync(0xffffffffu, word[q], src[r] < 0 ? 0 : src[r]);
-        e[r] = __shfl_sync(0xffffffffu, excl[q], src[r] < 0 ? 0 : src[r]);
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if (src[r] >= 0 && ((m[r] >> lane) & 1u))
-          emit((wb + 32 * q + src[r]) * 32 + lane, wbase + e[r] + __popc(m[r] & lm));
-    }
-  }
-}
-
 // Whether item kg is live (emits pairs); its projection records exist only then.
 __device__ __forceinline__ bool item_live(const uint32_t* live_mask, int64_t kg) {
   return (live_mask[kg >> 5] >> (kg & 31)) & 1u;
@@ -340,6 +255,30 @@ inline cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// Dynamic shared memory that caps `kernel` at `bps` resident blocks per multiprocessor (0: no
+// cap, none added): the multiprocessor's shared memory divided by bps, less the kernel's static
+// shared memory and the per-block reserve, rounded down to 128 bytes (0 when the cap is above
+// what fits anyway). Raises the kernel's dynamic shared memory limit when the padding needs it.
+template <typename... KArgs>
+inline size_t cap_smem(void (*kernel)(KArgs...), int bps) {
+  if (bps <= 0) return 0;
+  int dev = 0, per_sm = 0, reserve = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 0;
+  long pad = static_cast<long>(per_sm) / bps - static_cast<long>(fa.sharedSizeBytes) - reserve;
+  const long room = static_cast<long>(optin) - static_cast<long>(fa.sharedSizeBytes);
+  pad = (pad < room ? pad : room) / 128 * 128;
+  if (pad <= 0) return 0;
+  if (pad > fa.maxDynamicSharedSizeBytes &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(pad)) != cudaSuccess)
+    return 0;
+  return static_cast<size_t>(pad);
 }
 
 // ---------------------------------------------------------------------------- device helpers

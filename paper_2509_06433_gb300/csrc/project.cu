@@ -245,7 +245,6 @@ __device__ __forceinline__ Projected project_item(const Layout& L, const GaussPt
         const float kap = __fmul_rn(2.0f, Lm);
         P.E = Ellipse{u, v, bb, __fdiv_rn(1.0f, c), __fsqrt_rn(det), __fsqrt_rn(__fmul_rn(kap, a)),
                       __fsqrt_rn(__fmul_rn(kap, c)), __fdiv_rn(bb, a)};
-        at<Ellipse>(ws, L.proj_ell)[idx] = P.E;
         P.live = true;
       }
     }
@@ -276,7 +275,8 @@ __device__ __forceinline__ Projected project_item(const Layout& L, const GaussPt
 // 2 writes its row-span table entries. An item that emits pairs is live: its bit goes to
 // live_mask, its binning record (depth key, tiles emitted, item id, row-span entries) to the
 // block's segment of the staging arrays in item order (compacted by k_live_copy), its depth
-// key's digits to the item-sort histograms.
+// key's digits to the item-sort histograms. The last block to finish scans the blocks' live
+// counts into their first positions among the live items.
 __global__ void __launch_bounds__(kProjThreads, 3) k_project(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                          uint8_t* __restrict__ ws) {
   pdl_wait();
@@ -544,12 +544,6 @@ __global__ void __launch_bounds__(kProjThreads, 3) k_project(Layout L, GaussPtrs
 #pragma unroll
       for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p * 256 + ((item_key >> (8 * p)) & 0xffu)], 1u);
     }
-    // Gaussians live in at least one view: one atomic OR per warp and mask word
-    const int64_t g_item = is_live ? idx - static_cast<int64_t>(kv) * L.N : 0;
-    const uint32_t gw = is_live ? static_cast<uint32_t>(g_item >> 5) : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, gw);
-    const uint32_t bits = __reduce_or_sync(peers, is_live ? (1u << (g_item & 31)) : 0u);
-    if (is_live && lane == __ffs(peers) - 1) atomicOr(&at<uint32_t>(ws, L.live_g)[gw], bits);
     __syncthreads();
     if (threadIdx.x == 0) {
       uint32_t tot = 0;
@@ -579,39 +573,45 @@ __global__ void __launch_bounds__(kProjThreads, 3) k_project(Layout L, GaussPtrs
   for (int p = 0; p < 4; ++p)
     for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kProjThreads + threadIdx.x; i < used; i += gsize)
       sst[static_cast<uint64_t>(p) * used + i] = 0;
-  pdl_trigger();
-}
-
-// Exclusive scan of the projection blocks' live counts (one block): each block's first
-// position among the live items, and the number of live items.
-__global__ void __launch_bounds__(1024) k_live_offsets(Layout L, uint8_t* __restrict__ ws) {
-  pdl_begin();
-  const uint32_t* cnt = at<uint32_t>(ws, L.live_blocks);
-  uint32_t* base = at<uint32_t>(ws, L.live_bases);
-  __shared__ uint32_t s_w[32];
-  uint32_t carry = 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t b0 = 0; b0 < L.n_proj_groups; b0 += 1024) {
-    const int64_t b = b0 + threadIdx.x;
-    const uint32_t x = b < L.n_proj_groups ? cnt[b] : 0u;
-    uint32_t incl = x;
+  // the last block to finish scans the blocks' live counts: each block's first position among
+  // the live items (live_bases), and the number of live items
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  Status* st = at<Status>(ws, L.status);
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->proj_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    const uint32_t* cnt = at<uint32_t>(ws, L.live_blocks);
+    uint32_t* bases = at<uint32_t>(ws, L.live_bases);
+    uint32_t carry = 0;
+    for (int64_t b0 = 0; b0 < L.n_proj_groups; b0 += kProjThreads) {
+      const int64_t b = b0 + threadIdx.x;
+      const uint32_t x = b < L.n_proj_groups ? __ldcg(&cnt[b]) : 0u;
+      uint32_t incl = x;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) s_wcnt[wib] = incl;
+      __syncthreads();
+      uint32_t before = 0, total = 0;
+      for (int w = 0; w < kProjThreads / 32; ++w) {
+        before += w < wib ? s_wcnt[w] : 0u;
+        total += s_wcnt[w];
+      }
+      if (b < L.n_proj_groups) bases[b] = carry + before + incl - x;
+      carry += total;
+      __syncthreads();
     }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    uint32_t before = 0, total = 0;
-    for (int w = 0; w < 32; ++w) {
-      before += w < warp ? s_w[w] : 0u;
-      total += s_w[w];
+    if (threadIdx.x == 0) {
+      st->n_live = carry;
+      st->proj_done = 0;
     }
-    if (b < L.n_proj_groups) base[b] = carry + before + incl - x;
-    carry += total;
-    __syncthreads();
   }
-  if (threadIdx.x == 0) at<Status>(ws, L.status)->n_live = carry;
+  pdl_trigger();
 }
 
 // Compaction of the live items, in increasing item order k N + g: each projection block's
@@ -658,7 +658,6 @@ cudaError_t launch_project(const Layout& L, const GaussPtrs& g, const gs_camera_
   auto* w = static_cast<uint8_t*>(ws);
   const unsigned groups = static_cast<unsigned>(L.n_proj_groups);
   launch(k_project, groups, kProjThreads, 0, s, L, g, cams, w);
-  launch(k_live_offsets, 1, 1024, 0, s, L, w);
   launch(k_live_copy, groups, kProjThreads, 0, s, L, w);
   return cudaGetLastError();
 }

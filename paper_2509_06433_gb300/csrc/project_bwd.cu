@@ -112,95 +112,75 @@ __device__ __forceinline__ Sum10 sum_pairs_warp(const float* __restrict__ pg, co
   return mine;
 }
 
-// The Gaussians live in at least one view (live_g mask of the projection), compacted in
-// increasing order into lg_list (its length to the low word of lg_lb[1]).
-__global__ void __launch_bounds__(kCompactWarps * 32) k_live_gaussians(Layout L, uint8_t* __restrict__ ws) {
-  pdl_begin();
-  uint64_t* lb = at<uint64_t>(ws, L.lg_lb);
-  uint32_t* list = at<uint32_t>(ws, L.lg_list);
-  const uint32_t* live_g = at<uint32_t>(ws, L.live_g);
-  compact_mask(live_g, (L.N + 31) / 32, static_cast<uint32_t*>(nullptr), lb, reinterpret_cast<uint32_t*>(&lb[1]),
-               &at<Status>(ws, L.status)->err, [&](int64_t g, uint64_t pos) { list[pos] = static_cast<uint32_t>(g); });
+// Blocks of k_item_grads: up to eight per multiprocessor, no more than there are chunks.
+int64_t item_grad_blocks(const Layout& L) {
+  int64_t resident = static_cast<int64_t>(device_sms()) * 8;
+  if (resident > kMaxPoseBlocks) resident = kMaxPoseBlocks;
+  return L.n_item_chunks < resident ? L.n_item_chunks : resident;
 }
 
-// With out.overwrite: the gradients of the Gaussians no view sees are stored as zero.
-__global__ void __launch_bounds__(256) k_zero_unseen(Layout L, const uint8_t* __restrict__ ws, gs_grads_t out) {
-  pdl_begin();
-  const uint32_t* live_g = at<uint32_t>(ws, L.live_g);
-  const int cw = L.color_mode == GS_COLOR_SH ? 3 * L.sh_coeffs : 3;
-  for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < L.N;
-       g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    if ((live_g[g >> 5] >> (g & 31)) & 1u) continue;
-    if (out.means) out.means[3 * g] = out.means[3 * g + 1] = out.means[3 * g + 2] = 0.0f;
-    if (out.log_scales) out.log_scales[3 * g] = out.log_scales[3 * g + 1] = out.log_scales[3 * g + 2] = 0.0f;
-    if (out.quats)
-      for (int j = 0; j < 4; ++j) out.quats[4 * g + j] = 0.0f;
-    if (out.opacity_logits) out.opacity_logits[g] = 0.0f;
-    if (out.rgb)
-      for (int j = 0; j < cw; ++j) out.rgb[cw * g + j] = 0.0f;
-  }
-}
+// Per-item partial gradient of the projection backward (16 floats): the mean's gradient in
+// world coordinates (0-2), the gradient of M = Q diag(exp(s)) (3-11, row-major), the opacity's
+// (12) and the colour's (13-15; with spherical harmonics the colour gradient after the clamp).
+constexpr int kPartial = 16;
 
-// One thread per live Gaussian (lg_list); blocks past the list's end return at once.
-__global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
-                                                           const uint8_t* __restrict__ ws, gs_grads_t out,
-                                                           float* __restrict__ pose_partials) {
+// Backward of the projection for one live (view, Gaussian) item, one thread per item in the
+// compact order of the live items (increasing k N + g): sums the item's pair records in slot
+// order (warp-cooperatively for items with many pairs), applies the chain rule of the view's
+// projection, writes the item's partial (when parameter gradients are wanted) and sums the
+// items' pose gradients per view: a chunk's items are in view order, so each view present in a
+// chunk gets the chunk's sum, added in chunk order to the block's per-view sums in shared
+// memory, which go to pose_partials[block][view] at the end. The blocks stride over the chunks
+// of kPoseBlock live items (the grid does not depend on the data, so the order is fixed).
+__global__ void __launch_bounds__(kPoseBlock) k_item_grads(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
+                                                          uint8_t* __restrict__ ws, int want_params,
+                                                          float* __restrict__ pose_partials) {
   pdl_wait();
-  const int64_t n_list = static_cast<int64_t>(*reinterpret_cast<const uint32_t*>(&at<uint64_t>(ws, L.lg_lb)[1]));
-  const int64_t li = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
-  if (static_cast<int64_t>(blockIdx.x) * kPoseBlock >= n_list) return;  // (whole block: uniform)
-  const bool valid = li < n_list;
-  const int64_t g = valid ? static_cast<int64_t>(at<uint32_t>(ws, L.lg_list)[li]) : 0;
-  const uint32_t* live_mask = at<uint32_t>(ws, L.live_mask);
-  const uint32_t* live_wpre = at<uint32_t>(ws, L.live_wpre);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t n_live = at<Status>(ws, L.status)->n_live;
+  const int64_t chunks = (n_live + kPoseBlock - 1) / kPoseBlock;
+  const uint32_t* live_kg = at<uint32_t>(ws, L.live_kg);
   const uint32_t* live_off = at<uint32_t>(ws, L.live_off);
   const uint32_t* live_count = at<uint32_t>(ws, L.live_count);
   const float* pg = at<float>(ws, L.pair_grads);
   const uint32_t* pvalid = at<uint32_t>(ws, L.pair_valid);
+  float4* partials = at<float4>(ws, L.item_partials);
+  extern __shared__ float s_pose[];  // [K][6]: the block's pose sums per view
   __shared__ float s_red[kPoseBlock / 32][6];
-
-  float p[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, lg = 0.0f;
-  if (valid) {
-    for (int j = 0; j < 3; ++j) p[j] = load_attr(G.means, 3 * g + j, G.means_dtype);
-    for (int j = 0; j < 3; ++j) ls[j] = load_attr(G.log_scales, 3 * g + j, G.dtype);
-    for (int j = 0; j < 4; ++j) q[j] = load_attr(G.quats, 4 * g + j, G.dtype);
-    lg = load_attr(G.logits, g, G.dtype);
-  }
-  const float qlen = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-  const float iq = qlen > 0.0f ? 1.0f / qlen : 0.0f;
-  const float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
-  float Q[3][3];
-  Q[0][0] = 1.f - 2.f * (y * y + z * z); Q[0][1] = 2.f * (x * y - w * z); Q[0][2] = 2.f * (x * z + w * y);
-  Q[1][0] = 2.f * (x * y + w * z); Q[1][1] = 1.f - 2.f * (x * x + z * z); Q[1][2] = 2.f * (y * z - w * x);
-  Q[2][0] = 2.f * (x * z - w * y); Q[2][1] = 2.f * (y * z + w * x); Q[2][2] = 1.f - 2.f * (x * x + y * y);
-  const float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
-  float M[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) M[i][j] = Q[i][j] * S[j];
-
-  float d_mean[3] = {0, 0, 0}, dM_acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  float d_op = 0.0f, d_rgb[3] = {0, 0, 0};
-  bool sh_touched = false;  // spherical-harmonic gradients already written for this Gaussian
-
-  for (int k = 0; k < L.K; ++k) {
-    float pose[6] = {0, 0, 0, 0, 0, 0};
-    int4 tl = make_int4(0, 0, 0, 0);  // (pair offset, -, -, tiles emitted)
-    const int64_t kg = static_cast<int64_t>(k) * L.N + g;
-    if (valid && item_live(live_mask, kg)) {
-      const uint32_t pos = live_rank(live_mask, live_wpre, kg);
-      tl.x = static_cast<int>(live_off[pos]);
-      tl.w = static_cast<int>(live_count[pos]);
+  __shared__ int s_k0, s_k1;
+  for (int i = threadIdx.x; i < 6 * L.K; i += kPoseBlock) s_pose[i] = 0.0f;
+  for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+    const int64_t pos = c * kPoseBlock + threadIdx.x;
+    const bool valid = pos < n_live;
+    uint32_t kg = 0, off = 0, cnt = 0;
+    if (valid) {
+      kg = live_kg[pos];
+      off = live_off[pos];
+      cnt = live_count[pos];
     }
-    const Sum10 s =
-        sum_pairs_warp(pg, pvalid, static_cast<uint32_t>(tl.x), static_cast<uint32_t>(tl.w), L.cap, tl.w > 0);
-    if (tl.w > 0) {
+    const int k = static_cast<int>(kg / static_cast<uint32_t>(L.N > 0 ? L.N : 1));
+    const int64_t g = static_cast<int64_t>(kg) - static_cast<int64_t>(k) * L.N;
+    const Sum10 s = sum_pairs_warp(pg, pvalid, off, cnt, L.cap, valid);
+    float pose[6] = {0, 0, 0, 0, 0, 0};
+    if (valid) {
+      float p[3], ls[3], q[4];
+      for (int j = 0; j < 3; ++j) p[j] = load_attr(G.means, 3 * g + j, G.means_dtype);
+      for (int j = 0; j < 3; ++j) ls[j] = load_attr(G.log_scales, 3 * g + j, G.dtype);
+      for (int j = 0; j < 4; ++j) q[j] = load_attr(G.quats, 4 * g + j, G.dtype);
+      const float qlen = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+      const float iq = qlen > 0.0f ? 1.0f / qlen : 0.0f;
+      const float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
+      float Q[3][3];
+      Q[0][0] = 1.f - 2.f * (y * y + z * z); Q[0][1] = 2.f * (x * y - w * z); Q[0][2] = 2.f * (x * z + w * y);
+      Q[1][0] = 2.f * (x * y + w * z); Q[1][1] = 1.f - 2.f * (x * x + z * z); Q[1][2] = 2.f * (y * z - w * x);
+      Q[2][0] = 2.f * (x * z - w * y); Q[2][1] = 2.f * (y * z + w * x); Q[2][2] = 1.f - 2.f * (x * x + y * y);
+      const float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+      float M[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[i][j] = Q[i][j] * S[j];
       const float gu = s.v[0], gv = s.v[1], gA = s.v[2], gB = s.v[3], gC = s.v[4], gz = s.v[5];
-      d_op += s.v[6];
-      d_rgb[0] += s.v[7];
-      d_rgb[1] += s.v[8];
-      d_rgb[2] += s.v[9];
       const gs_camera_t cam = cams[k];
       const float* R = cam.R;
       float pc[3];
@@ -255,11 +235,6 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
         dN[1][j] = J11 * dm2[j];
         dN[2][j] = J02 * dm1[j] + J12 * dm2[j];
       }
-      // dM = R^T dN (accumulated over views)
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) dM_acc[i][j] += R[i] * dN[0][j] + R[3 + i] * dN[1][j] + R[6 + i] * dN[2][j];
       // camera-space mean
       const float iz2 = iz * iz;
       float dpc[3];
@@ -275,8 +250,9 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
         dpc[1] += -cam.fy * iz2 * dJ12;
         dpc[2] += cam.fy * pc[1] * iz2 * iz * dJ12;
       }
+      float dmean[3];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) d_mean[j] += R[j] * dpc[0] + R[3 + j] * dpc[1] + R[6 + j] * dpc[2];
+      for (int j = 0; j < 3; ++j) dmean[j] = R[j] * dpc[0] + R[3 + j] * dpc[1] + R[6 + j] * dpc[2];
       // pose: rho = dp_c ; phi = p_c x dp_c + vee(A - A^T), A = Nm dN^T
       float Am[3][3];
 #pragma unroll
@@ -289,71 +265,169 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
       pose[3] = pc[1] * dpc[2] - pc[2] * dpc[1] + Am[1][2] - Am[2][1];
       pose[4] = pc[2] * dpc[0] - pc[0] * dpc[2] + Am[2][0] - Am[0][2];
       pose[5] = pc[0] * dpc[1] - pc[1] * dpc[0] + Am[0][1] - Am[1][0];
+      float gc0 = s.v[7], gc1 = s.v[8], gc2 = s.v[9];
       if (L.color_mode == GS_COLOR_SH) {
-        // view-dependent colour: this view's colour gradient through the clamp (raw < 0: zero)
-        // into the coefficients, dL/df_i = Y_i g, written per view (accumulated in the output,
-        // so no per-coefficient registers), and into the unit direction u = (p - C) / |p - C|:
-        // dL/dp = (I - u u^T) (sum_i (f_i . g) grad Y_i) / |p - C|; the camera centre moves by
-        // -R^T rho under the pose perturbation, so dL/drho = R dL/dp.
+        // view-dependent colour: the colour gradient through the clamp (raw < 0: zero); its part
+        // through the unit direction u = (p - C) / |p - C| goes to the mean, dL/dp = (I - u u^T)
+        // (sum_i (f_i . g) grad Y_i) / |p - C|, and, as the camera centre moves by -R^T rho
+        // under the pose perturbation, to rho (dL/drho = R dL/dp)
         const ShDir u = sh_dir(p[0], p[1], p[2], cam);
         float Y[kShMaxCoeffs];
         sh_basis(u.x, u.y, u.z, Y);
         bool fin = true;
         const float3 raw = sh_raw(G.rgb, G.dtype, g, L.sh_coeffs, Y, fin);
-        const float gc0 = raw.x >= 0.0f ? s.v[7] : 0.0f, gc1 = raw.y >= 0.0f ? s.v[8] : 0.0f,
-                    gc2 = raw.z >= 0.0f ? s.v[9] : 0.0f;
-        const int64_t base = g * L.sh_coeffs * 3;
-        const bool store_c = out.overwrite && !sh_touched;
-        float sv[kShMaxCoeffs];
-#pragma unroll
-        for (int i = 0; i < kShMaxCoeffs; ++i) {
-          sv[i] = 0.0f;
-          if (i < L.sh_coeffs) {
-            const float f0 = load_attr(G.rgb, base + 3 * i + 0, G.dtype);
-            const float f1 = load_attr(G.rgb, base + 3 * i + 1, G.dtype);
-            const float f2 = load_attr(G.rgb, base + 3 * i + 2, G.dtype);
-            sv[i] = gc0 * f0 + gc1 * f1 + gc2 * f2;
-            if (out.rgb) {
-              float* o3 = out.rgb + base + 3 * i;
-              put(o3 + 0, store_c, Y[i] * gc0);
-              put(o3 + 1, store_c, Y[i] * gc1);
-              put(o3 + 2, store_c, Y[i] * gc2);
-            }
-          }
-        }
-        sh_touched = true;
+        gc0 = raw.x >= 0.0f ? gc0 : 0.0f;
+        gc1 = raw.y >= 0.0f ? gc1 : 0.0f;
+        gc2 = raw.z >= 0.0f ? gc2 : 0.0f;
         if (L.sh_degree > 0) {
-          float gx, gy, gz;
-          sh_basis_vjp(u.x, u.y, u.z, sv, gx, gy, gz);
-          const float ud = gx * u.x + gy * u.y + gz * u.z;
-          const float dd0 = (gx - u.x * ud) * u.inv_r, dd1 = (gy - u.y * ud) * u.inv_r,
-                      dd2 = (gz - u.z * ud) * u.inv_r;
-          d_mean[0] += dd0;
-          d_mean[1] += dd1;
-          d_mean[2] += dd2;
+          const int64_t base = g * L.sh_coeffs * 3;
+          float sv[kShMaxCoeffs];
+#pragma unroll
+          for (int i = 0; i < kShMaxCoeffs; ++i) {
+            sv[i] = 0.0f;
+            if (i < L.sh_coeffs)
+              sv[i] = gc0 * load_attr(G.rgb, base + 3 * i + 0, G.dtype) + gc1 * load_attr(G.rgb, base + 3 * i + 1, G.dtype) +
+                      gc2 * load_attr(G.rgb, base + 3 * i + 2, G.dtype);
+          }
+          float gx, gy, gzz;
+          sh_basis_vjp(u.x, u.y, u.z, sv, gx, gy, gzz);
+          const float ud = gx * u.x + gy * u.y + gzz * u.z;
+          const float dd0 = (gx - u.x * ud) * u.inv_r, dd1 = (gy - u.y * ud) * u.inv_r, dd2 = (gzz - u.z * ud) * u.inv_r;
+          dmean[0] += dd0;
+          dmean[1] += dd1;
+          dmean[2] += dd2;
           pose[0] += R[0] * dd0 + R[1] * dd1 + R[2] * dd2;
           pose[1] += R[3] * dd0 + R[4] * dd1 + R[5] * dd2;
           pose[2] += R[6] * dd0 + R[7] * dd1 + R[8] * dd2;
         }
       }
-    }
-    // block reduction of this view's pose gradient
+      if (want_params) {
+        // dM = R^T dN
+        float dM[3][3];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      float v = pose[i];
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5][i] = v;
+          for (int j = 0; j < 3; ++j) dM[i][j] = R[i] * dN[0][j] + R[3 + i] * dN[1][j] + R[6 + i] * dN[2][j];
+        float4* dst = partials + pos * (kPartial / 4);
+        dst[0] = make_float4(dmean[0], dmean[1], dmean[2], dM[0][0]);
+        dst[1] = make_float4(dM[0][1], dM[0][2], dM[1][0], dM[1][1]);
+        dst[2] = make_float4(dM[1][2], dM[2][0], dM[2][1], dM[2][2]);
+        dst[3] = make_float4(s.v[6], gc0, gc1, gc2);
+      }
     }
+    // the block's pose sums per view: its items are in view order, from view s_k0 to s_k1
+    if (threadIdx.x == 0) s_k0 = valid ? k : 0;
+    const bool last_valid = valid && (threadIdx.x == kPoseBlock - 1 || pos + 1 == n_live);
+    if (last_valid) s_k1 = k;
     __syncthreads();
-    if (threadIdx.x < 6) {
-      float v = 0.0f;
-      for (int wv = 0; wv < kPoseBlock / 32; ++wv) v += s_red[wv][threadIdx.x];
-      pose_partials[(static_cast<int64_t>(blockIdx.x) * L.K + k) * 6 + threadIdx.x] = v;
+    const int k0 = s_k0, k1 = s_k1;
+    for (int kk = k0; kk <= k1; ++kk) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        float v = (valid && k == kk) ? pose[i] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[wib][i] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < 6) {
+        float v = 0.0f;
+        for (int wv = 0; wv < kPoseBlock / 32; ++wv) v += s_red[wv][threadIdx.x];
+        s_pose[6 * kk + threadIdx.x] += v;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
-  if (!valid) return;
+  __syncthreads();
+  for (int i = threadIdx.x; i < 6 * L.K; i += kPoseBlock)
+    pose_partials[static_cast<int64_t>(blockIdx.x) * 6 * L.K + i] = s_pose[i];
+  pdl_trigger();
+}
+
+// Parameter gradients, one thread per Gaussian: the partials of its live items summed in view
+// order (found by their rank among the live items), then the chain rule through M = Q
+// diag(exp(s)) to the log-scales and (through the normalisation) the quaternion, the opacity's
+// sigmoid to the logit; with spherical harmonics each view's colour gradient goes to the
+// coefficients through that view's basis values. A Gaussian that no view sees gets zero
+// gradients (stored with out.overwrite, nothing added otherwise).
+__global__ void __launch_bounds__(kPoseBlock) k_gaussian_grads(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
+                                                              const uint8_t* __restrict__ ws, gs_grads_t out) {
+  pdl_wait();
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * kPoseBlock + threadIdx.x;
+  if (g >= L.N) return;
+  const uint32_t* live_mask = at<uint32_t>(ws, L.live_mask);
+  const uint32_t* live_wpre = at<uint32_t>(ws, L.live_wpre);
+  const float4* partials = at<float4>(ws, L.item_partials);
+  const bool store = out.overwrite != 0;
+  const bool sh = L.color_mode == GS_COLOR_SH;
+  float acc[kPartial];
+#pragma unroll
+  for (int i = 0; i < kPartial; ++i) acc[i] = 0.0f;
+  bool seen = false, sh_touched = false;
+  uint32_t words[4], bases[4];
+  float p[3] = {0, 0, 0};
+  if (sh && out.rgb) for (int j = 0; j < 3; ++j) p[j] = load_attr(G.means, 3 * g + j, G.means_dtype);
+  for (int k = 0; k < L.K; ++k) {
+    // the mask words and rank bases of four views at a time are loaded together
+    if ((k & 3) == 0) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t kgj = static_cast<int64_t>(k + j) * L.N + g;
+        words[j] = k + j < L.K ? live_mask[kgj >> 5] : 0u;
+        bases[j] = (words[j] >> (kgj & 31)) & 1u ? live_wpre[kgj >> 5] : 0u;
+      }
+    }
+    const int64_t kg = static_cast<int64_t>(k) * L.N + g;
+    const uint32_t word = words[k & 3];
+    if (!((word >> (kg & 31)) & 1u)) continue;
+    seen = true;
+    const uint32_t pos = bases[k & 3] + __popc(word & ((1u << (kg & 31)) - 1u));
+    const float4* src = partials + static_cast<int64_t>(pos) * (kPartial / 4);
+    const float4 a = src[0], b = src[1], c = src[2], d = src[3];
+    const float v[kPartial] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
+#pragma unroll
+    for (int i = 0; i < kPartial; ++i) acc[i] += v[i];
+    if (sh && out.rgb) {  // dL/df_i += Y_i(u_k) g_k for this view's direction
+      const ShDir u = sh_dir(p[0], p[1], p[2], cams[k]);
+      float Y[kShMaxCoeffs];
+      sh_basis(u.x, u.y, u.z, Y);
+      const int64_t base = g * L.sh_coeffs * 3;
+      const bool first = store && !sh_touched;
+      for (int i = 0; i < L.sh_coeffs; ++i) {
+        float* o3 = out.rgb + base + 3 * i;
+        put(o3 + 0, first, Y[i] * d.y);
+        put(o3 + 1, first, Y[i] * d.z);
+        put(o3 + 2, first, Y[i] * d.w);
+      }
+      sh_touched = true;
+    }
+  }
+  if (!seen) {
+    if (store) {
+      if (out.means) out.means[3 * g] = out.means[3 * g + 1] = out.means[3 * g + 2] = 0.0f;
+      if (out.log_scales) out.log_scales[3 * g] = out.log_scales[3 * g + 1] = out.log_scales[3 * g + 2] = 0.0f;
+      if (out.quats)
+        for (int j = 0; j < 4; ++j) out.quats[4 * g + j] = 0.0f;
+      if (out.opacity_logits) out.opacity_logits[g] = 0.0f;
+      if (out.rgb) {
+        const int cw = sh ? 3 * L.sh_coeffs : 3;
+        for (int j = 0; j < cw; ++j) out.rgb[cw * g + j] = 0.0f;
+      }
+    }
+    return;
+  }
+  float ls[3], q[4];
+  for (int j = 0; j < 3; ++j) ls[j] = load_attr(G.log_scales, 3 * g + j, G.dtype);
+  for (int j = 0; j < 4; ++j) q[j] = load_attr(G.quats, 4 * g + j, G.dtype);
+  const float lg = load_attr(G.logits, g, G.dtype);
+  const float qlen = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const float iq = qlen > 0.0f ? 1.0f / qlen : 0.0f;
+  const float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
+  float Q[3][3];
+  Q[0][0] = 1.f - 2.f * (y * y + z * z); Q[0][1] = 2.f * (x * y - w * z); Q[0][2] = 2.f * (x * z + w * y);
+  Q[1][0] = 2.f * (x * y + w * z); Q[1][1] = 1.f - 2.f * (x * x + z * z); Q[1][2] = 2.f * (y * z - w * x);
+  Q[2][0] = 2.f * (x * z - w * y); Q[2][1] = 2.f * (y * z + w * x); Q[2][2] = 1.f - 2.f * (x * x + y * y);
+  const float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
   // M = Q diag(S): dQ = dM diag(S), dS_j = sum_i dM_ij Q_ij
   float dQ[3][3], dls[3];
 #pragma unroll
@@ -361,8 +435,9 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
     float ds = 0.0f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      dQ[i][j] = dM_acc[i][j] * S[j];
-      ds += dM_acc[i][j] * Q[i][j];
+      const float dMij = acc[3 + 3 * i + j];
+      dQ[i][j] = dMij * S[j];
+      ds += dMij * Q[i][j];
     }
     dls[j] = ds * S[j];
   }
@@ -377,31 +452,20 @@ __global__ void __launch_bounds__(kPoseBlock) k_project_bwd(Layout L, GaussPtrs 
   const float qd = w * dqh[0] + x * dqh[1] + y * dqh[2] + z * dqh[3];
   const float qh[4] = {w, x, y, z};
   const float o = 1.0f / (1.0f + expf(-lg));
-  // accumulate (+=) or, with out.overwrite, store (=)
-  const bool store = out.overwrite != 0;
   if (out.means)
-    for (int j = 0; j < 3; ++j) put(out.means + 3 * g + j, store, d_mean[j]);
+    for (int j = 0; j < 3; ++j) put(out.means + 3 * g + j, store, acc[j]);
   if (out.log_scales)
     for (int j = 0; j < 3; ++j) put(out.log_scales + 3 * g + j, store, dls[j]);
   if (out.quats)
-    for (int j = 0; j < 4; ++j)
-      put(out.quats + 4 * g + j, store, (dqh[j] - qh[j] * qd) * iq);
-  if (out.opacity_logits) put(out.opacity_logits + g, store, d_op * o * (1.0f - o));
-  if (out.rgb) {
-    if (L.color_mode != GS_COLOR_SH) {
-      for (int j = 0; j < 3; ++j) put(out.rgb + 3 * g + j, store, d_rgb[j]);
-    } else if (out.overwrite && !sh_touched) {  // seen by no view: zero gradient
-      for (int j = 0; j < 3 * L.sh_coeffs; ++j) out.rgb[g * 3 * L.sh_coeffs + j] = 0.0f;
-    }
-  }
-  pdl_trigger();
+    for (int j = 0; j < 4; ++j) put(out.quats + 4 * g + j, store, (dqh[j] - qh[j] * qd) * iq);
+  if (out.opacity_logits) put(out.opacity_logits + g, store, acc[12] * o * (1.0f - o));
+  if (out.rgb && !sh)
+    for (int j = 0; j < 3; ++j) put(out.rgb + 3 * g + j, store, acc[13 + j]);
 }
 
-// pose[k][i] += (or, with overwrite, =) the sum over blocks of pose_partials[block][k][i].
-__global__ void k_pose_reduce(const float* __restrict__ partials, const uint32_t* __restrict__ n_list, int K,
-                              float* __restrict__ pose, int overwrite) {
+__global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_blocks, int K, float* __restrict__ pose,
+                              int overwrite) {
   pdl_begin();
-  const int64_t n_blocks = (static_cast<int64_t>(*n_list) + kPoseBlock - 1) / kPoseBlock;
   const int k = blockIdx.x;
   const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float v = 0.0f;
@@ -464,21 +528,18 @@ cudaError_t launch_project_bwd(const Layout& L, const GaussPtrs& g, const gs_cam
     if (out.overwrite && out.pose) cudaMemsetAsync(out.pose, 0, sizeof(float) * 6 * L.K, s);
     return cudaGetLastError();
   }
+  auto* w = static_cast<uint8_t*>(ws);
   float* partials = at<float>(ws, L.pose_partials);
-  uint64_t* lb = at<uint64_t>(ws, L.lg_lb);
-  const int64_t cblocks = compact_blocks((L.N + 31) / 32);
-  cudaMemsetAsync(lb, 0, (static_cast<size_t>(cblocks) + 2) * 8, s);
-  launch(k_live_gaussians, static_cast<unsigned>(cblocks), kCompactWarps * 32, 0, s, L, static_cast<uint8_t*>(ws));
-  if (out.overwrite && (out.means || out.log_scales || out.quats || out.opacity_logits || out.rgb)) {
-    const int64_t zb = (L.N + 255) / 256, cap = static_cast<int64_t>(device_sms()) * 8;
-    launch(k_zero_unseen, static_cast<unsigned>(zb < cap ? zb : cap), 256, 0, s, L, static_cast<const uint8_t*>(ws),
-           out);
-  }
-  launch(k_project_bwd, static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s, L, g, cams, static_cast<uint8_t*>(ws),
-         out, partials);
+  const bool params = out.means || out.log_scales || out.quats || out.opacity_logits || out.rgb;
+  const int64_t grid = item_grad_blocks(L);
+  const size_t smem = sizeof(float) * 6 * L.K;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_item_grads, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  launch(k_item_grads, static_cast<unsigned>(grid), kPoseBlock, smem, s, L, g, cams, w, params ? 1 : 0, partials);
+  if (params) launch(k_gaussian_grads, static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s, L, g, cams,
+                     static_cast<const uint8_t*>(ws), out);
   if (out.pose)
-    launch(k_pose_reduce, L.K, 6 * 32, 0, s, partials, reinterpret_cast<const uint32_t*>(lb + 1), L.K, out.pose,
-           out.overwrite);
+    launch(k_pose_reduce, L.K, 6 * 32, 0, s, static_cast<const float*>(partials), grid, L.K, out.pose, out.overwrite);
   return cudaGetLastError();
 }
 

@@ -54,9 +54,9 @@ cudaError_t launch_raster_bwd(const Layout& L, void* ws, const float* rgb, const
   const unsigned grid = static_cast<unsigned>(L.n_tiles);
   uint8_t* w = static_cast<uint8_t*>(ws);
   const int ch = pick_chunk(L.bwd_chunk, 32, 128, kBwdChunk);
-#define GS_BWD(P, C)                                                                                        \
-  launch(k_raster_bwd<P, C>, grid, kTilePixels / P, 0, s, L, w, rgb, depth, T_final, last, dL_drgb, dL_ddepth, \
-         dL_dT)
+#define GS_BWD(P, C)                                                                                             \
+  launch(k_raster_bwd<P, C>, grid, kTilePixels / P, cap_smem(k_raster_bwd<P, C>, L.raster_bps), s, L, w, rgb, depth, \
+         T_final, last, dL_drgb, dL_ddepth, dL_dT)
 #define GS_BWD_CH(P)                 \
   switch (ch) {                      \
     case 32: GS_BWD(P, 32); break;   \

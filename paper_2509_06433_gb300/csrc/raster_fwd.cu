@@ -307,8 +307,9 @@ cudaError_t launch_raster_fwd_l1_bwd(const Layout& L, void* ws, float* rgb, floa
   const int px = pick_px(L.fwd_px, kDefaultFwdPx);
   const int ch = pick_chunk(L.fwd_chunk, 64, 256, kFwdChunk);
   // the backward phase stages kBwdChunk splats per chunk (the chunk depth changes no result)
-#define GS_FB(P, C)                                                                                          \
-  launch(k_raster_fwd<P, C, false, true, false, kBwdChunk>, grid, kTilePixels / P, 0, s, L, w, rgb, depth, T_final, \
+#define GS_FB(P, C)                                                                                             \
+  launch(k_raster_fwd<P, C, false, true, false, kBwdChunk>, grid, kTilePixels / P,                                 \
+         cap_smem(k_raster_fwd<P, C, false, true, false, kBwdChunk>, L.raster_bps), s, L, w, rgb, depth, T_final, \
          last, ev, cp, F, Occlusion{})
 #define GS_FB_CH(P)                  \
   switch (ch) {                      \
@@ -347,9 +348,9 @@ cudaError_t launch_raster_fwd(const Layout& L, void* ws, float* rgb, float* dept
                   loss->d_loss};
   const int px = pick_px(L.fwd_px, kDefaultFwdPx);
   const int ch = pick_chunk(L.fwd_chunk, 64, 256, kFwdChunk);
-#define GS_FWD(P, C, ST, LO) \
-  launch(k_raster_fwd<P, C, ST, LO>, grid, kTilePixels / P, 0, s, L, w, rgb, depth, T_final, last, ev, cp, F, \
-         Occlusion{})
+#define GS_FWD(P, C, ST, LO)                                                                                  \
+  launch(k_raster_fwd<P, C, ST, LO>, grid, kTilePixels / P, cap_smem(k_raster_fwd<P, C, ST, LO>, L.raster_bps), s, \
+         L, w, rgb, depth, T_final, last, ev, cp, F, Occlusion{})
 #define GS_FWD_CH(P, ST, LO)              \
   switch (ch) {                           \
     case 64: GS_FWD(P, 64, ST, LO); break;   \

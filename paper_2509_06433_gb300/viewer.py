@@ -8,7 +8,10 @@ map.json is ``ipc.SharedMap.descriptor()``. Each frame waits on the map's publis
 renders all viewpoints (one K-view launch per stage) and synchronises, as a viewer that
 presents every frame would. The poses orbit a target point (a stereo pair of eyes 64 mm apart
 per viewpoint pair) unless explicit cameras are given (--cams, a float32 .npy [views, 16]).
-The result file holds the frame rate; --save writes the last frame's RGB as .npy.
+The result file holds the frame rate; --save writes the last frame (rgb, depth, T, last) as
+.npz. With --control, frames are rendered only while that file exists (the viewer idles,
+polling every millisecond, otherwise) and the loop runs until the --stop file appears; the
+frame rate then counts the frames and the time spent while active.
 """
 from __future__ import annotations
 
@@ -65,7 +68,9 @@ def main(argv=None):
     ap.add_argument("--target", type=float, nargs=3, default=(0.0, 0.0, 5.0))
     ap.add_argument("--radius", type=float, default=4.0)
     ap.add_argument("--cams", default=None, help="float32 .npy [views, 16]: fixed cameras instead of the orbit")
-    ap.add_argument("--save", default=None, help=".npy path for the last frame's RGB [views, 3, H, W]")
+    ap.add_argument("--save", default=None, help=".npz path for the last frame (rgb, depth, T, last)")
+    ap.add_argument("--control", default=None, help="render only while this file exists (until --stop)")
+    ap.add_argument("--stop", default=None, help="with --control: end when this file exists")
     a = ap.parse_args(argv)
 
     import torch
@@ -101,18 +106,32 @@ def main(argv=None):
     if a.ready:
         open(a.ready, "w").close()
     frame_ms = []
-    t0 = time.perf_counter()
-    for i in range(a.frames):
-        s = time.perf_counter()
-        frame(i)
-        torch.cuda.current_stream().synchronize()  # a viewer presents every frame
-        frame_ms.append(1e3 * (time.perf_counter() - s))
-    dt = time.perf_counter() - t0
+    i = 0
+    if a.control:  # render while the control file exists, until the stop file appears
+        while not (a.stop and os.path.exists(a.stop)):
+            if not os.path.exists(a.control):
+                time.sleep(1e-3)
+                continue
+            s = time.perf_counter()
+            frame(i)
+            torch.cuda.current_stream().synchronize()  # a viewer presents every frame
+            frame_ms.append(1e3 * (time.perf_counter() - s))
+            i += 1
+        n, dt = len(frame_ms), 1e-3 * sum(frame_ms)
+    else:
+        t0 = time.perf_counter()
+        for i in range(a.frames):
+            s = time.perf_counter()
+            frame(i)
+            torch.cuda.current_stream().synchronize()  # a viewer presents every frame
+            frame_ms.append(1e3 * (time.perf_counter() - s))
+        n, dt = a.frames, time.perf_counter() - t0
     _, err, total, _ = r.status()
     if a.save:
-        np.save(a.save, out["rgb"].cpu().numpy())
-    res = {"fps": a.frames / dt, "frames": a.frames, "seconds": dt, "views": K, "width": W, "height": H,
-           "frame_ms_median": float(np.median(frame_ms)), "frame_ms_p99": float(np.percentile(frame_ms, 99)),
+        np.savez(a.save, **{k: v.cpu().numpy() for k, v in out.items()})
+    res = {"fps": n / dt if dt > 0 else 0.0, "frames": n, "seconds": dt, "views": K, "width": W, "height": H,
+           "frame_ms_median": float(np.median(frame_ms)) if frame_ms else None,
+           "frame_ms_p99": float(np.percentile(frame_ms, 99)) if frame_ms else None,
            "pairs_last_frame": int(total), "device_error_word": int(err), "gaussians": view.N}
     view.close()
     tmp = a.out + ".tmp"

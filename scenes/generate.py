@@ -307,6 +307,7 @@ SCENE_CONFIGS = {
     "window500k": (1003, 500_000, 8, 640, 480, 525.0, "bf16"),
     "aerial2m": (1004, 2_000_000, 16, 1280, 720, 900.0, "f16"),
     "turn_room": (1005, 500_000, 10, 672, 376, 260.0, "f32"),
+    "turn_room_detail": (1006, 1_000_000, 10, 672, 376, 260.0, "f32"),
 }
 
 
@@ -323,6 +324,10 @@ def make_scene(name: str, seed: int | None = None, n: int | None = None, K: int 
     turn_room  : the window500k room with a smooth colour texture; K views (672 x 376) from its
                  middle turning by 90 deg of yaw: the key-frame sequence of a robot's turn,
                  rendered from this map.
+    turn_room_detail : the same turn in a denser room (1M Gaussians, splats 0.6x as wide)
+                 whose texture adds a fine band (6 to 15 cycles per metre, a few pixels per cycle
+                 at the turn's distances) to the smooth one: detail that key-frame insertion at a
+                 4-pixel stride cannot reproduce, so reaching a PSNR takes optimisation.
     """
     dseed, dn, dK, dW, dH, df, _ = SCENE_CONFIGS[name]
     seed = dseed if seed is None else seed
@@ -353,6 +358,13 @@ def make_scene(name: str, seed: int | None = None, n: int | None = None, K: int 
     if name == "turn_room":
         d = _room(rng, n)
         d["rgb"] = _smooth_texture(rng, d["means"])
+        return _to_scene(d, _turn(rng, K, W, H, f), W, H, name)
+    if name == "turn_room_detail":
+        d = _room(rng, n)
+        d["log_scales"] -= np.float32(0.5)  # finer splats than turn_room's
+        d["rgb"] = np.clip(_smooth_texture(rng, d["means"]) + _smooth_texture(rng, d["means"], waves=4, amp=0.05,
+                                                                               cycles=(6.0, 15.0), noise=0.0) - 0.5,
+                           0.0, 1.0)
         return _to_scene(d, _turn(rng, K, W, H, f), W, H, name)
     if name == "aerial2m":
         d = _aerial(rng, n)

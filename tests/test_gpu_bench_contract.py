@@ -27,10 +27,10 @@ def test_bench_line():
     e = d["e2e"]
     assert 0 < e["value"] < d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] > 10_000_000 and e["d2h_bytes_per_step"] > 5_000_000
-    # per step: the projection and the live-item compaction (3), the 11 kernels of gs_bin_sort at
+    # per step: the projection and the live-item compaction (2), the 11 kernels of gs_bin_sort at
     # 16 x 1280x720, the fused forward + backward compositing, and the backward projection (live
-    # Gaussians, zero gradients of unseen ones, the chain rule, the pose reduction)
-    assert d["gpu_launches"] == 20 * (3 + 11 + 1 + 4)
+    # items, per-Gaussian sums and chain rule, the pose reduction)
+    assert d["gpu_launches"] == 20 * (2 + 11 + 1 + 3)
     assert d["roofline"]["kernel"] == "raster_fwd_l1_bwd"
     r = d["roofline"]
     assert r["bound"] in ("alu", "hbm") and r["unit"] in ("TFLOP/s", "GB/s")

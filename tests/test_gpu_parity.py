@@ -319,6 +319,42 @@ def test_pixels_per_thread_variants_agree(name):
     r.cfg.fwd_chunk, r.cfg.bwd_chunk = 0, 0
 
 
+def test_blocks_per_sm_cap_changes_nothing():
+    """A cap on the compositing kernels' resident blocks per SM (padding of their dynamic shared
+    memory) changes occupancy only: images and gradients are bit-identical, for the two-launch
+    and the one-launch forms."""
+    torch, api = torch_mods()
+    s = scene("map100k")
+    r, g, ct, _, _ = gpu_fwd("map100k")
+    gr, gd, gt = (torch.as_tensor(a).cuda() for a in _upstream("map100k", s))
+    rgb_t = torch.as_tensor(random_image(23, (s.K, 3, s.H, s.W), 0.0, 1.0)).cuda()
+    depth_t = torch.as_tensor(random_image(24, (s.K, s.H, s.W), 0.0, 8.0)).cuda()
+
+    def run():
+        out = r.render(g, ct)
+        grads = r.backward(g, ct, out, gr, gd, gt)
+        o = r.new_outputs()
+        g_rgb, g_depth, loss = torch.empty_like(o["rgb"]), torch.empty_like(o["depth"]), torch.zeros(1, device="cuda")
+        api.gs_raster_fwd_l1_bwd(r.cfg, r.ws, o["rgb"], o["depth"], o["T"], o["last"], rgb_t, depth_t, g_rgb, g_depth,
+                                 loss)
+        fused = r.screen_grads()
+        torch.cuda.synchronize()
+        return {**{k: v.clone() for k, v in out.items()}, **{"g_" + k: v for k, v in grads.items()},
+                **{"f_" + k: v for k, v in o.items()}, "f_loss": loss, **{"s_" + k: v for k, v in fused.items()}}
+    try:
+        r.cfg.fwd_px_per_thread = r.cfg.bwd_px_per_thread = 4
+        ref = run()
+        for cap in (8, 4, 2):
+            r.cfg.raster_blocks_per_sm = cap
+            got = run()
+            assert r.status()[0] == 0
+            for k in ref:
+                assert torch.equal(ref[k], got[k]), (cap, k)
+    finally:
+        r.cfg.raster_blocks_per_sm = 0
+        r.cfg.fwd_px_per_thread = r.cfg.bwd_px_per_thread = 0
+
+
 def test_backward_on_deep_lists():
     """Faint Gaussians (opacity 0.005..0.12): no pixel stops, so every tile's list is composited
     to its end, 200 to 1300 splats deep (many staging chunks per tile, transmittance near 0.1 at
@@ -422,11 +458,14 @@ def test_autotuner_picks_a_variant():
     assert (r.cfg.fwd_chunk, r.cfg.bwd_chunk) == res["chunks"]
     assert r.fused_compositing == res["fused"] and set(k[0] for k in res["fused_ms"]) == {1, 2, 4}
     assert res["two_launch_ms"] > 0 and all(v > 0 for v in res["fused_ms"].values())
+    assert res["blocks_per_sm"] in autotune.BLOCKS_PER_SM and r.cfg.raster_blocks_per_sm == res["blocks_per_sm"]
+    assert set(res["blocks_per_sm_ms"]) == set(autotune.BLOCKS_PER_SM)
     if res["fused"]:  # one launch: one pixels-per-thread value for both passes
         assert r.cfg.fwd_px_per_thread == r.cfg.bwd_px_per_thread
     check_images(to_np(r.render(g, ct)), oracle_fwd("fwd10k"))
     r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread = 0, 0
     r.cfg.fwd_chunk, r.cfg.bwd_chunk = 0, 0
+    r.cfg.raster_blocks_per_sm = 0
     del r.fused_compositing
 
 

@@ -47,6 +47,9 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=HEADLINE, choices=["aerial2m", "window500k", "map100k"],
+                    help="the mapping workload of the JSON line (default: the K-keyframe aerial site; the others "
+                         "serve smaller profiler captures)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=150.0,
@@ -77,6 +80,8 @@ def workload_config(name=HEADLINE):
         "map100k": f"{n} Gaussians (50% free in [-2,2]^2x[2,8] m, 50% on 3 planes), {K} view {W}x{H} f={f:g}",
         "aerial2m": f"{n} Gaussians (ground + 40 boxes, 20% large translucent), K={K} key-frames {W}x{H} f={f:g} "
                     f"at 3-10 m altitude, 20 deg down-tilt",
+        "window500k": f"{n} Gaussians (6 room walls + 10% free), K={K} key-frames {W}x{H} f={f:g} on a 0.3 m / "
+                      f"+-10 deg random walk",
     }[name]
     return {"workload": f"{name}: {what}; batched fwd+bwd with L1(RGB)+0.1 L1(depth) against the key-frames "
                         f"(renders of a perturbed copy), gradients of every parameter and pose",
@@ -378,7 +383,8 @@ def run_ours(args, rank, world):
     build()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    head = run_mapping(args, rank, world, HEADLINE, args.steps, args.warmup, clocks=True, extras=not args.no_extra)
+    head = run_mapping(args, rank, world, args.workload, args.steps, args.warmup, clocks=True,
+                       extras=not args.no_extra)
     line = {
         "metric": METRIC,
         "value": head.pop("value"),
@@ -391,11 +397,11 @@ def run_ours(args, rank, world):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": f"synthetic (seeded {HEADLINE} scene, {STORAGE[HEADLINE]} attribute storage; no dataset)",
+        "data": f"synthetic (seeded {args.workload} scene, {STORAGE[args.workload]} attribute storage; no dataset)",
         "config": head.pop("config") | {"parallelism": f"replicas x{world}"},
     }
     line.update(head)
-    if not args.no_extra:
+    if not args.no_extra and args.workload != "map100k":
         # the single-view mapping step (100k Gaussians, one 640x480 view, FP32) for comparison
         line["map100k"] = run_mapping(args, rank, world, "map100k", args.steps, args.warmup, clocks=False,
                                       extras=False)
@@ -1017,7 +1023,7 @@ def main():
             line["view_dependent_colour"] = measure_sh(dev)
             line["viewer_ipc"] = measure_viewer(dev)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = oracle_step_rate(args.cpu_seconds)
+            line["cpu_baseline"] = oracle_step_rate(args.cpu_seconds, args.workload)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Layout L, uint8_t* _
     if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
 }
 
-// Pairs [b * kEmitPairs, (b + 1) * kEmitPairs) of the emission order. The block stages its
-// window of items (pair offsets, row-table ranges, view and Gaussian ids) and, when they fit,
+// Pairs [b * kEmitPairs, (b + 1) * kEmitPairs) of the emission order (window b; the blocks
+// stride over the windows). The block stages its window of items (pair offsets, row-table ranges, view and Gaussian ids) and, when they fit,
 // the window items' row-span entries in shared memory; each pair then finds its item and its
 // row by binary searches in shared memory.
 constexpr int kEmitRows = 1024;  // row-span entries staged per block (else read from the table)
@@ -277,13 +277,16 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
     for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kEmitThreads + threadIdx.x; i < (n + 31) / 32; i += gsize)
       valid[i] = 0;
   }
-  const uint64_t start = static_cast<uint64_t>(blockIdx.x) * kEmitPairs;
-  if (start >= n) return;
+  // the blocks stride over the windows of kEmitPairs pairs that hold emitted pairs
+  const uint64_t n_windows = (n + kEmitPairs - 1) / kEmitPairs;
+  for (uint64_t win_id = blockIdx.x; win_id < n_windows; win_id += gridDim.x) {
+  __syncthreads();  // the previous window's shared staging is no longer read
+  const uint64_t start = win_id * kEmitPairs;
   const uint64_t end = start + kEmitPairs < n ? start + kEmitPairs : n;
   const uint32_t* offsets = at<uint32_t>(ws, L.item_offsets);
-  if (threadIdx.x == 0) {  // the items holding the block's first and last pairs (k_item_offsets)
-    s_lo = at<uint32_t>(ws, L.emit_first)[blockIdx.x];
-    s_hi = at<uint32_t>(ws, L.emit_last)[blockIdx.x];
+  if (threadIdx.x == 0) {  // the items holding the window's first and last pairs (k_item_offsets)
+    s_lo = at<uint32_t>(ws, L.emit_first)[win_id];
+    s_hi = at<uint32_t>(ws, L.emit_last)[win_id];
   }
   __syncthreads();
   const int64_t lo = s_lo;
@@ -377,6 +380,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_pairs(Layout L, uint8_t* 
     keys[j] = (tid << 32) | s_g[a];
     vals[j] = jj;
   }
+  }  // windows
   pdl_trigger();
 }
 
@@ -391,7 +395,10 @@ cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s) {
   launch(k_scan_blocks, 1, kScanThreads, 0, s, L, w);
   launch(k_item_offsets, item_grid, kProjBlock, 0, s, L, w);
   launch(k_tile_scan, static_cast<unsigned>(L.K), kScanThreads, 0, s, L, w);
-  launch(k_emit_pairs, static_cast<unsigned>(L.n_emit_blocks), kEmitThreads, 0, s, L, w);
+  // the emission's blocks stride over the windows of emitted pairs (their number is on the device)
+  const int64_t emit_resident = static_cast<int64_t>(device_sms()) * 8;
+  launch(k_emit_pairs, static_cast<unsigned>(L.n_emit_blocks < emit_resident ? L.n_emit_blocks : emit_resident),
+         kEmitThreads, 0, s, L, w);
   return cudaGetLastError();
 }
 

@@ -104,7 +104,7 @@ bool make_layout(const gs_config_t* cfg, Layout* L) {
   L->hist = take(kMaxSortPasses * 256 * 4);
   L->sort_status = take(static_cast<size_t>(L->passes) * L->max_sort_tiles * 256 * 4);
   L->pair_grads = take(cap * kPairGradStride * 4);
-  L->pose_partials = take(static_cast<size_t>(kMaxPoseBlocks) * L->K * 6 * 4);
+  L->pose_partials = take((static_cast<size_t>(L->n_item_chunks) + L->K) * 6 * 4);
   L->loss_partials = take(static_cast<size_t>(L->n_loss_blocks) * 4);
   L->item_keys[0] = take(KN * 4);
   L->item_keys[1] = take(KN * 4);

@@ -395,8 +395,10 @@ cudaError_t launch_bin(const Layout& L, void* ws, cudaStream_t s) {
   launch(k_scan_blocks, 1, kScanThreads, 0, s, L, w);
   launch(k_item_offsets, item_grid, kProjBlock, 0, s, L, w);
   launch(k_tile_scan, static_cast<unsigned>(L.K), kScanThreads, 0, s, L, w);
-  // the emission's blocks stride over the windows of emitted pairs (their number is on the device)
-  const int64_t emit_resident = static_cast<int64_t>(device_sms()) * 8;
+  // the emission's blocks stride over the windows of emitted pairs (their number is on the device);
+  // enough blocks that a typical count takes one window per block (a block looping over several
+  // windows serialises their latency-bound searches), few enough that surplus blocks cost little
+  const int64_t emit_resident = static_cast<int64_t>(device_sms()) * 128;
   launch(k_emit_pairs, static_cast<unsigned>(L.n_emit_blocks < emit_resident ? L.n_emit_blocks : emit_resident),
          kEmitThreads, 0, s, L, w);
   return cudaGetLastError();

@@ -25,7 +25,6 @@ constexpr int kSortTileKeys = kSortThreads * kSortItems;
 constexpr int kMaxSortPasses = 8;
 constexpr int kPairGradStride = 12;   // floats per pair gradient record (10 used)
 constexpr int kPoseBlock = 256;       // Gaussians / live items per projection-backward block
-constexpr int kMaxPoseBlocks = 8 * 1024;  // bound on the blocks of the item-parallel backward (8 per SM)
 constexpr uint32_t kSpinLimit = 1u << 21;  // bounded decoupled look-back (about a second of polling)
 constexpr int kDefaultFwdPx = 2;      // pixels per thread of the compositing kernels when
 constexpr int kDefaultBwdPx = 2;      // gs_config_t leaves the choice to the library
@@ -43,6 +42,7 @@ struct Status {
   uint32_t n_live;          // live items: (view, Gaussian) items that emit at least one pair
   uint32_t view_ctr;        // tile-scan blocks started (one per view)
   uint32_t proj_done;       // projection blocks finished (the last one scans their live counts)
+  uint32_t grad_chunk_ctr;  // chunks of live items taken by the backward projection's blocks
 };
 static_assert(sizeof(Status) <= 256, "status block");
 

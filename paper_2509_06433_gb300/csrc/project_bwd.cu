@@ -114,8 +114,7 @@ __device__ __forceinline__ Sum10 sum_pairs_warp(const float* __restrict__ pg, co
 
 // Blocks of k_item_grads: up to eight per multiprocessor, no more than there are chunks.
 int64_t item_grad_blocks(const Layout& L) {
-  int64_t resident = static_cast<int64_t>(device_sms()) * 8;
-  if (resident > kMaxPoseBlocks) resident = kMaxPoseBlocks;
+  const int64_t resident = static_cast<int64_t>(device_sms()) * 8;
   return L.n_item_chunks < resident ? L.n_item_chunks : resident;
 }
 
@@ -128,10 +127,10 @@ constexpr int kPartial = 16;
 // compact order of the live items (increasing k N + g): sums the item's pair records in slot
 // order (warp-cooperatively for items with many pairs), applies the chain rule of the view's
 // projection, writes the item's partial (when parameter gradients are wanted) and sums the
-// items' pose gradients per view: a chunk's items are in view order, so each view present in a
-// chunk gets the chunk's sum, added in chunk order to the block's per-view sums in shared
-// memory, which go to pose_partials[block][view] at the end. The blocks stride over the chunks
-// of kPoseBlock live items (the grid does not depend on the data, so the order is fixed).
+// items' pose gradients per view. Blocks take chunks of kPoseBlock live items from a counter
+// (balanced whatever the chunks' work); a chunk's items are in view order, so each view k present
+// in chunk c gets the chunk's sum in slot c + k of pose_partials (unique: a later chunk's first
+// view is at least this chunk's last), which k_pose_reduce sums over the view's chunks in order.
 __global__ void __launch_bounds__(kPoseBlock) k_item_grads(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                           uint8_t* __restrict__ ws, int want_params,
                                                           float* __restrict__ pose_partials) {
@@ -145,11 +144,16 @@ __global__ void __launch_bounds__(kPoseBlock) k_item_grads(Layout L, GaussPtrs G
   const float* pg = at<float>(ws, L.pair_grads);
   const uint32_t* pvalid = at<uint32_t>(ws, L.pair_valid);
   float4* partials = at<float4>(ws, L.item_partials);
-  extern __shared__ float s_pose[];  // [K][6]: the block's pose sums per view
   __shared__ float s_red[kPoseBlock / 32][6];
   __shared__ int s_k0, s_k1;
-  for (int i = threadIdx.x; i < 6 * L.K; i += kPoseBlock) s_pose[i] = 0.0f;
-  for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+  __shared__ int64_t s_chunk;
+  uint32_t* ctr = &at<Status>(ws, L.status)->grad_chunk_ctr;
+  for (;;) {
+    __syncthreads();  // the previous chunk's s_k0 / s_k1 / s_chunk are read
+    if (threadIdx.x == 0) s_chunk = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const int64_t c = s_chunk;
+    if (c >= chunks) break;
     const int64_t pos = c * kPoseBlock + threadIdx.x;
     const bool valid = pos < n_live;
     uint32_t kg = 0, off = 0, cnt = 0;
@@ -333,14 +337,11 @@ __global__ void __launch_bounds__(kPoseBlock) k_item_grads(Layout L, GaussPtrs G
       if (threadIdx.x < 6) {
         float v = 0.0f;
         for (int wv = 0; wv < kPoseBlock / 32; ++wv) v += s_red[wv][threadIdx.x];
-        s_pose[6 * kk + threadIdx.x] += v;
+        pose_partials[(c + kk) * 6 + threadIdx.x] = v;
       }
       __syncthreads();
     }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 6 * L.K; i += kPoseBlock)
-    pose_partials[static_cast<int64_t>(blockIdx.x) * 6 * L.K + i] = s_pose[i];
   pdl_trigger();
 }
 
@@ -463,13 +464,25 @@ __global__ void __launch_bounds__(kPoseBlock) k_gaussian_grads(Layout L, GaussPt
     for (int j = 0; j < 3; ++j) put(out.rgb + 3 * g + j, store, acc[13 + j]);
 }
 
-__global__ void k_pose_reduce(const float* __restrict__ partials, int64_t n_blocks, int K, float* __restrict__ pose,
-                              int overwrite) {
+// pose[k][i] += (or, with overwrite, =) the sum over the chunks holding view k's live items of
+// their slot c + k of pose_partials, in chunk order.
+__global__ void k_pose_reduce(const float* __restrict__ partials, Layout L, const uint8_t* __restrict__ ws,
+                              float* __restrict__ pose, int overwrite) {
   pdl_begin();
-  const int k = blockIdx.x;
+  const int k = blockIdx.x, K = L.K;
   const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t* mask = at<uint32_t>(ws, L.live_mask);
+  const uint32_t* wpre = at<uint32_t>(ws, L.live_wpre);
+  const int64_t n_live = at<Status>(ws, L.status)->n_live;
+  // the view's live items are positions [r0, r1) among the live items
+  auto rank = [&](int64_t item) -> int64_t {
+    if (item >= L.KN) return n_live;
+    return wpre[item >> 5] + __popc(mask[item >> 5] & ((1u << (item & 31)) - 1u));
+  };
+  const int64_t r0 = rank(static_cast<int64_t>(k) * L.N), r1 = rank(static_cast<int64_t>(k + 1) * L.N);
   float v = 0.0f;
-  for (int64_t b = lane; b < n_blocks; b += 32) v += partials[(b * K + k) * 6 + i];
+  if (r1 > r0)
+    for (int64_t c = r0 / kPoseBlock + lane; c <= (r1 - 1) / kPoseBlock; c += 32) v += partials[(c + k) * 6 + i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane == 0) pose[k * 6 + i] = overwrite ? v : pose[k * 6 + i] + v;
@@ -531,15 +544,14 @@ cudaError_t launch_project_bwd(const Layout& L, const GaussPtrs& g, const gs_cam
   auto* w = static_cast<uint8_t*>(ws);
   float* partials = at<float>(ws, L.pose_partials);
   const bool params = out.means || out.log_scales || out.quats || out.opacity_logits || out.rgb;
-  const int64_t grid = item_grad_blocks(L);
-  const size_t smem = sizeof(float) * 6 * L.K;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_item_grads, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  launch(k_item_grads, static_cast<unsigned>(grid), kPoseBlock, smem, s, L, g, cams, w, params ? 1 : 0, partials);
+  cudaMemsetAsync(&at<Status>(ws, L.status)->grad_chunk_ctr, 0, sizeof(uint32_t), s);
+  launch(k_item_grads, static_cast<unsigned>(item_grad_blocks(L)), kPoseBlock, 0, s, L, g, cams, w, params ? 1 : 0,
+         partials);
   if (params) launch(k_gaussian_grads, static_cast<unsigned>(L.n_pose_blocks), kPoseBlock, 0, s, L, g, cams,
                      static_cast<const uint8_t*>(ws), out);
   if (out.pose)
-    launch(k_pose_reduce, L.K, 6 * 32, 0, s, static_cast<const float*>(partials), grid, L.K, out.pose, out.overwrite);
+    launch(k_pose_reduce, L.K, 6 * 32, 0, s, static_cast<const float*>(partials), L, static_cast<const uint8_t*>(ws),
+           out.pose, out.overwrite);
   return cudaGetLastError();
 }
 

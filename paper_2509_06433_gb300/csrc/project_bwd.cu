@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(kPoseBlock) k_gaussian_grads(Layout L, GaussPt
 __global__ void k_pose_reduce(const float* __restrict__ partials, Layout L, const uint8_t* __restrict__ ws,
                               float* __restrict__ pose, int overwrite) {
   pdl_begin();
-  const int k = blockIdx.x, K = L.K;
+  const int k = blockIdx.x;
   const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t* mask = at<uint32_t>(ws, L.live_mask);
   const uint32_t* wpre = at<uint32_t>(ws, L.live_wpre);

@@ -6,7 +6,7 @@ namespace gs {
 namespace {
 
 template <int PX, int CH>
-__global__ void __launch_bounds__(kTilePixels / PX) k_raster_bwd(Layout L, uint8_t* __restrict__ ws,
+__global__ void __launch_bounds__(kTilePixels / PX, PX == 4 ? kMinBlocksPx4 : 1) k_raster_bwd(Layout L, uint8_t* __restrict__ ws,
                                                                  const float* __restrict__ rgb,
                                                                  const float* __restrict__ depth,
                                                                  const float* __restrict__ T_final,

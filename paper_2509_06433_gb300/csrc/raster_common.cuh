@@ -4,9 +4,11 @@
 // column (PX = 1, 2 or 4, chosen per workload), so the horizontal offset to a splat is
 // shared and every splat record loaded from shared memory serves PX pixels. The per-pixel
 // update is branch-free (a masked blend with weight 0 leaves every accumulator bit for bit
-// unchanged), so the PX pixel chains interleave. The tile's depth-sorted list is walked in
-// chunks staged in shared memory as three float4 and a row mask per splat (coalesced loads
-// of the sorted keys, whose low word is the Gaussian id, one gather of the projected record each).
+// unchanged), so the PX pixel chains interleave, and pairs of them share packed FP32
+// instructions (add / multiply / FMA on two pixels at once). The tile's depth-sorted list is
+// walked in chunks staged in shared memory as five float4 of duplicated operands, the opacity
+// and a row mask per splat (coalesced loads of the sorted keys, whose low word is the Gaussian
+// id, one gather of the projected record each).
 //
 // Both kernels evaluate a splat's opacity with the same inline function on the same
 // operands, so the backward pass takes exactly the forward pass's skip and stop decisions
@@ -31,6 +33,10 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
+// Resident blocks per SM the compiler must fit at 4 pixels per thread (64 threads): a register
+// budget of 80 per thread, without spills. The packed pixel pairs leave the compositing loops
+// bound by instruction latency as much as by issue, and 12 blocks hide more of it than 10.
+constexpr int kMinBlocksPx4 = 12;
 constexpr int kFwdChunk = 128;  // splats staged per forward chunk (default; 64 and 256 also built)
 constexpr int kBwdChunk = 64;   // splats staged per backward chunk (default; 32 and 128 also built)
 
@@ -40,14 +46,65 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Staged splat: A = (x, y, qa, qb), B = (qc, opacity, depth, log2 opacity), C = (r, g, b, -) where
-// (x, y) is the 2D mean relative to the tile origin and power * log2(e) = qa dx^2 + qb dx dy + qc dy^2.
-// rows: bit r is set when the splat's ellipse {opacity * 2^power >= 1/255}, widened by a safety
-// margin, meets the pixel-centre row y = r + 0.5 of the tile within the columns [0.5, 15.5].
-// A warp none of whose rows is set skips the splat without changing any decision.
+// Packed FP32 (sm_100 family): one instruction applies an add, a multiply or a fused
+// multiply-add to two pixels' operands, each component rounded exactly as the scalar
+// __fadd_rn / __fmul_rn / __fmaf_rn would round it. A thread's PX pixels are processed in
+// groups of W = 2 (PX = 2, 4) or W = 1 (PX = 1) components, so every variant still takes
+// bit-identical decisions; the per-splat operands are staged in duplicated pairs so that they
+// feed the packed instructions straight from shared memory.
+template <int W>
+struct Vec;
+template <>
+struct Vec<1> {
+  using T = float;
+};
+template <>
+struct Vec<2> {
+  using T = float2;
+};
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float comp(float v, int) { return v; }
+__device__ __forceinline__ float comp(float2 v, int i) { return i ? v.y : v.x; }
+__device__ __forceinline__ void set_comp(float& v, int, float x) { v = x; }
+__device__ __forceinline__ void set_comp(float2& v, int i, float x) {
+  if (i) v.y = x;
+  else v.x = x;
+}
+__device__ __forceinline__ float hsum(float v) { return v; }
+__device__ __forceinline__ float hsum(float2 v) { return v.x + v.y; }
+template <int W>
+__device__ __forceinline__ typename Vec<W>::T bcast(float x) {
+  if constexpr (W == 1) return x;
+  else return make_float2(x, x);
+}
+// first / second pair of a staged float4 (x, x, y, y): (x, x) / (y, y), or x / y for W = 1
+template <int W>
+__device__ __forceinline__ typename Vec<W>::T first(const float4& v) {
+  if constexpr (W == 1) return v.x;
+  else return make_float2(v.x, v.y);
+}
+template <int W>
+__device__ __forceinline__ typename Vec<W>::T second(const float4& v) {
+  if constexpr (W == 1) return v.z;
+  else return make_float2(v.z, v.w);
+}
+
+// Staged splat, every per-splat operand duplicated into a pair: XY = (x, x, y, y) with (x, y)
+// the 2D mean relative to the tile origin; QAB = (qa, qa, qb, qb), QCL = (qc, qc, log2 o,
+// log2 o) with power * log2(e) = qa dx^2 + qb dx dy + qc dy^2; RG = (r, r, g, g), BZ = (b, b,
+// depth, depth); op = opacity. rows: bit r is set when the splat's ellipse {opacity * 2^power
+// >= 1/255}, widened by a safety margin, meets the pixel-centre row y = r + 0.5 of the tile
+// within the columns [0.5, 15.5]. A warp none of whose rows is set skips the splat without
+// changing any decision.
 template <int CH>
 struct Stage {
-  float4 A[CH], B[CH], C[CH];
+  float4 XY[CH], QAB[CH], QCL[CH], RG[CH], BZ[CH];
+  float op[CH];
   uint32_t rows[CH];
 };
 
@@ -99,40 +156,48 @@ __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layou
   const float4 co = at<float4>(ws, L.color_opacity)[k * L.color_stride + gid];
   const float x = __fadd_rn(__fsub_rn(uv.x, ox), uv.y), y = __fadd_rn(__fsub_rn(uv.z, oy), uv.w);
   const float qa = __fmul_rn(cn.x, -0.5f * kLog2e), qb = __fmul_rn(cn.y, -kLog2e), qc = __fmul_rn(cn.z, -0.5f * kLog2e);
-  S.A[j] = make_float4(x, y, qa, qb);
-  S.B[j] = make_float4(qc, co.w, cn.w, __log2f(co.w));
-  S.C[j] = make_float4(co.x, co.y, co.z, 0.0f);
+  const float lo = __log2f(co.w);
+  S.XY[j] = make_float4(x, x, y, y);
+  S.QAB[j] = make_float4(qa, qa, qb, qb);
+  S.QCL[j] = make_float4(qc, qc, lo, lo);
+  S.RG[j] = make_float4(co.x, co.x, co.y, co.y);
+  S.BZ[j] = make_float4(co.z, co.z, cn.w, cn.w);
+  S.op[j] = co.w;
   S.rows[j] = splat_rows(x, y, -qa, -qb, -qc, co.w);
   return gid;
 }
 
 // Opacity of a splat at a pixel, in one form shared by every compositing kernel, so that they
-// all take the same decisions. For the pixel column at offset dx from the splat's mean, a lane
-// forms once per splat (splat_column)
+// all take the same decisions. For the pixel column at offset dx = x - (column + 0.5) from the
+// splat's mean, a lane forms once per splat (splat_column)
 //   c1 = qb dx,   c0 = qa dx^2 + log2(opacity),
 // and per pixel row at offset dy the exponent  e = (qc dy + c1) dy + c0 = power log2(e) + log2(o),
-// so raw = 2^e = opacity * exp(power) costs two FMAs and one ex2. keep: the splat is not skipped
-// (power <= 0, i.e. e <= log2(o), and alpha >= 1/255); raw is the opacity before the 0.99 clamp.
+// so raw = 2^e = opacity * exp(power) costs two FMAs and one ex2. The splat is kept at the pixel
+// (not skipped) when power <= 0, i.e. e <= log2(o), and alpha = min(raw, 0.99) >= 1/255.
+// The offsets are formed as additions of the negated pixel centre (exact small integers + 0.5),
+// which round exactly as the subtractions would.
+template <int W>
 struct Column {
-  float c0, c1;
+  typename Vec<W>::T dx, c1, c0;
 };
-__device__ __forceinline__ Column splat_column(const float4& A, const float4& B, float dx) {
-  return {__fmaf_rn(__fmul_rn(A.z, dx), dx, B.w), __fmul_rn(A.w, dx)};
+template <int W>
+__device__ __forceinline__ Column<W> splat_column(const float4& XY, const float4& QAB, const float4& QCL,
+                                                  typename Vec<W>::T npx) {
+  Column<W> c;
+  c.dx = vadd(first<W>(XY), npx);
+  c.c1 = vmul(second<W>(QAB), c.dx);
+  c.c0 = vfma(vmul(first<W>(QAB), c.dx), c.dx, second<W>(QCL));
+  return c;
 }
-__device__ __forceinline__ float splat_exponent(const float4& B, Column c, float dy) {
-  return __fmaf_rn(__fmaf_rn(B.x, dy, c.c1), dy, c.c0);
+template <int W>
+__device__ __forceinline__ typename Vec<W>::T splat_exponent(const float4& QCL, const Column<W>& c,
+                                                             typename Vec<W>::T dy) {
+  return vfma(vfma(first<W>(QCL), dy, c.c1), dy, c.c0);
 }
-struct Alpha {
-  float alpha, raw;
-  bool keep;
-};
-__device__ __forceinline__ Alpha splat_alpha(const float4& B, Column c, float dy) {
-  Alpha r;
-  const float e = splat_exponent(B, c, dy);
-  r.raw = ex2_approx(e);
-  r.alpha = fminf(r.raw, kAlphaMax);
-  r.keep = (e <= B.w) && (r.alpha >= kAlphaMin);
-  return r;
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 struct TileCoord {

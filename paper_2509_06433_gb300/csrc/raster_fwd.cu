@@ -49,8 +49,27 @@ struct Occlusion {
 template <int CHB>
 using RasterWs = typename std::conditional<(CHB > 0), uint8_t*, const uint8_t*>::type;
 
+// Shared memory of the forward: its staged chunk; with the fused backward, the backward sweep's
+// shared memory in the same bytes (the forward's chunks are dead once every thread has passed
+// the loss reduction's barriers, before the sweep starts).
+template <int PX, int CH, int CHB>
+union FusedSmem {
+  Stage<CH> S;
+  BwdSmem<PX, CHB> M;
+};
+template <int PX, int CH, int CHB>
+struct FwdSmemOf {
+  using T = FusedSmem<PX, CH, CHB>;
+};
+template <int PX, int CH>
+struct FwdSmemOf<PX, CH, 0> {
+  struct T {
+    Stage<CH> S;
+  };
+};
+
 template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false, int CHB = 0>
-__global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws,
+__global__ void __launch_bounds__(kTilePixels / PX, PX == 4 ? kMinBlocksPx4 : 1) k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws,
                                                                  float* __restrict__ out_rgb,
                                                                  float* __restrict__ out_depth,
                                                                  float* __restrict__ out_T,
@@ -63,7 +82,8 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, Raste
   constexpr int kThreads = kTilePixels / PX;
   constexpr int kWarps = kThreads / 32;
   const float kInf = __int_as_float(0x7f800000);
-  __shared__ Stage<CH> S;
+  __shared__ typename FwdSmemOf<PX, CH, CHB>::T sm;
+  Stage<CH>& S = sm.S;
   __shared__ uint32_t s_red[2][kWarps];
   const TileCoord tc = tile_coord(L, blockIdx.x);
   const int lx = threadIdx.x & (kTile - 1), ly = (threadIdx.x / kTile) * PX;
@@ -74,15 +94,24 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, Raste
   const float pxc = static_cast<float>(lx) + 0.5f, pyc = static_cast<float>(ly) + 0.5f;
   // this warp's pixel rows: (2 * warp) * PX .. (2 * warp + 2) * PX - 1
   const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
-  float T[PX], cr[PX], cg[PX], cb[PX], cd[PX], amin[PX];
+  constexpr int W = PX >= 2 ? 2 : 1, G = PX / W;  // pixel q is component q % W of group q / W
+  using V = typename Vec<W>::T;
+  V T[G], cr[G], cg[G], cb[G], cd[G], npy[G];
+  float amin[PX];
   int32_t last[PX], stop_at[PX];
   float zmax[PX];
   uint32_t blended = 0;
   bool all_done = true;
+  const V npx = bcast<W>(-pxc), one = bcast<W>(1.0f), zero = bcast<W>(0.0f), minus1 = bcast<W>(-1.0f);
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    T[g] = one;
+    cr[g] = cg[g] = cb[g] = cd[g] = zero;
+#pragma unroll
+    for (int i = 0; i < W; ++i) set_comp(npy[g], i, -(pyc + static_cast<float>(g * W + i)));
+  }
 #pragma unroll
   for (int q = 0; q < PX; ++q) {
-    T[q] = 1.0f;
-    cr[q] = cg[q] = cb[q] = cd[q] = 0.0f;
     last[q] = 0;
     stop_at[q] = -1;
     const bool outside = !(px < L.W && py + q < L.H);
@@ -125,39 +154,49 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, Raste
         if (__all_sync(0xffffffffu, all_done)) break;
       }
       if (!(S.rows[j] & wrows)) continue;
-      const float4 A = S.A[j], B = S.B[j], C = S.C[j];
-      const float dx = __fsub_rn(A.x, pxc);
-      const Column col = splat_column(A, B, dx);
+      const float4 XY = S.XY[j], QAB = S.QAB[j], QCL = S.QCL[j], RG = S.RG[j], BZ = S.BZ[j];
+      const Column<W> col = splat_column<W>(XY, QAB, QCL, npx);
+      const V cR = first<W>(RG), cG = second<W>(RG), cB = first<W>(BZ), cZ = second<W>(BZ);
       const int pos = pos0 + j;
 #pragma unroll
-      for (int q = 0; q < PX; ++q) {
-        // pixel-centre offsets are formed the same way whatever PX is, so every variant
-        // takes bit-identical decisions
-        const float dy = __fsub_rn(A.y, pyc + static_cast<float>(q));
-        const float e = splat_exponent(B, col, dy);
-        const float alpha = fminf(ex2_approx(e), kAlphaMax);
-        bool keep = (e <= B.w) && (alpha >= amin[q]);
-        bool behind = false;
-        if (OCC) {
-          behind = B.z >= zmax[q];  // B.z: the splat's camera depth
-          keep = keep && !behind;
+      for (int g = 0; g < G; ++g) {
+        const V e = splat_exponent<W>(QCL, col, vadd(second<W>(XY), npy[g]));
+        const V nT = vmul(T[g], minus1);
+        V alpha;
+        bool keep[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+          const int q = g * W + i;
+          const float a = fminf(ex2_approx(comp(e, i)), kAlphaMax);
+          set_comp(alpha, i, a);
+          keep[i] = (comp(e, i) <= QCL.z) && (a >= amin[q]);
         }
-        const float Tn = __fmaf_rn(-T[q], alpha, T[q]);
-        const bool stop = keep && (Tn < kTStop);
-        const bool blend = keep && !stop;
-        const float ae = blend ? alpha : 0.0f;
-        const float w = __fmul_rn(ae, T[q]);
-        cr[q] = __fmaf_rn(C.x, w, cr[q]);
-        cg[q] = __fmaf_rn(C.y, w, cg[q]);
-        cb[q] = __fmaf_rn(C.z, w, cb[q]);
-        cd[q] = __fmaf_rn(B.z, w, cd[q]);
-        T[q] = __fmaf_rn(-T[q], ae, T[q]);
-        last[q] = blend ? pos + 1 : last[q];
-        amin[q] = (stop || behind) ? kInf : amin[q];
-        if (STATS) {
-          stop_at[q] = stop ? pos : stop_at[q];
-          blended += blend ? 1u : 0u;
+        const V Tn = vfma(nT, alpha, T[g]);  // T (1 - alpha)
+        V ae;  // alpha for a blended splat, else 0 (then w = 0 and T, the sums stay bit for bit)
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+          const int q = g * W + i;
+          bool kp = keep[i], behind = false;
+          if (OCC) {
+            behind = BZ.z >= zmax[q];  // the splat's camera depth at or behind the surface
+            kp = kp && !behind;
+          }
+          const bool stop = kp && (comp(Tn, i) < kTStop);
+          const bool blend = kp && !stop;
+          set_comp(ae, i, blend ? comp(alpha, i) : 0.0f);
+          last[q] = blend ? pos + 1 : last[q];
+          amin[q] = (stop || behind) ? kInf : amin[q];
+          if (STATS) {
+            stop_at[q] = stop ? pos : stop_at[q];
+            blended += blend ? 1u : 0u;
+          }
         }
+        const V w = vmul(ae, T[g]);
+        cr[g] = vfma(cR, w, cr[g]);
+        cg[g] = vfma(cG, w, cg[g]);
+        cb[g] = vfma(cB, w, cb[g]);
+        cd[g] = vfma(cZ, w, cd[g]);
+        T[g] = vfma(nT, ae, T[g]);
       }
     }
   }
@@ -174,29 +213,32 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, Raste
 #pragma unroll
   for (int q = 0; q < PX; ++q) {
     const int y = py + q;
+    float vr = comp(cr[q / W], q % W), vg = comp(cg[q / W], q % W), vb = comp(cb[q / W], q % W);
+    float vd = comp(cd[q / W], q % W);
+    const float vT = comp(T[q / W], q % W);
     if (px < L.W && y < L.H) {
       if (STATS) evals += static_cast<uint32_t>(stop_at[q] >= 0 ? stop_at[q] + 1 : len);
       const int64_t pix = static_cast<int64_t>(y) * L.W + px;
       const int64_t c0 = static_cast<int64_t>(tc.k) * 3 * HW + pix;
       if (OCC) {  // the external surface through the remaining transmittance
         if (O.rgb) {
-          cr[q] = __fmaf_rn(T[q], O.rgb[c0], cr[q]);
-          cg[q] = __fmaf_rn(T[q], O.rgb[c0 + HW], cg[q]);
-          cb[q] = __fmaf_rn(T[q], O.rgb[c0 + 2 * HW], cb[q]);
+          vr = __fmaf_rn(vT, O.rgb[c0], vr);
+          vg = __fmaf_rn(vT, O.rgb[c0 + HW], vg);
+          vb = __fmaf_rn(vT, O.rgb[c0 + 2 * HW], vb);
         }
-        cd[q] = __fmaf_rn(T[q], zmax[q], cd[q]);
+        vd = __fmaf_rn(vT, zmax[q], vd);
       }
       if (out_rgb) {
-        out_rgb[c0] = cr[q];
-        out_rgb[c0 + HW] = cg[q];
-        out_rgb[c0 + 2 * HW] = cb[q];
+        out_rgb[c0] = vr;
+        out_rgb[c0 + HW] = vg;
+        out_rgb[c0 + 2 * HW] = vb;
       }
-      if (out_depth) out_depth[tc.k * HW + pix] = cd[q];
-      if (out_T) out_T[tc.k * HW + pix] = T[q];
+      if (out_depth) out_depth[tc.k * HW + pix] = vd;
+      if (out_T) out_T[tc.k * HW + pix] = vT;
       if (out_last) out_last[tc.k * HW + pix] = last[q];
       if (LOSS) {
         // L = sum_k [ mean_{3HW} |R - R*| + lambda mean_{HW} |D - D*| ], sign(0) = 0
-        const float c[3] = {cr[q], cg[q], cb[q]};
+        const float c[3] = {vr, vg, vb};
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
           const float d = c[ch] - tgt[LOSS ? q : 0][ch];
@@ -205,7 +247,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, Raste
           F.g_rgb[c0 + ch * HW] = gv;
           if (CHB > 0) bg[CHB > 0 ? q : 0][ch] = gv;
         }
-        const float d = cd[q] - tgt[LOSS ? q : 0][3];
+        const float d = vd - tgt[LOSS ? q : 0][3];
         loss += fabsf(d) * invd;
         const float gv = sgn(d) * invd;
         F.g_depth[tc.k * HW + pix] = gv;
@@ -249,7 +291,7 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, Raste
   if constexpr (CHB > 0) {
     // the backward pass of this tile, from registers: the weighted colour behind the first
     // splat is the loss gradient applied to the pixel's output (no dL/dT_final term)
-    __shared__ BwdSmem<PX, CHB> M;
+    BwdSmem<PX, CHB>& M = sm.M;
     float Sg[PX], hT[PX], gr[PX], gg[PX], gb[PX], gd[PX];
     int lst[PX];
 #pragma unroll
@@ -259,11 +301,13 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_raster_fwd(Layout L, Raste
       gb[q] = bg[q][2];
       gd[q] = bg[q][3];
       const bool in = px < L.W && py + q < L.H;
-      Sg[q] = in ? weighted_colour(gr[q], gg[q], gb[q], gd[q], cr[q], cg[q], cb[q], cd[q]) : 0.0f;
+      Sg[q] = in ? weighted_colour(gr[q], gg[q], gb[q], gd[q], comp(cr[q / W], q % W), comp(cg[q / W], q % W),
+                                   comp(cb[q / W], q % W), comp(cd[q / W], q % W))
+                 : 0.0f;
       hT[q] = 0.0f;
       lst[q] = in ? last[q] : 0;
     }
-    bwd_sweep<PX, CHB>(M, L, ws, tc, rg, Sg, hT, gr, gg, gb, gd, lst);
+    bwd_sweep<PX, CHB, false>(M, L, ws, tc, rg, Sg, hT, gr, gg, gb, gd, lst);
     pdl_trigger();
   }
   if (STATS) {

@@ -92,9 +92,11 @@ __device__ __forceinline__ float weighted_colour(float gr, float gg, float gb, f
 // upstream gradients and `last` (0 for pixels outside the image). The sweep walks the tile's
 // list front to back up to the largest `last` of its pixels, recomputing T from 1, and writes
 // one record per pair in front of some pixel's last contributor. All threads of the block call it.
-template <int PX, int CH>
+// HT = false: every hT is zero (no dL/dT_final term) and the sweep leaves it out; the results are
+// the same bit for bit (a zero addend changes at most the sign of a zero, which the sums drop).
+template <int PX, int CH, bool HT = true>
 __device__ __forceinline__ void bwd_sweep(BwdSmem<PX, CH>& M, const Layout& L, uint8_t* __restrict__ ws,
-                                          const TileCoord& tc, uint2 rg, float (&Sg)[PX], const float (&hT)[PX],
+                                          const TileCoord& tc, uint2 rg, const float (&Sg)[PX], const float (&hT)[PX],
                                           const float (&gr)[PX], const float (&gg)[PX], const float (&gb)[PX],
                                           const float (&gd)[PX], const int (&last)[PX]) {
   constexpr int kThreads = kTilePixels / PX;
@@ -108,12 +110,26 @@ __device__ __forceinline__ void bwd_sweep(BwdSmem<PX, CH>& M, const Layout& L, u
   const uint32_t wrows = ((1u << (2 * PX)) - 1u) << ((threadIdx.x >> 5) * 2 * PX);
   float* pair_grads = at<float>(ws, L.pair_grads);
   uint32_t* pair_valid = at<uint32_t>(ws, L.pair_valid);
-  float T[PX];
+  constexpr int W = PX >= 2 ? 2 : 1, G = PX / W;  // pixel q is component q % W of group q / W
+  using V = typename Vec<W>::T;
+  const V npx = bcast<W>(-pxc), zero = bcast<W>(0.0f), minus1 = bcast<W>(-1.0f);
+  V T[G], npy[G], Sgv[G], hTv[G], grv[G], ggv[G], gbv[G], gdv[G];
   int wl = 0;
 #pragma unroll
-  for (int q = 0; q < PX; ++q) {
-    T[q] = 1.0f;
-    wl = max(wl, last[q]);
+  for (int g = 0; g < G; ++g) {
+    T[g] = bcast<W>(1.0f);
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const int q = g * W + i;
+      set_comp(npy[g], i, -(pyc + static_cast<float>(q)));
+      set_comp(Sgv[g], i, Sg[q]);
+      set_comp(hTv[g], i, hT[q]);
+      set_comp(grv[g], i, gr[q]);
+      set_comp(ggv[g], i, gg[q]);
+      set_comp(gbv[g], i, gb[q]);
+      set_comp(gdv[g], i, gd[q]);
+      wl = max(wl, last[q]);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
@@ -143,51 +159,68 @@ __device__ __forceinline__ void bwd_sweep(BwdSmem<PX, CH>& M, const Layout& L, u
     const int nw = min(n, warp_last - pos0);  // splats of this chunk this warp must visit
     for (int j = 0; j < nw; ++j) {
       if (!(M.S.rows[j] & wrows)) continue;
-      const float4 A = M.S.A[j], B = M.S.B[j];
-      const float dx = __fsub_rn(A.x, pxc);
-      const Column col = splat_column(A, B, dx);
+      const float4 XY = M.S.XY[j], QAB = M.S.QAB[j], QCL = M.S.QCL[j];
+      const Column<W> col = splat_column<W>(XY, QAB, QCL, npx);
       const int pos = pos0 + j;
       // phase 1: opacity and keep/skip decision for the thread's pixels
-      Alpha a[PX];
-      float dy[PX];
+      V dy[G], alpha[G];
+      float raw[PX];
       bool okq[PX];
       bool contrib = false;
 #pragma unroll
-      for (int q = 0; q < PX; ++q) {
-        dy[q] = __fsub_rn(A.y, pyc + static_cast<float>(q));
-        a[q] = splat_alpha(B, col, dy[q]);
-        okq[q] = a[q].keep && (pos < last[q]);
-        contrib = contrib || okq[q];
-      }
-      // phase 2 (skipped when no pixel of the warp keeps the splat): gradient terms
-      if (!__any_sync(0xffffffffu, contrib)) continue;
-      const float4 C = M.S.C[j];
-      float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f, cz = 0.0f, cr = 0.0f, cgr = 0.0f, cb = 0.0f;
+      for (int g = 0; g < G; ++g) {
+        dy[g] = vadd(second<W>(XY), npy[g]);
+        const V e = splat_exponent<W>(QCL, col, dy[g]);
 #pragma unroll
-      for (int q = 0; q < PX; ++q) {
-        // aok = alpha for a kept splat, else 0: then w = 0 and Sg, T stay bit for bit unchanged
-        const bool ok = okq[q];
-        const bool open = ok && !(a[q].raw > kAlphaMax);  // the 0.99 clamp passes no gradient
-        const float Tq = T[q];
-        const float aok = ok ? a[q].alpha : 0.0f;
-        const float w = __fmul_rn(aok, Tq);
-        const float cgz = C.x * gr[q] + C.y * gg[q] + C.z * gb[q] + B.z * gd[q];
-        const float sg = __fmaf_rn(-cgz, w, Sg[q]);  // colour/depth behind this splat, weighted by dL/dpixel
-        const float dalpha = Tq * cgz - __fdividef(sg + hT[q], 1.0f - a[q].alpha);
-        const float dpow = (open ? a[q].alpha : 0.0f) * dalpha;
-        const float ydp = dy[q] * dpow;
-        P0 += dpow;
-        P1 += ydp;
-        P2 = fmaf(dy[q], ydp, P2);
-        cz = fmaf(w, gd[q], cz);
-        cr = fmaf(w, gr[q], cr);
-        cgr = fmaf(w, gg[q], cgr);
-        cb = fmaf(w, gb[q], cb);
-        Sg[q] = sg;
-        T[q] = __fmaf_rn(-Tq, aok, Tq);
+        for (int i = 0; i < W; ++i) {
+          const int q = g * W + i;
+          raw[q] = ex2_approx(comp(e, i));
+          const float a = fminf(raw[q], kAlphaMax);
+          set_comp(alpha[g], i, a);
+          okq[q] = (comp(e, i) <= QCL.z) && (a >= kAlphaMin) && (pos < last[q]);
+          contrib = contrib || okq[q];
+        }
       }
-      const float dxP0 = dx * P0;
-      const float v[10] = {dxP0, P1, dx * dxP0, dx * P1, P2, cz, P0, cr, cgr, cb};
+      // phase 2 (skipped when no pixel of the warp keeps the splat): gradient terms, two pixels
+      // per packed instruction. The colour-gradient sums are kept negated (nw = -w).
+      if (!__any_sync(0xffffffffu, contrib)) continue;
+      const float4 RG = M.S.RG[j], BZ = M.S.BZ[j];
+      const V cR = first<W>(RG), cG = second<W>(RG), cB = first<W>(BZ), cZ = second<W>(BZ);
+      V P0 = zero, P1 = zero, P2 = zero, ncz = zero, ncr = zero, ncg = zero, ncb = zero;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        // aok = alpha for a kept splat, else 0: then w = 0 and Sg, T stay unchanged;
+        // oal = alpha where the gradient passes (kept and not clamped at 0.99), else 0
+        V aok, oal, nr;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+          const int q = g * W + i;
+          const float a = comp(alpha[g], i);
+          set_comp(aok, i, okq[q] ? a : 0.0f);
+          set_comp(oal, i, (okq[q] && !(raw[q] > kAlphaMax)) ? a : 0.0f);
+          set_comp(nr, i, rcp_approx(a - 1.0f));  // -1 / (1 - alpha)
+        }
+        const V nT = vmul(T[g], minus1);
+        const V nw = vmul(aok, nT);
+        const V cgz = vfma(cZ, gdv[g], vfma(cB, gbv[g], vfma(cG, ggv[g], vmul(cR, grv[g]))));
+        const V sg = vfma(cgz, nw, Sgv[g]);  // colour/depth behind this splat, weighted by dL/dpixel
+        const V dalpha = vfma(T[g], cgz, vmul(HT ? vadd(sg, hTv[g]) : sg, nr));
+        const V dpow = vmul(oal, dalpha);
+        const V ydp = vmul(dy[g], dpow);
+        P0 = vadd(P0, dpow);
+        P1 = vadd(P1, ydp);
+        P2 = vfma(dy[g], ydp, P2);
+        ncz = vfma(nw, gdv[g], ncz);
+        ncr = vfma(nw, grv[g], ncr);
+        ncg = vfma(nw, ggv[g], ncg);
+        ncb = vfma(nw, gbv[g], ncb);
+        Sgv[g] = sg;
+        T[g] = vfma(nT, aok, T[g]);
+      }
+      const float p0 = hsum(P0), p1 = hsum(P1);
+      const float dx = comp(col.dx, 0);
+      const float dxP0 = dx * p0;
+      const float v[10] = {dxP0, p1, dx * dxP0, dx * p1, hsum(P2), hsum(ncz), p0, hsum(ncr), hsum(ncg), hsum(ncb)};
       const float r = warp_reduce10(v, lane);
       if (writer) M.part[warp][j][idx] = r;
     }
@@ -201,17 +234,17 @@ __device__ __forceinline__ void bwd_sweep(BwdSmem<PX, CH>& M, const Layout& L, u
         for (int w = 0; w < kWarps; ++w) acc += M.part[w][jj][q];
         R[q] = acc;
       }
-      // R = (sum dx P0, sum P1, sum dx^2 P0, sum dx P1, sum P2, dz, sum P0, dr, dg, db)
-      const float4 A = M.S.A[jj], B = M.S.B[jj];
-      const float du = kLn2 * (2.0f * A.z * R[0] + A.w * R[1]);
-      const float dv = kLn2 * (2.0f * B.x * R[1] + A.w * R[0]);
-      const float dop = R[6] != 0.0f ? R[6] / B.y : 0.0f;
+      // R = (sum dx P0, sum P1, sum dx^2 P0, sum dx P1, sum P2, -dz, sum P0, -dr, -dg, -db)
+      const float qa = M.S.QAB[jj].x, qb = M.S.QAB[jj].z, qc = M.S.QCL[jj].x, op = M.S.op[jj];
+      const float du = kLn2 * (2.0f * qa * R[0] + qb * R[1]);
+      const float dv = kLn2 * (2.0f * qc * R[1] + qb * R[0]);
+      const float dop = R[6] != 0.0f ? R[6] / op : 0.0f;
       const uint32_t slot = M.slot[jj];
       if (!GS_INDEX_OK(static_cast<int64_t>(slot) < L.cap, &at<Status>(ws, L.status)->err)) continue;
       float4* dst = reinterpret_cast<float4*>(pair_grads + static_cast<size_t>(slot) * kPairGradStride);
       dst[0] = make_float4(du, dv, -0.5f * R[2], -R[3]);
-      dst[1] = make_float4(-0.5f * R[4], R[5], dop, R[7]);
-      dst[2] = make_float4(R[8], R[9], 0.0f, 0.0f);
+      dst[1] = make_float4(-0.5f * R[4], -R[5], dop, -R[7]);
+      dst[2] = make_float4(-R[8], -R[9], 0.0f, 0.0f);
       atomicOr(&pair_valid[slot >> 5], 1u << (slot & 31));
     }
     __syncthreads();

@@ -277,12 +277,36 @@ __device__ __forceinline__ Projected project_item(const Layout& L, const GaussPt
 // block's segment of the staging arrays in item order (compacted by k_live_copy), its depth
 // key's digits to the item-sort histograms. The last block to finish scans the blocks' live
 // counts into their first positions among the live items.
+// The block of items (in item order) that launched block b takes. The n blocks of items are seen
+// as rows of Bv = ceil(n / K) blocks, one row per view (rows cut at block boundaries, so a row
+// is about one view's items; the last row may be shorter), and the launch order walks this
+// grid column by column: the blocks in flight at any time read about the same Gaussians for
+// every view, which then come from L2 for all but the first view. A bijection of [0, n).
+__device__ __forceinline__ int64_t proj_block(const Layout& L, int64_t b) {
+  const int64_t n = L.n_proj_groups;
+  if (L.K <= 1) return b;
+  const int64_t bv = (n + L.K - 1) / L.K;
+  const int64_t rows = (n + bv - 1) / bv;  // non-empty rows (at most K)
+  if (rows <= 1) return b;
+  const int64_t rem = n - (rows - 1) * bv;  // blocks in the last row, 1 .. bv
+  int64_t r, k;
+  if (b < rem * rows) {  // columns that every row has
+    r = b / rows;
+    k = b % rows;
+  } else {  // the remaining columns, which the last row lacks
+    const int64_t c = b - rem * rows;
+    r = rem + c / (rows - 1);
+    k = c % (rows - 1);
+  }
+  return k * bv + r;
+}
+
 __global__ void __launch_bounds__(kProjThreads, 3) k_project(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                          uint8_t* __restrict__ ws) {
   pdl_wait();
   constexpr int kWords = kProjItemsMax / 32;
   const int words = L.proj_items / 32;
-  const int64_t blk = blockIdx.x;
+  const int64_t blk = proj_block(L, blockIdx.x);
   const int64_t first = blk * L.proj_items;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   __shared__ uint32_t s_hist[4 * 256];

@@ -68,8 +68,10 @@ struct FwdSmemOf<PX, CH, 0> {
   };
 };
 
-template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false, int CHB = 0>
-__global__ void __launch_bounds__(kTilePixels / PX, PX == 4 ? kMinBlocksPx4 : 1) k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws,
+// MANY = false (the fused variant only): compiled without the 12-blocks-per-SM register budget,
+// for grids that fit on the GPU in one wave anyway, where each block's own latency sets the time.
+template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false, int CHB = 0, bool MANY = true>
+__global__ void __launch_bounds__(kTilePixels / PX, (PX == 4 && MANY) ? kMinBlocksPx4 : 1) k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws,
                                                                  float* __restrict__ out_rgb,
                                                                  float* __restrict__ out_depth,
                                                                  float* __restrict__ out_T,
@@ -350,11 +352,29 @@ cudaError_t launch_raster_fwd_l1_bwd(const Layout& L, void* ws, float* rgb, floa
                     loss.d_loss};
   const int px = pick_px(L.fwd_px, kDefaultFwdPx);
   const int ch = pick_chunk(L.fwd_chunk, 64, 256, kFwdChunk);
-  // the backward phase stages kBwdChunk splats per chunk (the chunk depth changes no result)
-#define GS_FB(P, C)                                                                                             \
-  launch(k_raster_fwd<P, C, false, true, false, kBwdChunk>, grid, kTilePixels / P,                                 \
-         cap_smem(k_raster_fwd<P, C, false, true, false, kBwdChunk>, L.raster_bps), s, L, w, rgb, depth, T_final, \
+  // the backward phase stages kBwdChunk splats per chunk (the chunk depth changes no result); at 4
+  // pixels per thread, a grid that the variant without the 12-block register budget runs in one
+  // wave (its resident blocks per SM, from the occupancy calculator, times the SMs) takes it
+  static int uncapped_blocks[64] = {};  // per device: resident blocks per SM of the uncapped variant
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!uncapped_blocks[dev]) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_raster_fwd<4, 128, false, true, false, kBwdChunk, false>,
+                                                  kTilePixels / 4, 0);
+    uncapped_blocks[dev] = b > 0 ? b : 1;
+  }
+  const bool one_wave = L.n_tiles <= static_cast<int64_t>(device_sms()) * uncapped_blocks[dev];
+#define GS_FB_M(P, C, M)                                                                                             \
+  launch(k_raster_fwd<P, C, false, true, false, kBwdChunk, M>, grid, kTilePixels / P,                                 \
+         cap_smem(k_raster_fwd<P, C, false, true, false, kBwdChunk, M>, L.raster_bps), s, L, w, rgb, depth, T_final, \
          last, ev, cp, F, Occlusion{})
+#define GS_FB(P, C)                       \
+  if (one_wave) {                         \
+    GS_FB_M(P, C, (P != 4));              \
+  } else {                                \
+    GS_FB_M(P, C, true);                  \
+  }
 #define GS_FB_CH(P)                  \
   switch (ch) {                      \
     case 64: GS_FB(P, 64); break;    \
@@ -368,6 +388,7 @@ cudaError_t launch_raster_fwd_l1_bwd(const Layout& L, void* ws, float* rgb, floa
   }
 #undef GS_FB_CH
 #undef GS_FB
+#undef GS_FB_M
   return cudaGetLastError();
 }
 

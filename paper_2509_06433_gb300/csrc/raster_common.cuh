@@ -6,9 +6,9 @@
 // update is branch-free (a masked blend with weight 0 leaves every accumulator bit for bit
 // unchanged), so the PX pixel chains interleave, and pairs of them share packed FP32
 // instructions (add / multiply / FMA on two pixels at once). The tile's depth-sorted list is
-// walked in chunks staged in shared memory as five float4 of duplicated operands, the opacity
-// and a row mask per splat (coalesced loads of the sorted keys, whose low word is the Gaussian
-// id, one gather of the projected record each).
+// walked in chunks staged in shared memory as three float4 and a row mask per splat (coalesced
+// loads of the sorted keys, whose low word is the Gaussian id, one gather of the projected
+// record each).
 //
 // Both kernels evaluate a splat's opacity with the same inline function on the same
 // operands, so the backward pass takes exactly the forward pass's skip and stop decisions
@@ -50,8 +50,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // multiply-add to two pixels' operands, each component rounded exactly as the scalar
 // __fadd_rn / __fmul_rn / __fmaf_rn would round it. A thread's PX pixels are processed in
 // groups of W = 2 (PX = 2, 4) or W = 1 (PX = 1) components, so every variant still takes
-// bit-identical decisions; the per-splat operands are staged in duplicated pairs so that they
-// feed the packed instructions straight from shared memory.
+// bit-identical decisions; a splat's operands are broadcast into register pairs once per splat
+// (staging them duplicated in shared memory instead costs more in loads and shared memory than
+// the broadcasts).
 template <int W>
 struct Vec;
 template <>
@@ -82,29 +83,14 @@ __device__ __forceinline__ typename Vec<W>::T bcast(float x) {
   if constexpr (W == 1) return x;
   else return make_float2(x, x);
 }
-// first / second pair of a staged float4 (x, x, y, y): (x, x) / (y, y), or x / y for W = 1
-template <int W>
-__device__ __forceinline__ typename Vec<W>::T first(const float4& v) {
-  if constexpr (W == 1) return v.x;
-  else return make_float2(v.x, v.y);
-}
-template <int W>
-__device__ __forceinline__ typename Vec<W>::T second(const float4& v) {
-  if constexpr (W == 1) return v.z;
-  else return make_float2(v.z, v.w);
-}
-
-// Staged splat, every per-splat operand duplicated into a pair: XY = (x, x, y, y) with (x, y)
-// the 2D mean relative to the tile origin; QAB = (qa, qa, qb, qb), QCL = (qc, qc, log2 o,
-// log2 o) with power * log2(e) = qa dx^2 + qb dx dy + qc dy^2; RG = (r, r, g, g), BZ = (b, b,
-// depth, depth); op = opacity. rows: bit r is set when the splat's ellipse {opacity * 2^power
-// >= 1/255}, widened by a safety margin, meets the pixel-centre row y = r + 0.5 of the tile
-// within the columns [0.5, 15.5]. A warp none of whose rows is set skips the splat without
-// changing any decision.
+// Staged splat: A = (x, y, qa, qb), B = (qc, opacity, depth, log2 opacity), C = (r, g, b, -) where
+// (x, y) is the 2D mean relative to the tile origin and power * log2(e) = qa dx^2 + qb dx dy + qc dy^2.
+// rows: bit r is set when the splat's ellipse {opacity * 2^power >= 1/255}, widened by a safety
+// margin, meets the pixel-centre row y = r + 0.5 of the tile within the columns [0.5, 15.5]. A
+// warp none of whose rows is set skips the splat without changing any decision.
 template <int CH>
 struct Stage {
-  float4 XY[CH], QAB[CH], QCL[CH], RG[CH], BZ[CH];
-  float op[CH];
+  float4 A[CH], B[CH], C[CH];
   uint32_t rows[CH];
 };
 
@@ -157,12 +143,9 @@ __device__ __forceinline__ uint32_t stage_splat(Stage<CH>& S, int j, const Layou
   const float x = __fadd_rn(__fsub_rn(uv.x, ox), uv.y), y = __fadd_rn(__fsub_rn(uv.z, oy), uv.w);
   const float qa = __fmul_rn(cn.x, -0.5f * kLog2e), qb = __fmul_rn(cn.y, -kLog2e), qc = __fmul_rn(cn.z, -0.5f * kLog2e);
   const float lo = __log2f(co.w);
-  S.XY[j] = make_float4(x, x, y, y);
-  S.QAB[j] = make_float4(qa, qa, qb, qb);
-  S.QCL[j] = make_float4(qc, qc, lo, lo);
-  S.RG[j] = make_float4(co.x, co.x, co.y, co.y);
-  S.BZ[j] = make_float4(co.z, co.z, cn.w, cn.w);
-  S.op[j] = co.w;
+  S.A[j] = make_float4(x, y, qa, qb);
+  S.B[j] = make_float4(qc, co.w, cn.w, lo);
+  S.C[j] = make_float4(co.x, co.y, co.z, 0.0f);
   S.rows[j] = splat_rows(x, y, -qa, -qb, -qc, co.w);
   return gid;
 }
@@ -181,18 +164,17 @@ struct Column {
   typename Vec<W>::T dx, c1, c0;
 };
 template <int W>
-__device__ __forceinline__ Column<W> splat_column(const float4& XY, const float4& QAB, const float4& QCL,
-                                                  typename Vec<W>::T npx) {
+__device__ __forceinline__ Column<W> splat_column(const float4& A, const float4& B, typename Vec<W>::T npx) {
   Column<W> c;
-  c.dx = vadd(first<W>(XY), npx);
-  c.c1 = vmul(second<W>(QAB), c.dx);
-  c.c0 = vfma(vmul(first<W>(QAB), c.dx), c.dx, second<W>(QCL));
+  c.dx = vadd(bcast<W>(A.x), npx);
+  c.c1 = vmul(bcast<W>(A.w), c.dx);
+  c.c0 = vfma(vmul(bcast<W>(A.z), c.dx), c.dx, bcast<W>(B.w));
   return c;
 }
 template <int W>
-__device__ __forceinline__ typename Vec<W>::T splat_exponent(const float4& QCL, const Column<W>& c,
+__device__ __forceinline__ typename Vec<W>::T splat_exponent(const float4& B, const Column<W>& c,
                                                              typename Vec<W>::T dy) {
-  return vfma(vfma(first<W>(QCL), dy, c.c1), dy, c.c0);
+  return vfma(vfma(bcast<W>(B.x), dy, c.c1), dy, c.c0);
 }
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;

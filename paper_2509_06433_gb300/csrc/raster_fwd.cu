@@ -156,13 +156,13 @@ __global__ void __launch_bounds__(kTilePixels / PX, (PX == 4 && MANY) ? kMinBloc
         if (__all_sync(0xffffffffu, all_done)) break;
       }
       if (!(S.rows[j] & wrows)) continue;
-      const float4 XY = S.XY[j], QAB = S.QAB[j], QCL = S.QCL[j], RG = S.RG[j], BZ = S.BZ[j];
-      const Column<W> col = splat_column<W>(XY, QAB, QCL, npx);
-      const V cR = first<W>(RG), cG = second<W>(RG), cB = first<W>(BZ), cZ = second<W>(BZ);
+      const float4 A = S.A[j], B = S.B[j], C = S.C[j];
+      const Column<W> col = splat_column<W>(A, B, npx);
+      const V cR = bcast<W>(C.x), cG = bcast<W>(C.y), cB = bcast<W>(C.z), cZ = bcast<W>(B.z), Ay = bcast<W>(A.y);
       const int pos = pos0 + j;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        const V e = splat_exponent<W>(QCL, col, vadd(second<W>(XY), npy[g]));
+        const V e = splat_exponent<W>(B, col, vadd(Ay, npy[g]));
         const V nT = vmul(T[g], minus1);
         V alpha;
         bool keep[W];
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kTilePixels / PX, (PX == 4 && MANY) ? kMinBloc
           const int q = g * W + i;
           const float a = fminf(ex2_approx(comp(e, i)), kAlphaMax);
           set_comp(alpha, i, a);
-          keep[i] = (comp(e, i) <= QCL.z) && (a >= amin[q]);
+          keep[i] = (comp(e, i) <= B.w) && (a >= amin[q]);
         }
         const V Tn = vfma(nT, alpha, T[g]);  // T (1 - alpha)
         V ae;  // alpha for a blended splat, else 0 (then w = 0 and T, the sums stay bit for bit)
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kTilePixels / PX, (PX == 4 && MANY) ? kMinBloc
           const int q = g * W + i;
           bool kp = keep[i], behind = false;
           if (OCC) {
-            behind = BZ.z >= zmax[q];  // the splat's camera depth at or behind the surface
+            behind = B.z >= zmax[q];  // the splat's camera depth at or behind the surface
             kp = kp && !behind;
           }
           const bool stop = kp && (comp(Tn, i) < kTStop);

@@ -159,8 +159,9 @@ __device__ __forceinline__ void bwd_sweep(BwdSmem<PX, CH>& M, const Layout& L, u
     const int nw = min(n, warp_last - pos0);  // splats of this chunk this warp must visit
     for (int j = 0; j < nw; ++j) {
       if (!(M.S.rows[j] & wrows)) continue;
-      const float4 XY = M.S.XY[j], QAB = M.S.QAB[j], QCL = M.S.QCL[j];
-      const Column<W> col = splat_column<W>(XY, QAB, QCL, npx);
+      const float4 A = M.S.A[j], B = M.S.B[j];
+      const Column<W> col = splat_column<W>(A, B, npx);
+      const V Ay = bcast<W>(A.y);
       const int pos = pos0 + j;
       // phase 1: opacity and keep/skip decision for the thread's pixels
       V dy[G], alpha[G];
@@ -169,23 +170,23 @@ __device__ __forceinline__ void bwd_sweep(BwdSmem<PX, CH>& M, const Layout& L, u
       bool contrib = false;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        dy[g] = vadd(second<W>(XY), npy[g]);
-        const V e = splat_exponent<W>(QCL, col, dy[g]);
+        dy[g] = vadd(Ay, npy[g]);
+        const V e = splat_exponent<W>(B, col, dy[g]);
 #pragma unroll
         for (int i = 0; i < W; ++i) {
           const int q = g * W + i;
           raw[q] = ex2_approx(comp(e, i));
           const float a = fminf(raw[q], kAlphaMax);
           set_comp(alpha[g], i, a);
-          okq[q] = (comp(e, i) <= QCL.z) && (a >= kAlphaMin) && (pos < last[q]);
+          okq[q] = (comp(e, i) <= B.w) && (a >= kAlphaMin) && (pos < last[q]);
           contrib = contrib || okq[q];
         }
       }
       // phase 2 (skipped when no pixel of the warp keeps the splat): gradient terms, two pixels
       // per packed instruction. The colour-gradient sums are kept negated (nw = -w).
       if (!__any_sync(0xffffffffu, contrib)) continue;
-      const float4 RG = M.S.RG[j], BZ = M.S.BZ[j];
-      const V cR = first<W>(RG), cG = second<W>(RG), cB = first<W>(BZ), cZ = second<W>(BZ);
+      const float4 C = M.S.C[j];
+      const V cR = bcast<W>(C.x), cG = bcast<W>(C.y), cB = bcast<W>(C.z), cZ = bcast<W>(B.z);
       V P0 = zero, P1 = zero, P2 = zero, ncz = zero, ncr = zero, ncg = zero, ncb = zero;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
@@ -235,7 +236,7 @@ __device__ __forceinline__ void bwd_sweep(BwdSmem<PX, CH>& M, const Layout& L, u
         R[q] = acc;
       }
       // R = (sum dx P0, sum P1, sum dx^2 P0, sum dx P1, sum P2, -dz, sum P0, -dr, -dg, -db)
-      const float qa = M.S.QAB[jj].x, qb = M.S.QAB[jj].z, qc = M.S.QCL[jj].x, op = M.S.op[jj];
+      const float qa = M.S.A[jj].z, qb = M.S.A[jj].w, qc = M.S.B[jj].x, op = M.S.B[jj].y;
       const float du = kLn2 * (2.0f * qa * R[0] + qb * R[1]);
       const float dv = kLn2 * (2.0f * qc * R[1] + qb * R[0]);
       const float dop = R[6] != 0.0f ? R[6] / op : 0.0f;

@@ -455,7 +455,11 @@ def test_autotuner_picks_a_variant():
     assert res["choice"][0] in (1, 2, 4) and res["choice"][1] in (1, 2, 4)
     assert (r.cfg.fwd_px_per_thread, r.cfg.bwd_px_per_thread) == res["choice"]
     assert res["chunks"][0] in (64, 128, 256) and res["chunks"][1] in (32, 64, 128)
-    assert (r.cfg.fwd_chunk, r.cfg.bwd_chunk) == res["chunks"]
+    if res["fused"]:  # the one-launch form's backward phase stages a fixed chunk; bwd_chunk keeps the
+        # standalone backward's best
+        assert res["chunks"] == (r.cfg.fwd_chunk, autotune.FUSED_BWD_CHUNK)
+    else:
+        assert (r.cfg.fwd_chunk, r.cfg.bwd_chunk) == res["chunks"]
     assert r.fused_compositing == res["fused"] and set(k[0] for k in res["fused_ms"]) == {1, 2, 4}
     assert res["two_launch_ms"] > 0 and all(v > 0 for v in res["fused_ms"].values())
     assert res["blocks_per_sm"] in autotune.BLOCKS_PER_SM and r.cfg.raster_blocks_per_sm == res["blocks_per_sm"]

@@ -97,14 +97,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(Layout L, uint8_t*
   Status* st = at<Status>(ws, L.status);
   const int64_t chunks = (static_cast<int64_t>(st->n_live) + kProjBlock - 1) / kProjBlock;
   __shared__ uint64_t tmp[32];
-  uint64_t carry = 0;
-  for (int64_t base = 0; base < chunks; base += kScanThreads) {
-    const int64_t i = base + threadIdx.x;
-    const uint64_t x = (i < chunks) ? sums[i] : 0;
-    uint64_t tot;
-    const uint64_t incl = block_inclusive_scan1024(x, tmp, &tot);
-    if (i < chunks) offs[i] = carry + incl - x;
-    carry += tot;
+  // each thread sums a run of consecutive totals, one block-wide scan of the runs' sums gives
+  // every run its start, and the thread then writes its run's offsets (one barrier round, not
+  // one per 1024 totals)
+  const int64_t per = (chunks + kScanThreads - 1) / kScanThreads;
+  const int64_t b0 = threadIdx.x * per, b1 = b0 + per < chunks ? b0 + per : chunks;
+  uint64_t run = 0;
+  for (int64_t i = b0; i < b1; ++i) run += sums[i];
+  uint64_t carry;
+  uint64_t start = block_inclusive_scan1024(run, tmp, &carry) - run;
+  for (int64_t i = b0; i < b1; ++i) {
+    offs[i] = start;
+    start += sums[i];
   }
   if (threadIdx.x == 0) {
     st->total_pairs = carry;

@@ -111,18 +111,25 @@ __device__ __forceinline__ uint32_t pack16(int lo, int hi) {
 // scales) has length <= max S, so |m1| <= (fx / z)(1 + |tx|) max S (m1, m2: the rows of J R Q S
 // whose squares sum, with the dilation, to the trace a + c), and lambda_max <= a + c +
 // sqrt(0.1). The bound carries a 1% + 2 px margin and the 2D mean a 1e-4 relative + 1 px one,
-// so the exact computation would cull such an item too. NaN anywhere keeps the item (the
-// exact path culls it itself).
+// so the exact computation would cull such an item too; the margins also cover the few-ulp
+// errors of the approximate exp, reciprocal, quotient and square root the bound is computed
+// with (it runs for every item, the exact projection only for the survivors). NaN anywhere
+// keeps the item (the exact path culls it itself).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ bool off_screen(const Layout& L, const gs_camera_t& cam, float xc, float yc, float zc,
                                            const float (&ls)[3]) {
-  const float smax = expf(fmaxf(ls[0], fmaxf(ls[1], ls[2]))) * 1.001f;
-  const float iz = 1.0f / zc;
+  const float smax = __expf(fmaxf(ls[0], fmaxf(ls[1], ls[2]))) * 1.002f;
+  const float iz = __fdividef(1.0f, zc);
   const float xz = xc * iz, yz = yc * iz;
-  const float limx = 1.3f * (0.5f * static_cast<float>(L.W) / cam.fx);
-  const float limy = 1.3f * (0.5f * static_cast<float>(L.H) / cam.fy);
+  const float limx = 1.3f * __fdividef(0.5f * static_cast<float>(L.W), cam.fx);
+  const float limy = 1.3f * __fdividef(0.5f * static_cast<float>(L.H), cam.fy);
   const float m1 = fabsf(cam.fx) * iz * (1.0f + fminf(fabsf(xz), limx)) * smax;
   const float m2 = fabsf(cam.fy) * iz * (1.0f + fminf(fabsf(yz), limy)) * smax;
-  const float rb = 3.0f * sqrtf(m1 * m1 + m2 * m2 + 1.0f) * 1.01f + 2.0f;
+  const float rb = 3.0f * sqrt_approx(m1 * m1 + m2 * m2 + 1.0f) * 1.01f + 2.0f;
   const float u = cam.fx * xz + cam.cx, v = cam.fy * yz + cam.cy;
   const float mu = 1e-4f * fabsf(u) + 1.0f, mv = 1e-4f * fabsf(v) + 1.0f;
   const float xhi = static_cast<float>(kTile * (L.Tx + 1)), yhi = static_cast<float>(kTile * (L.Ty + 1));

@@ -25,11 +25,17 @@ SCENES = {
     "ragged_tiny": lambda: make_scene("map100k", n=600, W=50, H=37, f=40.0),
     "window_k3": lambda: make_scene("window500k", n=20000, K=3, W=160, H=120, f=130.0),
 }
+# scenes of the fused-form test only: 3 views of 640x480 are 3600 tiles, more than one wave of the
+# compositing kernel's variant without the 12-blocks-per-SM register budget, so the 4-pixel fused
+# launch takes the variant compiled for 12 blocks (the scenes above take the other one)
+FUSED_ONLY = {
+    "window_k3_vga": lambda: make_scene("window500k", n=60000, K=3, W=640, H=480, f=525.0),
+}
 
 
 @functools.lru_cache(maxsize=None)
 def scene(name):
-    return SCENES[name]()
+    return (SCENES.get(name) or FUSED_ONLY[name])()
 
 
 @functools.lru_cache(maxsize=None)
@@ -378,7 +384,7 @@ def test_backward_on_deep_lists():
         assert e < GRAD_RTOL, (k, e)
 
 
-@pytest.mark.parametrize("name", ["ragged_tiny", "map100k", "window_k3"])
+@pytest.mark.parametrize("name", ["ragged_tiny", "map100k", "window_k3", "window_k3_vga"])
 def test_fused_forward_backward_equals_the_two_calls(name):
     """gs_raster_fwd_l1_bwd (each tile's block continues into its backward pass) equals
     gs_raster_fwd_l1 followed by gs_raster_bwd bit for bit: images, T, last, loss gradient images,

@@ -131,7 +131,7 @@ constexpr int kPartial = 16;
 // (balanced whatever the chunks' work); a chunk's items are in view order, so each view k present
 // in chunk c gets the chunk's sum in slot c + k of pose_partials (unique: a later chunk's first
 // view is at least this chunk's last), which k_pose_reduce sums over the view's chunks in order.
-__global__ void __launch_bounds__(kPoseBlock) k_item_grads(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
+__global__ void __launch_bounds__(kPoseBlock, 4) k_item_grads(Layout L, GaussPtrs G, const gs_camera_t* __restrict__ cams,
                                                           uint8_t* __restrict__ ws, int want_params,
                                                           float* __restrict__ pose_partials) {
   pdl_wait();

@@ -34,9 +34,12 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
 // Resident blocks per SM the compiler must fit at 4 pixels per thread (64 threads): a register
-// budget of 80 per thread, without spills. The packed pixel pairs leave the compositing loops
-// bound by instruction latency as much as by issue, and 12 blocks hide more of it than 10.
+// budget of 80 per thread (no spills) for the forward and backward kernels, 72 (a few spilled
+// bytes) for the fused forward + backward. The packed pixel pairs leave the compositing loops
+// bound by instruction latency as much as by issue, and more resident blocks hide more of it
+// (the fused kernel at aerial2m: 6.68 ms at 10 blocks, 6.15 at 12, 6.00 at 14).
 constexpr int kMinBlocksPx4 = 12;
+constexpr int kMinBlocksFusedPx4 = 14;
 constexpr int kFwdChunk = 128;  // splats staged per forward chunk (default; 64 and 256 also built)
 constexpr int kBwdChunk = 64;   // splats staged per backward chunk (default; 32 and 128 also built)
 

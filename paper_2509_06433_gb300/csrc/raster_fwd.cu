@@ -68,10 +68,10 @@ struct FwdSmemOf<PX, CH, 0> {
   };
 };
 
-// MANY = false (the fused variant only): compiled without the 12-blocks-per-SM register budget,
-// for grids that fit on the GPU in one wave anyway, where each block's own latency sets the time.
+// MANY = false (the fused variant only): compiled without the blocks-per-SM register budget, for
+// grids that fit on the GPU in one wave anyway, where each block's own latency sets the time.
 template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false, int CHB = 0, bool MANY = true>
-__global__ void __launch_bounds__(kTilePixels / PX, (PX == 4 && MANY) ? kMinBlocksPx4 : 1) k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws,
+__global__ void __launch_bounds__(kTilePixels / PX, (PX == 4 && MANY) ? (CHB > 0 ? kMinBlocksFusedPx4 : kMinBlocksPx4) : 1) k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws,
                                                                  float* __restrict__ out_rgb,
                                                                  float* __restrict__ out_depth,
                                                                  float* __restrict__ out_T,
@@ -353,8 +353,8 @@ cudaError_t launch_raster_fwd_l1_bwd(const Layout& L, void* ws, float* rgb, floa
   const int px = pick_px(L.fwd_px, kDefaultFwdPx);
   const int ch = pick_chunk(L.fwd_chunk, 64, 256, kFwdChunk);
   // the backward phase stages kBwdChunk splats per chunk (the chunk depth changes no result); at 4
-  // pixels per thread, a grid that the variant without the 12-block register budget runs in one
-  // wave (its resident blocks per SM, from the occupancy calculator, times the SMs) takes it
+  // pixels per thread, a grid that the variant without the blocks-per-SM register budget runs in
+  // one wave (its resident blocks per SM, from the occupancy calculator, times the SMs) takes it
   static int uncapped_blocks[64] = {};  // per device: resident blocks per SM of the uncapped variant
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;

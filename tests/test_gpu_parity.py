@@ -26,8 +26,8 @@ SCENES = {
     "window_k3": lambda: make_scene("window500k", n=20000, K=3, W=160, H=120, f=130.0),
 }
 # scenes of the fused-form test only: 3 views of 640x480 are 3600 tiles, more than one wave of the
-# compositing kernel's variant without the 12-blocks-per-SM register budget, so the 4-pixel fused
-# launch takes the variant compiled for 12 blocks (the scenes above take the other one)
+# compositing kernel's variant without the blocks-per-SM register budget, so the 4-pixel fused
+# launch takes the variant compiled for more resident blocks (the scenes above take the other one)
 FUSED_ONLY = {
     "window_k3_vga": lambda: make_scene("window500k", n=60000, K=3, W=640, H=480, f=525.0),
 }

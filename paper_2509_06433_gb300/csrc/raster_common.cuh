@@ -102,10 +102,16 @@ struct Stage {
 // inside the strip is convex, so its y-extent is an interval: its ends are the ellipse's
 // top / bottom points when they lie inside the strip, else the ellipse's crossings of the
 // strip edge on their side. Margins: 2% + 2e-4 on tau (log2 units), 0.05 px on the strip, 0.05
-// px + 0.2% of the half-height on the interval. Anything that is not a proper ellipse keeps
-// every row.
+// px + 0.2% of the half-height on the interval; they also cover the few-ulp errors of the
+// approximate logarithm, quotients and square roots used here (every staged splat computes its
+// mask, in both passes). Anything that is not a proper ellipse keeps every row.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ uint32_t splat_rows(float mx, float my, float Qa, float Qb, float Qc, float opacity) {
-  const float tau0 = log2f(255.0f * opacity);
+  const float tau0 = __log2f(255.0f * opacity);
   const float tau = tau0 + 0.02f * fabsf(tau0) + 2e-4f;
   if (!(tau >= 0.0f)) return 0u;  // opacity below 1/255 (or NaN): no pixel keeps the splat
   // determinant Qa Qc - (Qb/2)^2 with the products' rounding errors restored (no cancellation)
@@ -113,17 +119,17 @@ __device__ __forceinline__ uint32_t splat_rows(float mx, float my, float Qa, flo
   const float p1 = Qa * Qc, p2 = h * h;
   const float D = (p1 - p2) + (fmaf(Qa, Qc, -p1) - fmaf(h, h, -p2));
   if (!(Qa > 0.0f) || !(Qc > 0.0f) || !(D > 0.0f)) return 0xffffu;
-  const float hx = sqrtf(tau * Qc / D), hy = sqrtf(tau * Qa / D);
+  const float hx = sqrt_approx(__fdividef(tau * Qc, D)), hy = sqrt_approx(__fdividef(tau * Qa, D));
   if (!(hx < 1e7f) || !(hy < 1e7f)) return 0xffffu;
   constexpr float xa = 0.5f - 0.05f, xb = 15.5f + 0.05f;
   if (mx + hx < xa || mx - hx > xb) return 0u;
-  const float sl = h / Qa;  // the ellipse's widest chord at height dy is centred on mx - sl dy
+  const float sl = __fdividef(h, Qa);  // the ellipse's widest chord at height dy is centred on mx - sl dy
   const float xt = mx - sl * hy, xbot = mx + sl * hy;
   // dy where the ellipse crosses x = xe (upper: sign +1)
   auto cross = [&](float xe, float sign) {
     const float dxe = xe - mx, ad = fabsf(dxe);
     const float disc = fmaxf(D * (hx - ad) * (hx + ad), 0.0f);  // Qc tau - D dxe^2
-    return (fmaf(sign, sqrtf(disc), -h * dxe)) / Qc;
+    return __fdividef(fmaf(sign, sqrt_approx(disc), -h * dxe), Qc);
   };
   const float up = xt < xa ? cross(xa, 1.0f) : (xt > xb ? cross(xb, 1.0f) : hy);
   const float dn = xbot < xa ? cross(xa, -1.0f) : (xbot > xb ? cross(xb, -1.0f) : -hy);

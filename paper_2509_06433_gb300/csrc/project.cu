@@ -314,6 +314,8 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(Layout L, GaussPtrs
                                                          uint8_t* __restrict__ ws) {
   pdl_wait();
   constexpr int kWords = kProjItemsMax / 32;
+  static_assert(kWords == 64, "the survivor scan below gives each lane of warp 0 two mask words");
+  static_assert(kWords % (kProjThreads / 32) == 0, "phase 1 covers the mask words in whole rounds");
   const int words = L.proj_items / 32;
   const int64_t blk = proj_block(L, blockIdx.x);
   const int64_t first = blk * L.proj_items;

@@ -102,6 +102,10 @@ __device__ __forceinline__ FF proj_coord(float f, float c, FF x, FF z) {
   return renorm(s.hi, __fadd_rn(pl, s.lo));
 }
 
+// Row spans a projection warp keeps from its first row pass for its second (per round of 32
+// items; rows beyond are computed again).
+constexpr int kSpanCache = 128;
+
 __device__ __forceinline__ uint32_t pack16(int lo, int hi) {
   return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
 }
@@ -329,6 +333,8 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(Layout L, GaussPtrs
   __shared__ uint32_t s_seg;
   __shared__ int s_acc[kProjThreads / 32][3][32];  // per warp and lane: tiles, first row, last row
   __shared__ int s_carry[kProjThreads / 32][32];   // tiles of an item's rows already written
+  // the first kSpanCache row spans of each warp's round (pass 1), read again by pass 2
+  __shared__ int2 s_span[kProjThreads / 32][kSpanCache];
   const int gstride = L.Tx + 1;
   const int gcells = gstride * (L.Ty + 1);
   const bool use_sgrid = gcells <= kProjGridCells;
@@ -472,9 +478,11 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(Layout L, GaussPtrs
     s_acc[wib][1][lane] = 0x7fffffff;
     s_acc[wib][2][lane] = -1;
     __syncwarp();
+    int st1 = 0;  // this lane's item's first row number in pass 1
     {
       int total = 0;
-      const int st = warp_excl_scan(P.live ? P.y1 - P.y0 : 0, total);
+      st1 = warp_excl_scan(P.live ? P.y1 - P.y0 : 0, total);
+      const int st = st1;
       for (int rb = 0; rb < total; rb += 32) {
         const int r = rb + lane;
         const int o = owner(st, r);
@@ -485,6 +493,7 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(Layout L, GaussPtrs
         if (r < total) {
           const int ty = oy0 + (r - ost);
           const int2 sp = row_span(eo, ty, ox0, ox1);
+          if (r < kSpanCache) s_span[wib][r] = sp;
           if (sp.x <= sp.y) {
             atomicAdd(&s_acc[wib][0][o], sp.y - sp.x + 1);
             atomicMin(&s_acc[wib][1][o], ty);
@@ -533,18 +542,28 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(Layout L, GaussPtrs
       for (int b2 = 0; b2 < total; b2 += 32) {
         const int r = b2 + lane;
         const int o = owner(st, r);
-        const Ellipse eo = owner_ellipse(P.E, o);
-        const int ox0 = __shfl_sync(0xffffffffu, P.x0, o), ox1 = __shfl_sync(0xffffffffu, P.x1, o);
         const int ofirst = __shfl_sync(0xffffffffu, row_first, o);
         const uint32_t obase = __shfl_sync(0xffffffffu, rbase, o);
         const int ost = __shfl_sync(0xffffffffu, st, o);
+        // the row's index in pass 1 (the owner's rows from its rectangle's first row on)
+        const int r1 = __shfl_sync(0xffffffffu, st1, o) + (ofirst - __shfl_sync(0xffffffffu, P.y0, o)) + (r - ost);
+        const bool cached = r < total && r1 < kSpanCache;
         int2 sp = make_int2(1, 0);
         int ty = 0, len = 0;
-        if (r < total) {
-          ty = ofirst + (r - ost);
-          sp = row_span(eo, ty, ox0, ox1);
-          len = sp.x <= sp.y ? sp.y - sp.x + 1 : 0;
+        if (__all_sync(0xffffffffu, cached || r >= total)) {
+          if (r < total) {
+            ty = ofirst + (r - ost);
+            sp = s_span[wib][r1];
+          }
+        } else {
+          const Ellipse eo = owner_ellipse(P.E, o);
+          const int ox0 = __shfl_sync(0xffffffffu, P.x0, o), ox1 = __shfl_sync(0xffffffffu, P.x1, o);
+          if (r < total) {
+            ty = ofirst + (r - ost);
+            sp = cached ? s_span[wib][r1] : row_span(eo, ty, ox0, ox1);
+          }
         }
+        len = sp.x <= sp.y ? sp.y - sp.x + 1 : 0;
         // inclusive sum of len over this round's rows of the same item (they are adjacent lanes)
         int inc = len;
 #pragma unroll

@@ -71,14 +71,11 @@ struct FwdSmemOf<PX, CH, 0> {
 // MANY = false (the fused variant only): compiled without the blocks-per-SM register budget, for
 // grids that fit on the GPU in one wave anyway, where each block's own latency sets the time.
 template <int PX, int CH, bool STATS, bool LOSS, bool OCC = false, int CHB = 0, bool MANY = true>
-__global__ void __launch_bounds__(kTilePixels / PX, (PX == 4 && MANY) ? (CHB > 0 ? kMinBlocksFusedPx4 : kMinBlocksPx4) : 1) k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws,
-                                                                 float* __restrict__ out_rgb,
-                                                                 float* __restrict__ out_depth,
-                                                                 float* __restrict__ out_T,
-                                                                 int32_t* __restrict__ out_last,
-                                                                 uint64_t* __restrict__ evals_out,
-                                                                 uint64_t* __restrict__ blended_out, FusedLoss F,
-                                                                 Occlusion O) {
+__global__ void __launch_bounds__(kTilePixels / PX,
+                                  (PX == 4 && MANY) ? (CHB > 0 ? kMinBlocksFusedPx4 : kMinBlocksPx4) : 1)
+    k_raster_fwd(Layout L, RasterWs<CHB> __restrict__ ws, float* __restrict__ out_rgb, float* __restrict__ out_depth,
+                 float* __restrict__ out_T, int32_t* __restrict__ out_last, uint64_t* __restrict__ evals_out,
+                 uint64_t* __restrict__ blended_out, FusedLoss F, Occlusion O) {
   static_assert(CHB == 0 || (LOSS && !STATS && !OCC), "the fused backward follows the loss-fused forward");
   pdl_wait();
   constexpr int kThreads = kTilePixels / PX;

@@ -50,15 +50,6 @@ __device__ __forceinline__ int reduce10_index(int lane) {
 }
 __device__ __forceinline__ bool reduce10_writer(int lane) { return !(lane & 1) && (!(lane & 2) || !(lane & 12)); }
 
-// Gradient record layout (floats): 0 du, 1 dv, 2 dA, 3 dB, 4 dC, 5 dz, 6 do, 7 dr, 8 dg, 9 db.
-//
-// Per pixel, with dpow = dL/dpower / ln 2 (zero where the splat is skipped or clamped) and
-// (dx, dy) the offset mean - pixel centre, the geometric terms are sums over the pixels of
-//   du = ln2 (2 qa dx + qb dy) dpow,  dv = ln2 (qb dx + 2 qc dy) dpow,
-//   dA = -dx^2 dpow / 2,  dB = -dx dy dpow,  dC = -dy^2 dpow / 2,  do = dpow / opacity.
-// A lane's pixels share dx, so it keeps only P0 = sum dpow, P1 = sum dy dpow, P2 = sum dy^2 dpow
-// and the warp reduces R = (dx P0, P1, dx^2 P0, dx P1, P2, P0); the splat's coefficients
-// qa, qb, qc, opacity are applied once per pair when the warp partials are summed.
 // Shared memory of one backward sweep: the staged chunk, the chunk's record slots, the warp
 // partials of its 10 sums and the warps' largest `last`.
 template <int PX, int CH>
@@ -84,8 +75,9 @@ __device__ __forceinline__ float weighted_colour(float gr, float gg, float gb, f
 //   du = ln2 (2 qa dx + qb dy) dpow,  dv = ln2 (qb dx + 2 qc dy) dpow,
 //   dA = -dx^2 dpow / 2,  dB = -dx dy dpow,  dC = -dy^2 dpow / 2,  do = dpow / opacity.
 // A lane's pixels share dx, so it keeps only P0 = sum dpow, P1 = sum dy dpow, P2 = sum dy^2 dpow
-// and the warp reduces R = (dx P0, P1, dx^2 P0, dx P1, P2, P0); the splat's coefficients
-// qa, qb, qc, opacity are applied once per pair when the warp partials are summed.
+// (per packed pair of pixels, the halves added before the reduction) and the warp reduces
+// R = (dx P0, P1, dx^2 P0, dx P1, P2, P0); the splat's coefficients qa, qb, qc, opacity are
+// applied once per pair when the warp partials are summed.
 //
 // Per pixel of the calling thread (PX vertically adjacent pixels of one column): Sg = the
 // weighted colour of the forward output (weighted_colour), hT = dL/dT_final * T_final, the
